@@ -156,12 +156,18 @@ def element_corners(vertices: np.ndarray) -> np.ndarray:
     return out.reshape(nz * ny * nx, 2, 2, 2, 3)
 
 
-def node_coordinates(vertices: np.ndarray, lx: int) -> np.ndarray:
+def node_coordinates(vertices: np.ndarray, lx: int, elements=None) -> np.ndarray:
     """(E, lx, lx, lx, 3) positions of the GLL nodes [e][k][j][i] under the
-    trilinear map of each element."""
+    trilinear map of each element (all elements, or the listed ones)."""
+    corners = element_corners(vertices)
+    if elements is not None:
+        corners = corners[np.asarray(elements)]
+    return corners_to_nodes(corners, lx)
+
+
+def corners_to_nodes(corners: np.ndarray, lx: int) -> np.ndarray:
     xi, _ = gll(lx)
     phi = np.stack([(1.0 - xi) / 2.0, (1.0 + xi) / 2.0])  # [a][i]
-    corners = element_corners(vertices)
     # x[e,k,j,i,:] = sum_{c,b,a} corner[e,c,b,a,:] phi_c(xi_k) phi_b(xi_j) phi_a(xi_i)
     return np.einsum("ecbad,ck,bj,ai->ekjid", corners, phi, phi, phi, optimize=True)
 
@@ -175,8 +181,8 @@ def _ref_derivatives(f: np.ndarray, d: np.ndarray):
     return fr, fs, ft
 
 
-def box_geometry(vertices: np.ndarray, lx: int) -> dict:
-    """Isoparametric geometry of a box mesh.
+def box_geometry(vertices: np.ndarray, lx: int, elements=None) -> dict:
+    """Isoparametric geometry of a box mesh (all elements, or the listed ones).
 
     Returns a dict with xyz (E,lx,lx,lx,3), jac, B (mass = jac * W) and the
     six factors g11, g22, g33, g12, g13, g23 (each (E,lx,lx,lx)), where
@@ -185,7 +191,7 @@ def box_geometry(vertices: np.ndarray, lx: int) -> dict:
     """
     d = diff_matrix(lx)
     _, w = gll(lx)
-    xyz = node_coordinates(vertices, lx)
+    xyz = node_coordinates(vertices, lx, elements)
     jm = np.empty(xyz.shape[:4] + (3, 3))
     for a in range(3):
         fr, fs, ft = _ref_derivatives(xyz[..., a], d)

@@ -1,0 +1,78 @@
+"""ctypes binding of libaxhelm.so: loads the library and declares the
+prototype of every symbol in include/axhelm.h.  Argument marshalling only.
+
+The library must have been built (``paper_2506_20994_gb300.build.build()``);
+loading fails loudly otherwise - there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libaxhelm.so")
+
+c_int, c_double, c_float = ctypes.c_int, ctypes.c_double, ctypes.c_float
+c_int64, c_void_p, c_char_p = ctypes.c_int64, ctypes.c_void_p, ctypes.c_char_p
+P = ctypes.c_void_p  # every array argument is passed as a raw address
+
+# name -> (restype, argtypes); mirrors include/axhelm.h
+PROTOTYPES = {
+    "ax_strerror": (c_char_p, [c_int]),
+    "ax_version": (c_char_p, []),
+    "ax_helm": (c_int, [P] * 11 + [c_int, c_int, c_void_p]),
+    "ax_helm_variant": (c_int, [c_int] + [P] * 11 + [c_int, c_int, c_int, c_void_p]),
+    "ax_helm_f32": (c_int, [P] * 11 + [c_int, c_int, c_void_p]),
+    "ax_helm_bf16": (c_int, [P] * 11 + [c_int, c_int, c_void_p]),
+    "ax_gll": (c_int, [c_int, P, P]),
+    "ax_dmat": (c_int, [c_int, P, P]),
+    "ax_box_geometry": (c_int, [c_int, c_int, c_int, c_int, P] + [P] * 8),
+    "ax_box_numbering": (c_int, [c_int, c_int, c_int, c_int, P]),
+    "ax_df64_roundtrip": (c_int, [P, P, P, P, c_int64]),
+}
+
+AX_OK = 0
+AX_EINVAL = -1
+AX_ELAUNCH = -3
+AX_ENOMEM = -4
+AX_ENOTCONV = -5
+AX_EBREAKDOWN = -6
+AX_VARIANT_AUTO = 0
+AX_VARIANT_F64_NATIVE = 1
+AX_VARIANT_F64_DF = 2
+
+_lib = None
+_lock = threading.Lock()
+
+
+class AxError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        self.code = code
+        msg = lib().ax_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{fn} failed: {msg} ({code})")
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'`")
+            h = ctypes.CDLL(LIB_PATH, mode=ctypes.RTLD_GLOBAL)
+            for name, (res, args) in PROTOTYPES.items():
+                fn = getattr(h, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = h
+    return _lib
+
+
+def check(fn: str, code: int) -> None:
+    if code != AX_OK:
+        raise AxError(fn, code)

@@ -1,0 +1,144 @@
+// fp64-accurate element operator of Listing 2 that issues no fp64
+// instruction: fp64 inputs are split into double-float pairs with integer
+// operations, every contraction and the pointwise metric step run as
+// error-free fp32 transformations (df64.cuh), and w is re-assembled into
+// fp64 bits.  The schedule is the k-loop one of ax_kstep.cuh (lx*lx threads
+// per element, u and the weighted gradient staged in shared memory).
+//
+// Why: the fp64 pipe of sm_103a issues at a small fraction of the fp32
+// rate, so the fp64 operator on fp64 units is bound by fp64 throughput far
+// below the HBM roofline; fp32 pairs trade each fp64 FMA for about a dozen
+// fp32 operations, which the fp32 pipe issues much faster.
+#pragma once
+
+#include "common.cuh"
+#include "df64.cuh"
+
+namespace ax {
+
+template <int LX>
+__global__ void __launch_bounds__(256)
+ax_df64_kernel(double *__restrict__ w, const double *__restrict__ u,
+               const double *__restrict__ dx, const double *__restrict__ dxt,
+               const double *__restrict__ h1, const double *__restrict__ g11,
+               const double *__restrict__ g22, const double *__restrict__ g33,
+               const double *__restrict__ g12, const double *__restrict__ g13,
+               const double *__restrict__ g23, int nelv, int epb) {
+  using namespace df;
+  constexpr int N2 = LX * LX;
+  constexpr int N3 = LX * N2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  df2 *sdx = reinterpret_cast<df2 *>(smem_raw);
+  df2 *sdxt = sdx + N2;
+  const int le = threadIdx.x / N2;
+  const int p = threadIdx.x - le * N2;
+  const int i = p % LX;
+  const int j = p / LX;
+  df2 *su = sdxt + N2 + (size_t)le * 3 * N3;
+  df2 *swr = su + N3;
+  df2 *sws = swr + N3;
+
+  for (int t = threadIdx.x; t < N2; t += blockDim.x) {
+    sdx[t] = split(__ldg(dx + t));
+    sdxt[t] = split(__ldg(dxt + t));
+  }
+  const long long e = (long long)blockIdx.x * epb + le;
+  const bool active = e < nelv;
+  const size_t base = (size_t)(active ? e : 0) * N3 + p;
+
+  df2 uk[LX];
+#pragma unroll
+  for (int k = 0; k < LX; ++k) {
+    uk[k] = active ? split(__ldg(u + base + (size_t)k * N2)) : df2{0.f, 0.f};
+    su[k * N2 + p] = uk[k];
+  }
+  __syncthreads();
+
+  acc wacc[LX];
+#pragma unroll
+  for (int k = 0; k < LX; ++k) {
+    acc ar = prod(sdx[i], su[k * N2 + j * LX]);
+    acc as = prod(sdx[j], su[k * N2 + i]);
+    acc at = prod(sdx[k], uk[0]);
+#pragma unroll
+    for (int l = 1; l < LX; ++l) {
+      mac(ar, sdx[l * LX + i], su[k * N2 + j * LX + l]);
+      mac(as, sdx[l * LX + j], su[k * N2 + l * LX + i]);
+      mac(at, sdx[l * LX + k], uk[l]);
+    }
+    const df2 ur = result(ar), us = result(as), ut = result(at);
+    df2 wr{0.f, 0.f}, ws{0.f, 0.f}, wt{0.f, 0.f};
+    if (active) {
+      const size_t q = base + (size_t)k * N2;
+      const df2 a11 = split(__ldg(g11 + q)), a22 = split(__ldg(g22 + q));
+      const df2 a33 = split(__ldg(g33 + q)), a12 = split(__ldg(g12 + q));
+      const df2 a13 = split(__ldg(g13 + q)), a23 = split(__ldg(g23 + q));
+      const df2 hh = split(__ldg(h1 + q));
+      acc a = prod(a11, ur);
+      mac(a, a12, us);
+      mac(a, a13, ut);
+      wr = mul2(hh, result(a));
+      a = prod(a12, ur);
+      mac(a, a22, us);
+      mac(a, a23, ut);
+      ws = mul2(hh, result(a));
+      a = prod(a13, ur);
+      mac(a, a23, us);
+      mac(a, a33, ut);
+      wt = mul2(hh, result(a));
+    }
+    swr[k * N2 + p] = wr;
+    sws[k * N2 + p] = ws;
+#pragma unroll
+    for (int kk = 0; kk < LX; ++kk) {
+      if (k == 0)
+        wacc[kk] = prod(sdxt[kk], wt);
+      else
+        mac(wacc[kk], sdxt[k * LX + kk], wt);
+    }
+  }
+  __syncthreads();
+
+#pragma unroll
+  for (int k = 0; k < LX; ++k) {
+    acc a = wacc[k];
+#pragma unroll
+    for (int l = 0; l < LX; ++l) {
+      mac(a, sdxt[l * LX + i], swr[k * N2 + j * LX + l]);
+      mac(a, sdxt[l * LX + j], sws[k * N2 + l * LX + i]);
+    }
+    const df2 r = result(a);
+    if (active) w[base + (size_t)k * N2] = join(r.hi, r.lo);
+  }
+}
+
+template <int LX>
+constexpr size_t df64_smem(int epb) {
+  return (2 * (size_t)LX * LX + (size_t)epb * 3 * LX * LX * LX) * sizeof(df::df2);
+}
+
+template <int LX>
+int launch_df64(double *w, const double *u, const double *dx, const double *dxt,
+                const double *h1, const double *g11, const double *g22, const double *g33,
+                const double *g12, const double *g13, const double *g23, int nelv, int epb,
+                cudaStream_t stream) {
+  if (epb <= 0) epb = 256 / (LX * LX) < 1 ? 1 : 256 / (LX * LX);
+  if (epb * LX * LX > 256) return AX_EINVAL;
+  const size_t smem = df64_smem<LX>(epb);
+  auto kern = ax_df64_kernel<LX>;
+  static size_t granted = 48 * 1024;
+  if (smem > granted) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      (void)cudaGetLastError();
+      return AX_EINVAL;
+    }
+    granted = smem;
+  }
+  const unsigned grid = (unsigned)((nelv + epb - 1) / epb);
+  kern<<<grid, epb * LX * LX, smem, stream>>>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23,
+                                              nelv, epb);
+  return launch_status();
+}
+
+}  // namespace ax

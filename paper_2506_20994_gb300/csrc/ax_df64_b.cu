@@ -1,0 +1,24 @@
+// Instantiations of the double-float fp64-accurate element operator for
+// lx in {8, 9, 10} (split across files to compile in parallel).
+#include "ax_df64.cuh"
+#include "dispatch.h"
+
+namespace ax {
+
+int dispatch_df64_b(int lx, double *w, const double *u, const double *dx, const double *dxt,
+                    const double *h1, const double *g11, const double *g22, const double *g33,
+                    const double *g12, const double *g13, const double *g23, int nelv, int epb,
+                    cudaStream_t st) {
+  switch (lx) {
+    case 8:
+      return launch_df64<8>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nelv, epb, st);
+    case 9:
+      return launch_df64<9>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nelv, epb, st);
+    case 10:
+      return launch_df64<10>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nelv, epb, st);
+    default:
+      return AX_EINVAL;
+  }
+}
+
+}  // namespace ax

@@ -1,0 +1,86 @@
+// C-ABI entry points of the element operator (Listing 2): argument checks
+// and dispatch over lx and storage type to the templated kernels.
+#include "common.cuh"
+#include "dispatch.h"
+
+namespace {
+
+
+template <typename W, typename S, typename T>
+int check_args(W *w, const S *u, const T *dx, const T *dxt, const S *h1, const S *g11,
+               const S *g22, const S *g33, const S *g12, const S *g13, const S *g23, int lx,
+               int nelv) {
+  if (!ax::lx_ok(lx) || nelv < 0) return AX_EINVAL;
+  if (nelv == 0) return 1;  // no-op
+  if (!ax::all_nonnull(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23)) return AX_EINVAL;
+  return AX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ax_strerror(int code) {
+  switch (code) {
+    case AX_OK: return "ok";
+    case AX_EINVAL: return "invalid argument";
+    case AX_ELAUNCH: return "CUDA launch or call failed";
+    case AX_ENOMEM: return "allocation failed";
+    case AX_ENOTCONV: return "solver did not converge within maxit";
+    case AX_EBREAKDOWN: return "solver breakdown (p.Ap <= 0 or non-finite value)";
+    default: return "unknown status";
+  }
+}
+
+const char *ax_version(void) { return "axhelm 0.1 sm_103a"; }
+
+int ax_helm_variant(int variant, double *w, const double *u, const double *dx,
+                    const double *dxt, const double *h1, const double *g11, const double *g22,
+                    const double *g33, const double *g12, const double *g13, const double *g23,
+                    int lx, int nelv, int elems_per_block, void *stream) {
+  int rc = check_args(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx, nelv);
+  if (rc != AX_OK) return rc > 0 ? AX_OK : rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (variant == AX_VARIANT_AUTO)
+    variant = lx <= ax::AX_DF64_LX_MAX ? AX_VARIANT_F64_DF : AX_VARIANT_F64_NATIVE;
+  switch (variant) {
+    case AX_VARIANT_F64_NATIVE:
+      return ax::dispatch_kstep_f64(lx, w, u, dx, dxt, h1, g11, g22, g33, g12,
+                                                    g13, g23, nelv, elems_per_block, st);
+    case AX_VARIANT_F64_DF:
+      return ax::dispatch_df64(lx, w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nelv,
+                           elems_per_block, st);
+    default:
+      return AX_EINVAL;
+  }
+}
+
+int ax_helm(double *w, const double *u, const double *dx, const double *dxt, const double *h1,
+            const double *g11, const double *g22, const double *g33, const double *g12,
+            const double *g13, const double *g23, int lx, int nelv, void *stream) {
+  return ax_helm_variant(AX_VARIANT_AUTO, w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx,
+                         nelv, 0, stream);
+}
+
+int ax_helm_f32(float *w, const float *u, const float *dx, const float *dxt, const float *h1,
+                const float *g11, const float *g22, const float *g33, const float *g12,
+                const float *g13, const float *g23, int lx, int nelv, void *stream) {
+  int rc = check_args(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx, nelv);
+  if (rc != AX_OK) return rc > 0 ? AX_OK : rc;
+  return ax::dispatch_kstep_f32(lx, w, u, dx, dxt, h1, g11, g22, g33, g12, g13,
+                                             g23, nelv, 0, (cudaStream_t)stream);
+}
+
+int ax_helm_bf16(float *w, const ax_bf16 *u, const float *dx, const float *dxt,
+                 const ax_bf16 *h1, const ax_bf16 *g11, const ax_bf16 *g22, const ax_bf16 *g33,
+                 const ax_bf16 *g12, const ax_bf16 *g13, const ax_bf16 *g23, int lx, int nelv,
+                 void *stream) {
+  int rc = check_args(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx, nelv);
+  if (rc != AX_OK) return rc > 0 ? AX_OK : rc;
+  using B = __nv_bfloat16;
+  auto c = [](const ax_bf16 *p) { return reinterpret_cast<const B *>(p); };
+  return ax::dispatch_kstep_bf16(lx, w, c(u), dx, dxt, c(h1), c(g11), c(g22), c(g33),
+                                         c(g12), c(g13), c(g23), nelv, 0, (cudaStream_t)stream);
+}
+
+}  // extern "C"

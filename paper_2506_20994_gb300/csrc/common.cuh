@@ -1,0 +1,57 @@
+// Shared helpers of the CUDA library: status codes, argument checks, the
+// element-field loaders for each storage type, and launch bookkeeping.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/axhelm.h"
+
+#define AX_HD __host__ __device__ __forceinline__
+#define AX_D __device__ __forceinline__
+
+namespace ax {
+
+// Converts a CUDA launch status into an AX code (never aborts).
+inline int launch_status() {
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return AX_ELAUNCH;
+  }
+  return AX_OK;
+}
+
+inline bool lx_ok(int lx) { return lx >= AX_LX_MIN && lx <= AX_LX_MAX; }
+
+template <typename... P>
+inline bool all_nonnull(P... p) {
+  bool ok = true;
+  ((ok = ok && (p != nullptr)), ...);
+  return ok;
+}
+
+// Storage -> compute conversion of one element-field value.
+template <typename T>
+AX_D T ld_cvt(const double *p) { return (T)__ldg(p); }
+template <typename T>
+AX_D T ld_cvt(const float *p) { return (T)__ldg(p); }
+template <typename T>
+AX_D T ld_cvt(const __nv_bfloat16 *p) { return (T)__bfloat162float(__ldg(p)); }
+
+// Sets the dynamic shared-memory limit of a kernel once per process
+// (per kernel and per size class); returns false if the device refuses.
+template <typename K>
+inline bool ensure_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return true;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+}  // namespace ax

@@ -1,0 +1,55 @@
+// Declarations of the per-lx dispatchers; each is defined in its own
+// translation unit so that the kernel instantiations compile in parallel.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace ax {
+
+// Largest lx with a double-float instantiation.
+constexpr int AX_DF64_LX_MAX = 12;
+
+// k-loop kernel: fp64 storage and fp64 units.
+int dispatch_kstep_f64(int lx, double *w, const double *u, const double *dx, const double *dxt,
+                       const double *h1, const double *g11, const double *g22,
+                       const double *g33, const double *g12, const double *g13,
+                       const double *g23, int nelv, int epb, cudaStream_t st);
+// k-loop kernel: fp32 storage and arithmetic.
+int dispatch_kstep_f32(int lx, float *w, const float *u, const float *dx, const float *dxt,
+                       const float *h1, const float *g11, const float *g22, const float *g33,
+                       const float *g12, const float *g13, const float *g23, int nelv, int epb,
+                       cudaStream_t st);
+// k-loop kernel: bf16 storage of u, h1, G; fp32 D, arithmetic and w.
+int dispatch_kstep_bf16(int lx, float *w, const __nv_bfloat16 *u, const float *dx,
+                        const float *dxt, const __nv_bfloat16 *h1, const __nv_bfloat16 *g11,
+                        const __nv_bfloat16 *g22, const __nv_bfloat16 *g33,
+                        const __nv_bfloat16 *g12, const __nv_bfloat16 *g13,
+                        const __nv_bfloat16 *g23, int nelv, int epb, cudaStream_t st);
+
+// fp64-accurate double-float kernel, lx in 2..7 (a), 8..10 (b), 11..12 (c);
+// AX_EINVAL above AX_DF64_LX_MAX.
+#define AX_DF64_DECL(X)                                                                        \
+  int dispatch_df64_##X(int lx, double *w, const double *u, const double *dx,                  \
+                        const double *dxt, const double *h1, const double *g11,                \
+                        const double *g22, const double *g33, const double *g12,               \
+                        const double *g13, const double *g23, int nelv, int epb,               \
+                        cudaStream_t st);
+AX_DF64_DECL(a)
+AX_DF64_DECL(b)
+AX_DF64_DECL(c)
+#undef AX_DF64_DECL
+
+inline int dispatch_df64(int lx, double *w, const double *u, const double *dx, const double *dxt,
+                  const double *h1, const double *g11, const double *g22, const double *g33,
+                  const double *g12, const double *g13, const double *g23, int nelv, int epb,
+                  cudaStream_t st) {
+  if (lx > AX_DF64_LX_MAX) return AX_EINVAL;
+  auto f = lx <= 7 ? dispatch_df64_a : (lx <= 10 ? dispatch_df64_b : dispatch_df64_c);
+  return f(lx, w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nelv, epb, st);
+}
+
+}  // namespace ax
+
+#define AX_LX_CASES(M) \
+  M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16)

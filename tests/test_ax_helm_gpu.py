@@ -1,0 +1,168 @@
+"""GPU parity of the element operator (Listing 2) against the fp64 oracle,
+through the C ABI.
+
+Tolerances (relative L2 over the whole output, written per mode):
+  * fp64 (both the double-float and the fp64-unit kernel): 1e-12;
+  * fp32 storage + fp32 arithmetic: 1e-6;
+  * bf16 storage of u, h1, G with fp32 D and arithmetic: 2e-2.
+Sizes span several blocks and ragged tails (E = 1, 7, 64, 567); the full
+benchmark size (E = 32768, lx = 8) is checked on sampled elements that the
+oracle evaluates one by one.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import paper_2506_20994_gb300 as ax  # noqa: E402
+from paper_2506_20994_gb300 import synth  # noqa: E402
+
+from _cases import GKEYS, operator_case, rel_l2  # noqa: E402
+
+TOL = {"f64": 1e-12, "f32": 1e-6, "bf16": 2e-2}
+DIMS = [(1, 1, 1), (7, 1, 1), (4, 4, 4), (9, 9, 7)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ax.build()
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def _run_f64(case, variant, epb=0):
+    lx = case["lx"]
+    args = [_dev(case[k]) for k in ("u", "dx", "dxt", "h1") + GKEYS]
+    w = torch.full_like(args[0], float("nan"))
+    ax.ax_helm(w, *args, lx, variant=variant, elems_per_block=epb)
+    torch.cuda.synchronize()
+    return w.cpu().numpy()
+
+
+@pytest.mark.parametrize("lx", range(2, 13))
+@pytest.mark.parametrize("dims", DIMS, ids=lambda d: "E%d" % (d[0] * d[1] * d[2]))
+def test_f64_df_parity(lx, dims):
+    case = operator_case(dims, lx, seed=lx)
+    w = _run_f64(case, ax.AX_VARIANT_F64_DF)
+    assert rel_l2(w, case["w"]) <= TOL["f64"]
+    assert np.abs(w - case["w"]).max() <= 1e-11 * np.abs(case["w"]).max()
+
+
+@pytest.mark.parametrize("lx", list(range(2, 17)))
+def test_f64_native_parity(lx):
+    case = operator_case((3, 2, 2) if lx <= 12 else (2, 1, 1), lx, seed=100 + lx)
+    w = _run_f64(case, ax.AX_VARIANT_F64_NATIVE)
+    assert rel_l2(w, case["w"]) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("lx", [13, 16])
+def test_auto_variant_above_df_range(lx):
+    case = operator_case((2, 1, 1), lx, seed=7)
+    w = _run_f64(case, ax.AX_VARIANT_AUTO)
+    assert rel_l2(w, case["w"]) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("epb", [1, 2, 3, 4])
+def test_f64_df_elements_per_block(epb):
+    case = operator_case((5, 3, 1), 8, seed=31)
+    w = _run_f64(case, ax.AX_VARIANT_F64_DF, epb=epb)
+    assert rel_l2(w, case["w"]) <= TOL["f64"]
+
+
+def test_f64_df_adversarial_inputs():
+    """Constant fields (w ~ 0 by cancellation), wide magnitude range, zeros."""
+    lx = 8
+    case = operator_case((3, 3, 3), lx, seed=41)
+    # constant u: the oracle gives ~1e-16 noise; the kernel must too
+    const = dict(case)
+    const["u"] = np.full_like(case["u"], 2.5)
+    w = _run_f64(const, ax.AX_VARIANT_F64_DF)
+    ref_scale = np.abs(case["w"]).max() * 2.5
+    assert np.abs(w).max() <= 1e-13 * ref_scale
+    # per-element magnitudes spread over 1e-6 .. 1e6, some zero elements
+    wide = dict(case)
+    scale = 10.0 ** synth.uniform((case["u"].shape[0], 1, 1, 1), seed=42, lo=-6, hi=6)
+    wide["u"] = case["u"] * scale
+    wide["u"][::5] = 0.0
+    ref = oracle.ax_helm(wide["u"], case["dx"], case["dxt"], case["h1"],
+                         *[case[k] for k in GKEYS], lx)
+    w = _run_f64(wide, ax.AX_VARIANT_F64_DF)
+    per_el = np.linalg.norm((w - ref).reshape(len(ref), -1), axis=1)
+    per_ref = np.linalg.norm(ref.reshape(len(ref), -1), axis=1)
+    nz = per_ref > 0
+    assert np.all(per_el[nz] <= 1e-12 * per_ref[nz])
+    assert np.all(w[::5] == 0.0)
+
+
+def test_f64_deterministic():
+    case = operator_case((4, 4, 2), 6, seed=3)
+    a = _run_f64(case, ax.AX_VARIANT_F64_DF)
+    b = _run_f64(case, ax.AX_VARIANT_F64_DF)
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("lx", [2, 5, 6, 8, 10, 12, 16])
+def test_f32_parity(lx):
+    case = operator_case((4, 3, 2) if lx <= 12 else (2, 1, 1), lx, seed=200 + lx)
+    f = torch.float32
+    args = [_dev(case[k], f) for k in ("u", "dx", "dxt", "h1") + GKEYS]
+    w = torch.empty_like(args[0])
+    ax.ax_helm_f32(w, *args, lx)
+    torch.cuda.synchronize()
+    assert rel_l2(w.cpu().numpy(), case["w"]) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("lx", [2, 5, 8, 10, 12])
+def test_bf16_parity(lx):
+    case = operator_case((4, 3, 2), lx, seed=300 + lx)
+    b = torch.bfloat16
+    u = _dev(case["u"], b)
+    fields = [_dev(case[k], b) for k in ("h1",) + GKEYS]
+    dx, dxt = _dev(case["dx"], torch.float32), _dev(case["dxt"], torch.float32)
+    w = torch.empty(u.shape, dtype=torch.float32, device="cuda")
+    ax.ax_helm_bf16(w, u, dx, dxt, *fields, lx)
+    torch.cuda.synchronize()
+    assert rel_l2(w.cpu().numpy(), case["w"]) <= TOL["bf16"]
+
+
+def test_full_size_sampled_parity():
+    """E = 32768 (32^3), lx = 8, fp64, in the benchmark's launch
+    configuration; the oracle evaluates 96 sampled elements."""
+    lx, n = 8, 32
+    v = synth.box_vertices(n, seed=0)
+    g = ax.box_geometry(v, lx)
+    shape = g["g11"].shape
+    u = synth.uniform(shape, seed=1)
+    h1 = np.ones(shape)
+    dx, dxt = ax.dmat(lx)
+    args = [_dev(a) for a in (u, dx, dxt, h1)] + [_dev(g[k]) for k in GKEYS]
+    w = torch.empty_like(args[0])
+    ax.ax_helm(w, *args, lx)
+    torch.cuda.synchronize()
+    w = w.cpu().numpy()
+    pick = np.unique(np.concatenate([[0, shape[0] - 1], synth.rng(9).integers(0, shape[0], 94)]))
+    go = oracle.box_geometry(v, lx, elements=pick)
+    dxo, dxto = oracle.d_buffers(lx)
+    ref = oracle.ax_helm(u[pick], dxo, dxto, h1[pick], *[go[k] for k in GKEYS], lx)
+    assert rel_l2(w[pick], ref) <= TOL["f64"]
+
+
+def test_zero_elements_is_noop():
+    w = torch.full((8,), 7.0, dtype=torch.float64, device="cuda")
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    d = torch.zeros(4, dtype=torch.float64, device="cuda")
+    ax.ax_helm(e, e, d, d, e, e, e, e, e, e, e, 2)
+    torch.cuda.synchronize()
+    assert torch.all(w == 7.0)
+
+
+def test_bad_elements_per_block_rejected():
+    case = operator_case((1, 1, 1), 8, seed=1)
+    with pytest.raises(ax.AxError):
+        _run_f64(case, ax.AX_VARIANT_F64_DF, epb=5)

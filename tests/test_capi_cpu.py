@@ -1,0 +1,133 @@
+"""CPU checks of the C-ABI library: it loads, exports every symbol the header
+declares, its host set-up agrees with the oracle, the integer fp64 <-> fp32
+pair conversions used by the fp64 kernels are correct bit for bit, and the
+argument checks reject bad calls before touching the GPU."""
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2506_20994_gb300 as ax
+from paper_2506_20994_gb300 import _lib, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ax.build()
+
+
+def _header_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"^[A-Za-z_][\w \*]*?\b(ax_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
+
+
+def test_every_header_symbol_is_exported_and_bound():
+    names = _header_functions()
+    assert "ax_helm" in names and len(names) >= 10
+    lib = _lib.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in _lib.PROTOTYPES, f"{n} has no ctypes prototype"
+    assert lib.ax_version().decode().startswith("axhelm")
+
+
+@pytest.mark.parametrize("lx", range(2, 17))
+def test_host_gll_and_dmat_match_oracle(lx):
+    x, w = ax.gll(lx)
+    xo, wo = oracle.gll(lx)
+    np.testing.assert_allclose(x, xo, atol=2e-16 * lx)
+    np.testing.assert_allclose(w, wo, rtol=1e-14)
+    dx, dxt = ax.dmat(lx)
+    dxo, dxto = oracle.d_buffers(lx)
+    scale = np.abs(dxo).max()
+    np.testing.assert_allclose(dx, dxo, atol=1e-13 * scale)
+    np.testing.assert_allclose(dxt, dxto, atol=1e-13 * scale)
+
+
+@pytest.mark.parametrize("lx", [2, 3, 5, 8, 12])
+def test_host_geometry_matches_oracle(lx):
+    v = synth.box_vertices(3, 2, 4, seed=21)
+    g = ax.box_geometry(v, lx, want_xyz=True)
+    go = oracle.box_geometry(v, lx)
+    for k in ("g11", "g22", "g33", "g12", "g13", "g23"):
+        scale = np.abs(go["g11"]).max()
+        np.testing.assert_allclose(g[k], go[k], rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(g["mass"], go["B"], rtol=1e-12)
+    np.testing.assert_allclose(g["xyz"], go["xyz"], atol=1e-15)
+
+
+def test_host_numbering_matches_oracle():
+    for dims, lx in (((3, 2, 4), 5), ((1, 1, 1), 2), ((2, 5, 3), 8)):
+        np.testing.assert_array_equal(ax.box_numbering(*dims, lx), oracle.numbering(*dims, lx))
+
+
+def _ulp64(x):
+    return np.spacing(np.abs(x))
+
+
+def test_df64_split_is_exact_truncation():
+    g = synth.rng(5)
+    mags = 10.0 ** g.uniform(-20, 30, size=20000)
+    x = mags * np.where(g.uniform(size=mags.size) < 0.5, -1.0, 1.0)
+    x = np.concatenate([x, [1.0, -1.0, 2.0 ** -40, np.nextafter(1.0, 0), np.nextafter(1.0, 2),
+                            3.0, 1.0 / 3.0, -2.0 ** 100, 123456789.123456789]])
+    hi, lo, back = ax.df64_roundtrip(x)
+    hi64 = hi.astype(np.float64)
+    # hi is x truncated toward zero to fp32: |hi| <= |x| < |hi| + ulp32(hi)
+    assert np.all(np.abs(hi64) <= np.abs(x))
+    assert np.all(np.abs(x) - np.abs(hi64) < np.spacing(np.abs(hi)).astype(np.float64))
+    assert np.all(np.sign(hi64) == np.sign(x))
+    # hi + lo carries 47 bits
+    err = np.abs(x - (hi64 + lo.astype(np.float64)))
+    assert np.all(err <= 2.0 ** -46 * np.abs(x))
+    # and the join brings it back to within one fp64 ulp
+    assert np.all(np.abs(back - x) <= 2.0 ** -46 * np.abs(x))
+
+
+def test_df64_small_and_special_values():
+    x = np.array([0.0, -0.0, 1e-30, -1e-35, 2.0 ** -126, 2.0 ** -130, 1e-40])
+    hi, lo, back = ax.df64_roundtrip(x)
+    # absolute error stays below 2^-100 where relative accuracy is not promised
+    assert np.all(np.abs(back - x) <= np.maximum(2.0 ** -46 * np.abs(x), 2.0 ** -100))
+    assert back[0] == 0.0 and back[1] == 0.0
+
+
+def test_df64_join_rounds_pairs():
+    """join(hi, lo) of a normalised pair is within one fp64 ulp of hi + lo,
+    including pairs that cross a power of two downwards."""
+    g = synth.rng(6)
+    hi = (g.uniform(0.5, 2.0, size=5000) * 2.0 ** g.integers(-40, 40, size=5000)).astype(np.float32)
+    hi[:200] = (2.0 ** g.integers(-30, 30, size=200)).astype(np.float32)  # powers of two
+    hi[::2] *= -1
+    ulp32 = np.spacing(np.abs(hi)).astype(np.float64)
+    lo = (g.uniform(-0.5, 0.5, size=hi.size) * ulp32).astype(np.float32)
+    exact = hi.astype(np.float64) + lo.astype(np.float64)
+    # join via the roundtrip entry: split(exact) -> norm -> join
+    _, _, back = ax.df64_roundtrip(exact)
+    assert np.all(np.abs(back - exact) <= 2.0 ** -46 * np.abs(exact))
+
+
+def test_argument_checks_need_no_gpu():
+    lib = _lib.lib()
+    nul = [None] * 11
+    # nelv == 0 is a no-op that succeeds
+    assert lib.ax_helm(*nul, 8, 0, None) == _lib.AX_OK
+    assert lib.ax_helm_f32(*nul, 8, 0, None) == _lib.AX_OK
+    # NULL pointers with nelv > 0
+    assert lib.ax_helm(*nul, 8, 5, None) == _lib.AX_EINVAL
+    # lx out of range, negative nelv
+    for lx in (0, 1, 17, 100):
+        assert lib.ax_helm(*nul, lx, 0, None) == _lib.AX_EINVAL
+    assert lib.ax_helm(*nul, 8, -1, None) == _lib.AX_EINVAL
+    assert lib.ax_helm_bf16(*nul, 1, 3, None) == _lib.AX_EINVAL
+    assert lib.ax_helm_variant(99, *[1] * 11, 8, 4, 0, None) == _lib.AX_EINVAL
+    assert lib.ax_gll(1, None, None) == _lib.AX_EINVAL
+    assert lib.ax_dmat(17, None, None) == _lib.AX_EINVAL
