@@ -97,6 +97,122 @@ int ax_helm_bf16(float *w, const ax_bf16 *u, const float *dx, const float *dxt,
                  const ax_bf16 *g23, int lx, int nelv, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Gather-scatter (direct-stiffness summation; Sec. "Neko and Small Tensor
+ * Kernel" names it as the second main ingredient beside the small matrix
+ * products): every local copy of a global node receives the sum over all
+ * copies of that node.
+ * ------------------------------------------------------------------------ */
+typedef struct ax_gs ax_gs;
+
+/* Builds the handle from the global id of every local point (host array
+ * glob[n_local], ids >= 0, n_local < 2^31).  Allocates device memory
+ * (the CSR list of shared nodes and 1/multiplicity per point) and
+ * synchronises `stream`.  AX_EINVAL on bad arguments, AX_ENOMEM if an
+ * allocation or copy fails. */
+int ax_gs_setup(ax_gs **gs, const int64_t *glob, int64_t n_local, void *stream);
+/* v[n_local] (device) <- summed over shared copies; deterministic order. */
+int ax_gs_sum(ax_gs *gs, double *v, void *stream);
+int ax_gs_sum_f32(ax_gs *gs, float *v, void *stream);
+/* Sizes of the handle (any pointer may be NULL). */
+int ax_gs_info(const ax_gs *gs, int64_t *n_local, int64_t *n_shared, int64_t *n_copies);
+/* Device array of 1/multiplicity per local point, owned by the handle. */
+const double *ax_gs_inverse_multiplicity(const ax_gs *gs);
+int ax_gs_free(ax_gs *gs);
+
+/* ------------------------------------------------------------------------
+ * Poisson solve: A p = mask .* gs(Ax(p)), the assembled stiffness operator
+ * of the weak form in Sec. "The Spectral Element Method" with homogeneous
+ * Dirichlet rows masked out.  Vectors are local (nelv*lx^3, continuous
+ * across shared nodes); inner products and norms are over unique global
+ * nodes (local sums weighted by 1/multiplicity).
+ * ------------------------------------------------------------------------ */
+typedef struct ax_poisson ax_poisson;
+
+#define AX_PREC_F32 1  /* inner solve: fp32 G, h1, D and fp32 vectors       */
+#define AX_PREC_BF16 2 /* inner solve: bf16 G, h1; fp32 D and fp32 vectors */
+
+/* Creates the operator handle.  dx..g23 and mask (1 interior, 0 on the
+ * Dirichlet boundary) are caller-owned device arrays that must outlive the
+ * handle; gs is borrowed likewise.  Allocates the work vectors and computes
+ * the exact assembled Jacobi diagonal on the device; synchronises stream. */
+int ax_poisson_create(ax_poisson **P, int lx, int nelv, const double *dx, const double *dxt,
+                      const double *h1, const double *g11, const double *g22,
+                      const double *g33, const double *g12, const double *g13,
+                      const double *g23, const double *mask, ax_gs *gs, void *stream);
+int ax_poisson_destroy(ax_poisson *P);
+/* w = mask .* gs(Ax(u)), fp64-accurate; asynchronous. */
+int ax_poisson_apply(ax_poisson *P, double *w, const double *u, void *stream);
+/* Device array of the masked inverse Jacobi diagonal, owned by P. */
+int ax_poisson_jacobi(const ax_poisson *P, const double **minv);
+/* How often the solvers read the residual norm back (default 1). */
+int ax_poisson_set_check_every(ax_poisson *P, int every);
+
+/* Jacobi-preconditioned CG in fp64 from x0 = 0 until ||r|| <= tol ||b||
+ * (b is masked first).  Writes the iteration count and the final relative
+ * residual.  Synchronises stream.  Returns AX_OK, AX_ENOTCONV (maxit
+ * reached), AX_EBREAKDOWN (p.Ap <= 0 or non-finite) or AX_EINVAL. */
+int ax_cg_solve(ax_poisson *P, double *x, const double *b, double tol, int maxit, int *iters,
+                double *relres, void *stream);
+
+/* Mixed-precision iterative refinement: outer loop r = b - A x in fp64
+ * (fp64-accurate operator), inner Jacobi-PCG on A d = r in fp32 with the
+ * operator data in fp32 (AX_PREC_F32) or bf16 (AX_PREC_BF16) to the
+ * relative tolerance inner_tol, x += d in fp64; stops when the fp64
+ * residual satisfies ||r|| <= tol ||b||.  The first call per mode converts
+ * the operator data (allocates).  Synchronises stream. */
+int ax_mpcg_solve(ax_poisson *P, int mode, double *x, const double *b, double tol,
+                  double inner_tol, int max_outer, int max_inner, int *outer_iters,
+                  int *inner_iters, double *relres, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batched operator over many independent meshes of uneven size and mixed
+ * lx in one persistent launch.  The paper applies Listing 2 to one mesh per
+ * launch and Neko picks its kernel variant by run-time timing (Sec.
+ * "Methodology"); the plan below generalises both: work items of tuned
+ * elements-per-block, statically balanced across persistent blocks.
+ * ------------------------------------------------------------------------ */
+typedef struct ax_batch ax_batch;
+
+#define AX_BATCH_F64 1 /* fp64 data, fp64-accurate double-float arithmetic */
+#define AX_BATCH_F32 2 /* fp32 data and arithmetic                         */
+
+/* One mesh of a batch: device pointers (double* for AX_BATCH_F64, float*
+ * for AX_BATCH_F32) in the conventions above; lx in [2, 12]. */
+typedef struct {
+  int lx, nelv;
+  void *w;
+  const void *u, *dx, *dxt, *h1, *g11, *g22, *g33, *g12, *g13, *g23;
+} ax_batch_mesh;
+
+/* Builds the plan (host array meshes[nmesh], copied; the device arrays are
+ * borrowed and must outlive the plan).  blocks_per_sm <= 0 picks the
+ * default residency.  Allocates the device work list; synchronises stream.
+ * Uses the tuned elements-per-block of each lx (ax_tune_*), else a default. */
+int ax_batch_create(ax_batch **B, int dtype, int nmesh, const ax_batch_mesh *meshes,
+                    int blocks_per_sm, void *stream);
+/* All meshes of the plan in one persistent kernel launch (asynchronous). */
+int ax_batch_launch(ax_batch *B, void *stream);
+/* The same launch replayed from a CUDA graph captured on the first call. */
+int ax_batch_graph_launch(ax_batch *B, void *stream);
+/* Plan sizes and the algorithmic flops / bytes of one launch. */
+int ax_batch_info(const ax_batch *B, int *nitems, int *nblocks, int64_t *smem_bytes,
+                  double *flops, double *bytes);
+int ax_batch_destroy(ax_batch *B);
+
+/* Autotuner: elements per block for (dtype, lx), process-wide.  ax_tune_run
+ * times every admissible value on the caller's buffers (nelv elements of
+ * the given dtype; w is overwritten; reps timed launches each) and records
+ * the fastest; ax_tune_set / ax_tune_get read and write the table (0 means
+ * the built-in default).  The single-mesh dispatch and ax_batch_create use
+ * the table. */
+int ax_tune_run(int dtype, int lx, int nelv, void *w, const void *u, const void *dx,
+                const void *dxt, const void *h1, const void *g11, const void *g22,
+                const void *g33, const void *g12, const void *g13, const void *g23, int reps,
+                int *best_epb, float *best_ms, void *stream);
+int ax_tune_set(int dtype, int lx, int elems_per_block);
+int ax_tune_get(int dtype, int lx, int *elems_per_block);
+
+/* ------------------------------------------------------------------------
  * Host-side discretisation set-up (no GPU needed; plain host memory).
  * ------------------------------------------------------------------------ */
 

@@ -13,13 +13,17 @@ from __future__ import annotations
 import numpy as np
 
 from . import _lib
-from ._lib import (AX_VARIANT_AUTO, AX_VARIANT_F64_DF, AX_VARIANT_F64_NATIVE, AxError,
+from ._lib import (AX_BATCH_F32, AX_BATCH_F64, AX_PREC_BF16, AX_PREC_F32, AX_VARIANT_AUTO,
+                   AX_VARIANT_F64_DF,
+                   AX_VARIANT_F64_NATIVE, AxError,
                    check, lib)
 
 __all__ = [
     "lib", "AxError", "gll", "dmat", "box_geometry", "box_numbering", "ax_helm",
     "ax_helm_f32", "ax_helm_bf16", "AX_VARIANT_AUTO", "AX_VARIANT_F64_DF",
-    "AX_VARIANT_F64_NATIVE", "df64_roundtrip", "build",
+    "AX_VARIANT_F64_NATIVE", "df64_roundtrip", "build", "GatherScatter", "Poisson",
+    "AX_PREC_F32", "AX_PREC_BF16", "Batch", "tune", "tune_set", "tune_get", "AX_BATCH_F64",
+    "AX_BATCH_F32",
 ]
 
 
@@ -153,3 +157,241 @@ def ax_helm_bf16(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx: int) -> No
                             h1.data_ptr(), g11.data_ptr(), g22.data_ptr(), g33.data_ptr(),
                             g12.data_ptr(), g13.data_ptr(), g23.data_ptr(), lx, nel, _stream())
     check("ax_helm_bf16", rc)
+
+
+# ---------------------------------------------------------------------------
+# gather-scatter and the Poisson solvers
+# ---------------------------------------------------------------------------
+class _DeviceArray:
+    """A borrowed device array exposed through __cuda_array_interface__ so
+    torch can view memory the library owns (no copy)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str, owner):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
+
+
+class GatherScatter:
+    """Direct-stiffness summation over shared nodes (ax_gs_*)."""
+
+    def __init__(self, glob: np.ndarray):
+        import ctypes
+        g = np.ascontiguousarray(glob, dtype=np.int64).ravel()
+        h = ctypes.c_void_p()
+        check("ax_gs_setup", lib().ax_gs_setup(ctypes.addressof(h), _addr(g), g.size, _stream()))
+        self._h = h
+        self.n_local = g.size
+
+    @property
+    def handle(self):
+        return self._h
+
+    def sum(self, v) -> None:
+        import torch
+        if v.dtype == torch.float64:
+            check("ax_gs_sum", lib().ax_gs_sum(self._h, v.data_ptr(), _stream()))
+        elif v.dtype == torch.float32:
+            check("ax_gs_sum_f32", lib().ax_gs_sum_f32(self._h, v.data_ptr(), _stream()))
+        else:
+            raise TypeError("gs sum needs fp64 or fp32")
+
+    def info(self):
+        import ctypes
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        check("ax_gs_info", lib().ax_gs_info(self._h, ctypes.addressof(a), ctypes.addressof(b),
+                                             ctypes.addressof(c)))
+        return {"n_local": a.value, "n_shared": b.value, "n_copies": c.value}
+
+    def inverse_multiplicity(self):
+        import torch
+        ptr = lib().ax_gs_inverse_multiplicity(self._h)
+        return torch.as_tensor(_DeviceArray(ptr, self.n_local, "<f8", self), device="cuda")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib._lib is not None:
+            _lib._lib.ax_gs_free(h)
+            self._h = None
+
+
+class Poisson:
+    """Poisson problem -div(h1 grad u) = f on a perturbed box with
+    homogeneous Dirichlet boundaries, set up on the host by the library
+    and solved on the GPU (ax_poisson_*, ax_cg_solve, ax_mpcg_solve)."""
+
+    GKEYS = ("g11", "g22", "g33", "g12", "g13", "g23")
+
+    def __init__(self, vertices: np.ndarray, lx: int, h1=None, device=None):
+        import ctypes
+        import torch
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        v = np.ascontiguousarray(vertices, dtype=np.float64)
+        nz, ny, nx = (s - 1 for s in v.shape[:3])
+        self.dims, self.lx = (nx, ny, nz), lx
+        geo = box_geometry(v, lx, want_xyz=True)
+        self.nelv = nx * ny * nz
+        self.xyz = geo["xyz"]
+        self.mass_host = geo["mass"]
+        glob = box_numbering(nx, ny, nz, lx)
+        self.glob = glob
+        n = lx - 1
+        NX, NY, NZ = nx * n + 1, ny * n + 1, nz * n + 1
+        X, Y, Z = glob % NX, (glob // NX) % NY, glob // (NX * NY)
+        on = (X == 0) | (X == NX - 1) | (Y == 0) | (Y == NY - 1) | (Z == 0) | (Z == NZ - 1)
+        mask = np.where(on, 0.0, 1.0)
+        h1v = np.ones_like(mask) if h1 is None else np.broadcast_to(
+            np.asarray(h1, dtype=np.float64), mask.shape).copy()
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=self.device)
+        dx, dxt = dmat(lx)
+        self.d = {"dx": t(dx), "dxt": t(dxt), "h1": t(h1v), "mask": t(mask)}
+        for k in self.GKEYS:
+            self.d[k] = t(geo[k])
+        self.mass = t(geo["mass"])
+        with torch.cuda.device(self.device):
+            self.gs = GatherScatter(glob)
+            h = ctypes.c_void_p()
+            d = self.d
+            rc = lib().ax_poisson_create(
+                ctypes.addressof(h), lx, self.nelv, d["dx"].data_ptr(), d["dxt"].data_ptr(),
+                d["h1"].data_ptr(), *[d[k].data_ptr() for k in self.GKEYS],
+                d["mask"].data_ptr(), self.gs.handle, _stream())
+            check("ax_poisson_create", rc)
+        self._h = h
+        self.shape = mask.shape
+
+    def rhs(self, f) -> "torch.Tensor":
+        """b = mask .* gs(B f) for a callable f(x, y, z) (evaluated on host)."""
+        import torch
+        x = self.xyz
+        fv = f(x[..., 0], x[..., 1], x[..., 2])
+        b = self.mass * torch.as_tensor(np.ascontiguousarray(fv), device=self.device)
+        self.gs.sum(b)
+        return b * self.d["mask"]
+
+    def apply(self, w, u) -> None:
+        check("ax_poisson_apply", lib().ax_poisson_apply(self._h, w.data_ptr(), u.data_ptr(),
+                                                         _stream()))
+
+    def jacobi(self):
+        import ctypes
+        import torch
+        p = ctypes.c_void_p()
+        check("ax_poisson_jacobi", lib().ax_poisson_jacobi(self._h, ctypes.addressof(p)))
+        n = int(np.prod(self.shape))
+        return torch.as_tensor(_DeviceArray(p.value, n, "<f8", self), device=self.device)
+
+    def set_check_every(self, k: int) -> None:
+        check("ax_poisson_set_check_every", lib().ax_poisson_set_check_every(self._h, k))
+
+    def cg(self, b, tol=1e-8, maxit=10000, raise_on_error=True):
+        """Jacobi-PCG in fp64; returns (x, iterations, relative residual, status)."""
+        import ctypes
+        import torch
+        x = torch.empty_like(b)
+        it, rel = ctypes.c_int(), ctypes.c_double()
+        rc = lib().ax_cg_solve(self._h, x.data_ptr(), b.data_ptr(), tol, maxit,
+                               ctypes.addressof(it), ctypes.addressof(rel), _stream())
+        if raise_on_error and rc not in (0, _lib.AX_ENOTCONV):
+            check("ax_cg_solve", rc)
+        return x, it.value, rel.value, rc
+
+    def mpcg(self, b, mode=_lib.AX_PREC_F32, tol=1e-8, inner_tol=1e-4, max_outer=50,
+             max_inner=10000, raise_on_error=True):
+        """fp64 iterative refinement around an fp32 (or bf16-data) inner PCG;
+        returns (x, outer iterations, inner iterations, relres, status)."""
+        import ctypes
+        import torch
+        x = torch.empty_like(b)
+        no, ni, rel = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        rc = lib().ax_mpcg_solve(self._h, mode, x.data_ptr(), b.data_ptr(), tol, inner_tol,
+                                 max_outer, max_inner, ctypes.addressof(no),
+                                 ctypes.addressof(ni), ctypes.addressof(rel), _stream())
+        if raise_on_error and rc not in (0, _lib.AX_ENOTCONV):
+            check("ax_mpcg_solve", rc)
+        return x, no.value, ni.value, rel.value, rc
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib._lib is not None:
+            _lib._lib.ax_poisson_destroy(h)
+            self._h = None
+
+
+# ---------------------------------------------------------------------------
+# batched multi-mesh launch and the elements-per-block autotuner
+# ---------------------------------------------------------------------------
+_FIELDS = ("w", "u", "dx", "dxt", "h1", "g11", "g22", "g33", "g12", "g13", "g23")
+
+
+class Batch:
+    """Many meshes (each a dict of CUDA tensors with keys w, u, dx, dxt, h1,
+    g11..g23 and an int "lx") in one persistent launch (ax_batch_*)."""
+
+    def __init__(self, meshes, dtype=_lib.AX_BATCH_F64, blocks_per_sm: int = 0):
+        import ctypes
+        import torch
+        want = torch.float64 if dtype == _lib.AX_BATCH_F64 else torch.float32
+        arr = (_lib.BatchMesh * max(1, len(meshes)))()
+        for q, m in enumerate(meshes):
+            lx = int(m["lx"])
+            for k in _FIELDS:
+                t = m[k]
+                if t.dtype != want or not t.is_cuda or not t.is_contiguous():
+                    raise TypeError(f"mesh {q}: {k} must be a contiguous CUDA {want} tensor")
+            nel = m["u"].numel() // lx ** 3
+            arr[q].lx, arr[q].nelv = lx, nel
+            for k in _FIELDS:
+                setattr(arr[q], k, m[k].data_ptr())
+        self._meshes = meshes  # keep the tensors alive
+        h = ctypes.c_void_p()
+        check("ax_batch_create", lib().ax_batch_create(ctypes.addressof(h), dtype, len(meshes),
+                                                       ctypes.addressof(arr), blocks_per_sm,
+                                                       _stream()))
+        self._h = h
+
+    def launch(self, graph: bool = False) -> None:
+        if graph:
+            check("ax_batch_graph_launch", lib().ax_batch_graph_launch(self._h, _stream()))
+        else:
+            check("ax_batch_launch", lib().ax_batch_launch(self._h, _stream()))
+
+    def info(self) -> dict:
+        import ctypes
+        a, b = ctypes.c_int(), ctypes.c_int()
+        s, f, y = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        check("ax_batch_info", lib().ax_batch_info(self._h, *[ctypes.addressof(x) for x in
+                                                              (a, b, s, f, y)]))
+        return {"items": a.value, "blocks": b.value, "smem": s.value, "flops": f.value,
+                "bytes": y.value}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib._lib is not None:
+            _lib._lib.ax_batch_destroy(h)
+            self._h = None
+
+
+def tune(dtype: int, lx: int, fields: dict, reps: int = 5):
+    """Times every elements-per-block choice for (dtype, lx) on the given
+    tensors (keys as in Batch; w is overwritten), records and returns
+    (best_epb, best_ms)."""
+    import ctypes
+    nel = fields["u"].numel() // lx ** 3
+    e, ms = ctypes.c_int(), ctypes.c_float()
+    rc = lib().ax_tune_run(dtype, lx, nel, *[fields[k].data_ptr() for k in _FIELDS], reps,
+                           ctypes.addressof(e), ctypes.addressof(ms), _stream())
+    check("ax_tune_run", rc)
+    return e.value, ms.value
+
+
+def tune_set(dtype: int, lx: int, epb: int) -> None:
+    check("ax_tune_set", lib().ax_tune_set(dtype, lx, epb))
+
+
+def tune_get(dtype: int, lx: int) -> int:
+    import ctypes
+    e = ctypes.c_int()
+    check("ax_tune_get", lib().ax_tune_get(dtype, lx, ctypes.addressof(e)))
+    return e.value

@@ -30,7 +30,36 @@ PROTOTYPES = {
     "ax_box_geometry": (c_int, [c_int, c_int, c_int, c_int, P] + [P] * 8),
     "ax_box_numbering": (c_int, [c_int, c_int, c_int, c_int, P]),
     "ax_df64_roundtrip": (c_int, [P, P, P, P, c_int64]),
+    "ax_gs_setup": (c_int, [P, P, c_int64, c_void_p]),
+    "ax_gs_sum": (c_int, [c_void_p, P, c_void_p]),
+    "ax_gs_sum_f32": (c_int, [c_void_p, P, c_void_p]),
+    "ax_gs_info": (c_int, [c_void_p, P, P, P]),
+    "ax_gs_inverse_multiplicity": (c_void_p, [c_void_p]),
+    "ax_gs_free": (c_int, [c_void_p]),
+    "ax_poisson_create": (c_int, [P, c_int, c_int] + [P] * 10 + [c_void_p, c_void_p]),
+    "ax_poisson_destroy": (c_int, [c_void_p]),
+    "ax_poisson_apply": (c_int, [c_void_p, P, P, c_void_p]),
+    "ax_poisson_jacobi": (c_int, [c_void_p, P]),
+    "ax_poisson_set_check_every": (c_int, [c_void_p, c_int]),
+    "ax_cg_solve": (c_int, [c_void_p, P, P, c_double, c_int, P, P, c_void_p]),
+    "ax_mpcg_solve": (c_int, [c_void_p, c_int, P, P, c_double, c_double, c_int, c_int, P, P, P,
+                              c_void_p]),
+    "ax_batch_create": (c_int, [P, c_int, c_int, P, c_int, c_void_p]),
+    "ax_batch_launch": (c_int, [c_void_p, c_void_p]),
+    "ax_batch_graph_launch": (c_int, [c_void_p, c_void_p]),
+    "ax_batch_info": (c_int, [c_void_p, P, P, P, P, P]),
+    "ax_batch_destroy": (c_int, [c_void_p]),
+    "ax_tune_run": (c_int, [c_int, c_int, c_int] + [P] * 11 + [c_int, P, P, c_void_p]),
+    "ax_tune_set": (c_int, [c_int, c_int, c_int]),
+    "ax_tune_get": (c_int, [c_int, c_int, P]),
 }
+
+
+class BatchMesh(ctypes.Structure):
+    """Mirror of ax_batch_mesh."""
+    _fields_ = [("lx", c_int), ("nelv", c_int)] + [
+        (n, c_void_p) for n in ("w", "u", "dx", "dxt", "h1", "g11", "g22", "g33", "g12", "g13",
+                                "g23")]
 
 AX_OK = 0
 AX_EINVAL = -1
@@ -41,6 +70,10 @@ AX_EBREAKDOWN = -6
 AX_VARIANT_AUTO = 0
 AX_VARIANT_F64_NATIVE = 1
 AX_VARIANT_F64_DF = 2
+AX_PREC_F32 = 1
+AX_PREC_BF16 = 2
+AX_BATCH_F64 = 1
+AX_BATCH_F32 = 2
 
 _lib = None
 _lock = threading.Lock()

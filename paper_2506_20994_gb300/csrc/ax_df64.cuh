@@ -9,6 +9,11 @@
 // rate, so the fp64 operator on fp64 units is bound by fp64 throughput far
 // below the HBM roofline; fp32 pairs trade each fp64 FMA for about a dozen
 // fp32 operations, which the fp32 pipe issues much faster.
+//
+// The body is a device function over `nel` (<= epb) consecutive elements
+// starting at element e0 of one mesh, so the per-mesh kernel and the
+// persistent multi-mesh kernel (batch.cu) share it.  Threads at or above
+// epb*lx*lx only take part in the block barriers.
 #pragma once
 
 #include "common.cuh"
@@ -17,21 +22,30 @@
 namespace ax {
 
 template <int LX>
-__global__ void __launch_bounds__(256)
-ax_df64_kernel(double *__restrict__ w, const double *__restrict__ u,
-               const double *__restrict__ dx, const double *__restrict__ dxt,
-               const double *__restrict__ h1, const double *__restrict__ g11,
-               const double *__restrict__ g22, const double *__restrict__ g33,
-               const double *__restrict__ g12, const double *__restrict__ g13,
-               const double *__restrict__ g23, int nelv, int epb) {
+constexpr size_t df64_smem(int epb) {
+  return (2 * (size_t)LX * LX + (size_t)epb * 3 * LX * LX * LX) * sizeof(df::df2);
+}
+
+template <int LX>
+__device__ __forceinline__ void df64_body(double *__restrict__ w, const double *__restrict__ u,
+                                          const double *__restrict__ dx,
+                                          const double *__restrict__ dxt,
+                                          const double *__restrict__ h1,
+                                          const double *__restrict__ g11,
+                                          const double *__restrict__ g22,
+                                          const double *__restrict__ g33,
+                                          const double *__restrict__ g12,
+                                          const double *__restrict__ g13,
+                                          const double *__restrict__ g23, long long e0, int nel,
+                                          int epb, unsigned char *smem_raw) {
   using namespace df;
   constexpr int N2 = LX * LX;
   constexpr int N3 = LX * N2;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   df2 *sdx = reinterpret_cast<df2 *>(smem_raw);
   df2 *sdxt = sdx + N2;
-  const int le = threadIdx.x / N2;
-  const int p = threadIdx.x - le * N2;
+  const bool own = (int)threadIdx.x < epb * N2;
+  const int le = own ? (int)threadIdx.x / N2 : 0;
+  const int p = (int)threadIdx.x - le * N2;
   const int i = p % LX;
   const int j = p / LX;
   df2 *su = sdxt + N2 + (size_t)le * 3 * N3;
@@ -42,79 +56,94 @@ ax_df64_kernel(double *__restrict__ w, const double *__restrict__ u,
     sdx[t] = split(__ldg(dx + t));
     sdxt[t] = split(__ldg(dxt + t));
   }
-  const long long e = (long long)blockIdx.x * epb + le;
-  const bool active = e < nelv;
-  const size_t base = (size_t)(active ? e : 0) * N3 + p;
+  const bool active = own && le < nel;
+  const size_t base = (size_t)(active ? e0 + le : 0) * N3 + p;
 
   df2 uk[LX];
+  if (own) {
 #pragma unroll
-  for (int k = 0; k < LX; ++k) {
-    uk[k] = active ? split(__ldg(u + base + (size_t)k * N2)) : df2{0.f, 0.f};
-    su[k * N2 + p] = uk[k];
+    for (int k = 0; k < LX; ++k) {
+      uk[k] = active ? split(__ldg(u + base + (size_t)k * N2)) : df2{0.f, 0.f};
+      su[k * N2 + p] = uk[k];
+    }
   }
   __syncthreads();
 
   acc wacc[LX];
+  if (own) {
 #pragma unroll
-  for (int k = 0; k < LX; ++k) {
-    acc ar = prod(sdx[i], su[k * N2 + j * LX]);
-    acc as = prod(sdx[j], su[k * N2 + i]);
-    acc at = prod(sdx[k], uk[0]);
+    for (int k = 0; k < LX; ++k) {
+      acc ar = prod(sdx[i], su[k * N2 + j * LX]);
+      acc as = prod(sdx[j], su[k * N2 + i]);
+      acc at = prod(sdx[k], uk[0]);
 #pragma unroll
-    for (int l = 1; l < LX; ++l) {
-      mac(ar, sdx[l * LX + i], su[k * N2 + j * LX + l]);
-      mac(as, sdx[l * LX + j], su[k * N2 + l * LX + i]);
-      mac(at, sdx[l * LX + k], uk[l]);
-    }
-    const df2 ur = result(ar), us = result(as), ut = result(at);
-    df2 wr{0.f, 0.f}, ws{0.f, 0.f}, wt{0.f, 0.f};
-    if (active) {
-      const size_t q = base + (size_t)k * N2;
-      const df2 a11 = split(__ldg(g11 + q)), a22 = split(__ldg(g22 + q));
-      const df2 a33 = split(__ldg(g33 + q)), a12 = split(__ldg(g12 + q));
-      const df2 a13 = split(__ldg(g13 + q)), a23 = split(__ldg(g23 + q));
-      const df2 hh = split(__ldg(h1 + q));
-      acc a = prod(a11, ur);
-      mac(a, a12, us);
-      mac(a, a13, ut);
-      wr = mul2(hh, result(a));
-      a = prod(a12, ur);
-      mac(a, a22, us);
-      mac(a, a23, ut);
-      ws = mul2(hh, result(a));
-      a = prod(a13, ur);
-      mac(a, a23, us);
-      mac(a, a33, ut);
-      wt = mul2(hh, result(a));
-    }
-    swr[k * N2 + p] = wr;
-    sws[k * N2 + p] = ws;
+      for (int l = 1; l < LX; ++l) {
+        mac(ar, sdx[l * LX + i], su[k * N2 + j * LX + l]);
+        mac(as, sdx[l * LX + j], su[k * N2 + l * LX + i]);
+        mac(at, sdx[l * LX + k], uk[l]);
+      }
+      const df2 ur = result(ar), us = result(as), ut = result(at);
+      df2 wr{0.f, 0.f}, ws{0.f, 0.f}, wt{0.f, 0.f};
+      if (active) {
+        const size_t q = base + (size_t)k * N2;
+        const df2 a11 = split(__ldg(g11 + q)), a22 = split(__ldg(g22 + q));
+        const df2 a33 = split(__ldg(g33 + q)), a12 = split(__ldg(g12 + q));
+        const df2 a13 = split(__ldg(g13 + q)), a23 = split(__ldg(g23 + q));
+        const df2 hh = split(__ldg(h1 + q));
+        acc a = prod(a11, ur);
+        mac(a, a12, us);
+        mac(a, a13, ut);
+        wr = mul2(hh, result(a));
+        a = prod(a12, ur);
+        mac(a, a22, us);
+        mac(a, a23, ut);
+        ws = mul2(hh, result(a));
+        a = prod(a13, ur);
+        mac(a, a23, us);
+        mac(a, a33, ut);
+        wt = mul2(hh, result(a));
+      }
+      swr[k * N2 + p] = wr;
+      sws[k * N2 + p] = ws;
 #pragma unroll
-    for (int kk = 0; kk < LX; ++kk) {
-      if (k == 0)
-        wacc[kk] = prod(sdxt[kk], wt);
-      else
-        mac(wacc[kk], sdxt[k * LX + kk], wt);
+      for (int kk = 0; kk < LX; ++kk) {
+        if (k == 0)
+          wacc[kk] = prod(sdxt[kk], wt);
+        else
+          mac(wacc[kk], sdxt[k * LX + kk], wt);
+      }
     }
   }
   __syncthreads();
 
+  if (own) {
 #pragma unroll
-  for (int k = 0; k < LX; ++k) {
-    acc a = wacc[k];
+    for (int k = 0; k < LX; ++k) {
+      acc a = wacc[k];
 #pragma unroll
-    for (int l = 0; l < LX; ++l) {
-      mac(a, sdxt[l * LX + i], swr[k * N2 + j * LX + l]);
-      mac(a, sdxt[l * LX + j], sws[k * N2 + l * LX + i]);
+      for (int l = 0; l < LX; ++l) {
+        mac(a, sdxt[l * LX + i], swr[k * N2 + j * LX + l]);
+        mac(a, sdxt[l * LX + j], sws[k * N2 + l * LX + i]);
+      }
+      const df2 r = result(a);
+      if (active) w[base + (size_t)k * N2] = join(r.hi, r.lo);
     }
-    const df2 r = result(a);
-    if (active) w[base + (size_t)k * N2] = join(r.hi, r.lo);
   }
 }
 
 template <int LX>
-constexpr size_t df64_smem(int epb) {
-  return (2 * (size_t)LX * LX + (size_t)epb * 3 * LX * LX * LX) * sizeof(df::df2);
+__global__ void __launch_bounds__(256)
+ax_df64_kernel(double *__restrict__ w, const double *__restrict__ u,
+               const double *__restrict__ dx, const double *__restrict__ dxt,
+               const double *__restrict__ h1, const double *__restrict__ g11,
+               const double *__restrict__ g22, const double *__restrict__ g33,
+               const double *__restrict__ g12, const double *__restrict__ g13,
+               const double *__restrict__ g23, int nelv, int epb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long e0 = (long long)blockIdx.x * epb;
+  const long long left = nelv - e0;
+  const int nel = left < epb ? (int)left : epb;
+  df64_body<LX>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, e0, nel, epb, smem_raw);
 }
 
 template <int LX>

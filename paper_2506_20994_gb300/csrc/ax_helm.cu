@@ -48,6 +48,7 @@ int ax_helm_variant(int variant, double *w, const double *u, const double *dx,
       return ax::dispatch_kstep_f64(lx, w, u, dx, dxt, h1, g11, g22, g33, g12,
                                                     g13, g23, nelv, elems_per_block, st);
     case AX_VARIANT_F64_DF:
+      if (elems_per_block <= 0) elems_per_block = ax::tuned_epb(AX_BATCH_F64, lx);
       return ax::dispatch_df64(lx, w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nelv,
                            elems_per_block, st);
     default:
@@ -68,7 +69,8 @@ int ax_helm_f32(float *w, const float *u, const float *dx, const float *dxt, con
   int rc = check_args(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx, nelv);
   if (rc != AX_OK) return rc > 0 ? AX_OK : rc;
   return ax::dispatch_kstep_f32(lx, w, u, dx, dxt, h1, g11, g22, g33, g12, g13,
-                                             g23, nelv, 0, (cudaStream_t)stream);
+                                             g23, nelv, ax::tuned_epb(AX_BATCH_F32, lx),
+                                             (cudaStream_t)stream);
 }
 
 int ax_helm_bf16(float *w, const ax_bf16 *u, const float *dx, const float *dxt,

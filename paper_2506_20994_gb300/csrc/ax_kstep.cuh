@@ -15,7 +15,8 @@
 //     the k-loop; the r- and s-parts read the weighted gradient back from
 //     shared memory after one block barrier.
 // Algorithmic traffic per element: u, h1, six G factors read and w written
-// once (9 * lx^3 values).
+// once (9 * lx^3 values).  The body works on `nel` (<= epb) consecutive
+// elements from e0, so the persistent multi-mesh kernel (batch.cu) reuses it.
 #pragma once
 
 #include "common.cuh"
@@ -25,20 +26,21 @@ namespace ax {
 AX_D double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
 AX_D float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
-template <int LX, typename S, typename T, typename W>
-__global__ void __launch_bounds__(1024)
-ax_kstep_kernel(W *__restrict__ w, const S *__restrict__ u, const T *__restrict__ dx,
-                const T *__restrict__ dxt, const S *__restrict__ h1,
-                const S *__restrict__ g11, const S *__restrict__ g22,
-                const S *__restrict__ g33, const S *__restrict__ g12,
-                const S *__restrict__ g13, const S *__restrict__ g23, int nelv, int epb) {
+template <int LX, typename SU, typename S, typename T, typename W>
+__device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restrict__ u,
+                                           const T *__restrict__ dx, const T *__restrict__ dxt,
+                                           const S *__restrict__ h1, const S *__restrict__ g11,
+                                           const S *__restrict__ g22, const S *__restrict__ g33,
+                                           const S *__restrict__ g12, const S *__restrict__ g13,
+                                           const S *__restrict__ g23, long long e0, int nel,
+                                           int epb, unsigned char *smem_raw) {
   constexpr int N2 = LX * LX;
   constexpr int N3 = LX * N2;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sdx = reinterpret_cast<T *>(smem_raw);
   T *sdxt = sdx + N2;
-  const int le = threadIdx.x / N2;
-  const int p = threadIdx.x - le * N2;
+  const bool own = (int)threadIdx.x < epb * N2;
+  const int le = own ? (int)threadIdx.x / N2 : 0;
+  const int p = (int)threadIdx.x - le * N2;
   const int i = p % LX;
   const int j = p / LX;
   T *su = sdxt + N2 + (size_t)le * 3 * N3;
@@ -49,58 +51,77 @@ ax_kstep_kernel(W *__restrict__ w, const S *__restrict__ u, const T *__restrict_
     sdx[t] = dx[t];
     sdxt[t] = dxt[t];
   }
-  const long long e = (long long)blockIdx.x * epb + le;
-  const bool active = e < nelv;
-  const size_t base = (size_t)(active ? e : 0) * N3 + p;
+  const bool active = own && le < nel;
+  const size_t base = (size_t)(active ? e0 + le : 0) * N3 + p;
 
   T uk[LX];
+  if (own) {
 #pragma unroll
-  for (int k = 0; k < LX; ++k) {
-    uk[k] = active ? ld_cvt<T>(u + base + (size_t)k * N2) : T(0);
-    su[k * N2 + p] = uk[k];
+    for (int k = 0; k < LX; ++k) {
+      uk[k] = active ? ld_cvt<T>(u + base + (size_t)k * N2) : T(0);
+      su[k * N2 + p] = uk[k];
+    }
   }
   __syncthreads();
 
   T wacc[LX];
+  if (own) {
 #pragma unroll
-  for (int k = 0; k < LX; ++k) wacc[k] = T(0);
-
+    for (int k = 0; k < LX; ++k) wacc[k] = T(0);
 #pragma unroll
-  for (int k = 0; k < LX; ++k) {
-    T ur = T(0), us = T(0), ut = T(0);
+    for (int k = 0; k < LX; ++k) {
+      T ur = T(0), us = T(0), ut = T(0);
 #pragma unroll
-    for (int l = 0; l < LX; ++l) {
-      ur = fma_t(sdx[l * LX + i], su[k * N2 + j * LX + l], ur);
-      us = fma_t(sdx[l * LX + j], su[k * N2 + l * LX + i], us);
-      ut = fma_t(sdx[l * LX + k], uk[l], ut);
+      for (int l = 0; l < LX; ++l) {
+        ur = fma_t(sdx[l * LX + i], su[k * N2 + j * LX + l], ur);
+        us = fma_t(sdx[l * LX + j], su[k * N2 + l * LX + i], us);
+        ut = fma_t(sdx[l * LX + k], uk[l], ut);
+      }
+      T wr = T(0), ws = T(0), wt = T(0);
+      if (active) {
+        const size_t q = base + (size_t)k * N2;
+        const T a11 = ld_cvt<T>(g11 + q), a22 = ld_cvt<T>(g22 + q), a33 = ld_cvt<T>(g33 + q);
+        const T a12 = ld_cvt<T>(g12 + q), a13 = ld_cvt<T>(g13 + q), a23 = ld_cvt<T>(g23 + q);
+        const T hh = ld_cvt<T>(h1 + q);
+        wr = hh * (a11 * ur + a12 * us + a13 * ut);
+        ws = hh * (a12 * ur + a22 * us + a23 * ut);
+        wt = hh * (a13 * ur + a23 * us + a33 * ut);
+      }
+      swr[k * N2 + p] = wr;
+      sws[k * N2 + p] = ws;
+#pragma unroll
+      for (int kk = 0; kk < LX; ++kk) wacc[kk] = fma_t(sdxt[k * LX + kk], wt, wacc[kk]);
     }
-    T wr = T(0), ws = T(0), wt = T(0);
-    if (active) {
-      const size_t q = base + (size_t)k * N2;
-      const T a11 = ld_cvt<T>(g11 + q), a22 = ld_cvt<T>(g22 + q), a33 = ld_cvt<T>(g33 + q);
-      const T a12 = ld_cvt<T>(g12 + q), a13 = ld_cvt<T>(g13 + q), a23 = ld_cvt<T>(g23 + q);
-      const T hh = ld_cvt<T>(h1 + q);
-      wr = hh * (a11 * ur + a12 * us + a13 * ut);
-      ws = hh * (a12 * ur + a22 * us + a23 * ut);
-      wt = hh * (a13 * ur + a23 * us + a33 * ut);
-    }
-    swr[k * N2 + p] = wr;
-    sws[k * N2 + p] = ws;
-#pragma unroll
-    for (int kk = 0; kk < LX; ++kk) wacc[kk] = fma_t(sdxt[k * LX + kk], wt, wacc[kk]);
   }
   __syncthreads();
 
+  if (own) {
 #pragma unroll
-  for (int k = 0; k < LX; ++k) {
-    T acc = wacc[k];
+    for (int k = 0; k < LX; ++k) {
+      T acc = wacc[k];
 #pragma unroll
-    for (int l = 0; l < LX; ++l) {
-      acc = fma_t(sdxt[l * LX + i], swr[k * N2 + j * LX + l], acc);
-      acc = fma_t(sdxt[l * LX + j], sws[k * N2 + l * LX + i], acc);
+      for (int l = 0; l < LX; ++l) {
+        acc = fma_t(sdxt[l * LX + i], swr[k * N2 + j * LX + l], acc);
+        acc = fma_t(sdxt[l * LX + j], sws[k * N2 + l * LX + i], acc);
+      }
+      if (active) w[base + (size_t)k * N2] = (W)acc;
     }
-    if (active) w[base + (size_t)k * N2] = (W)acc;
   }
+}
+
+template <int LX, typename SU, typename S, typename T, typename W>
+__global__ void __launch_bounds__(1024)
+ax_kstep_kernel(W *__restrict__ w, const SU *__restrict__ u, const T *__restrict__ dx,
+                const T *__restrict__ dxt, const S *__restrict__ h1,
+                const S *__restrict__ g11, const S *__restrict__ g22,
+                const S *__restrict__ g33, const S *__restrict__ g12,
+                const S *__restrict__ g13, const S *__restrict__ g23, int nelv, int epb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long e0 = (long long)blockIdx.x * epb;
+  const long long left = nelv - e0;
+  const int nel = left < epb ? (int)left : epb;
+  kstep_body<LX, SU, S, T, W>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, e0, nel, epb,
+                              smem_raw);
 }
 
 // Shared-memory bytes of one block of the k-loop kernel.
@@ -115,14 +136,14 @@ inline int kstep_default_epb(int lx) {
   return e < 1 ? 1 : e;
 }
 
-template <int LX, typename S, typename T, typename W>
-int launch_kstep(W *w, const S *u, const T *dx, const T *dxt, const S *h1, const S *g11,
+template <int LX, typename SU, typename S, typename T, typename W>
+int launch_kstep(W *w, const SU *u, const T *dx, const T *dxt, const S *h1, const S *g11,
                  const S *g22, const S *g33, const S *g12, const S *g13, const S *g23,
                  int nelv, int epb, cudaStream_t stream) {
   if (epb <= 0) epb = kstep_default_epb(LX);
   if (epb * LX * LX > 1024) return AX_EINVAL;
   const size_t smem = kstep_smem<LX, T>(epb);
-  auto kern = ax_kstep_kernel<LX, S, T, W>;
+  auto kern = ax_kstep_kernel<LX, SU, S, T, W>;
   static size_t granted = 48 * 1024;  // per instantiation
   if (smem > granted) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=

@@ -12,7 +12,7 @@ int dispatch_kstep_bf16(int lx, float *w, const __nv_bfloat16 *u, const float *d
   switch (lx) {
 #define AX_CASE(L)                                                                             \
   case L:                                                                                      \
-    return launch_kstep<L, __nv_bfloat16, float, float>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, \
+    return launch_kstep<L, __nv_bfloat16, __nv_bfloat16, float, float>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, \
                                              nelv, epb, st);
     AX_LX_CASES(AX_CASE)
 #undef AX_CASE

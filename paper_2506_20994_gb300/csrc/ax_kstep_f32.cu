@@ -12,7 +12,7 @@ int dispatch_kstep_f32(int lx, float *w, const float *u, const float *dx,
   switch (lx) {
 #define AX_CASE(L)                                                                             \
   case L:                                                                                      \
-    return launch_kstep<L, float, float, float>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, \
+    return launch_kstep<L, float, float, float, float>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, \
                                              nelv, epb, st);
     AX_LX_CASES(AX_CASE)
 #undef AX_CASE

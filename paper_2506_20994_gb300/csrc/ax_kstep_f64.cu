@@ -12,7 +12,7 @@ int dispatch_kstep_f64(int lx, double *w, const double *u, const double *dx,
   switch (lx) {
 #define AX_CASE(L)                                                                             \
   case L:                                                                                      \
-    return launch_kstep<L, double, double, double>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, \
+    return launch_kstep<L, double, double, double, double>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, \
                                              nelv, epb, st);
     AX_LX_CASES(AX_CASE)
 #undef AX_CASE

@@ -1,0 +1,564 @@
+// Poisson solve built on the element operator: the assembled, masked
+// operator A p = mask .* gs(Ax(p)) (the matrix-free evaluation of the weak
+// Poisson form of Sec. "The Spectral Element Method", assembled by the
+// gather-scatter of Sec. "Neko and Small Tensor Kernel"), the exact Jacobi
+// diagonal, Jacobi-preconditioned conjugate gradients in fp64, and an
+// iterative-refinement solve whose inner CG runs in fp32 (fp32 or bf16
+// operator data) while the outer residual, inner products and updates stay
+// fp64.  The paper prints no solver; the method is textbook PCG (Hestenes &
+// Stiefel 1952) and mixed-precision iterative refinement (Wilkinson 1963;
+// Carson & Higham 2018).
+//
+// Vectors are local (E * lx^3, element-major, continuous across shared
+// nodes).  Inner products run over unique global nodes, i.e. the local sum
+// weighted by 1/multiplicity.  The scalars of the iteration live on the
+// device; the host reads the residual norm every `check_every` iterations.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "dispatch.h"
+#include "reduce.cuh"
+
+struct ax_gs;
+extern "C" int ax_gs_sum(ax_gs *g, double *v, void *stream);
+extern "C" int ax_gs_sum_f32(ax_gs *g, float *v, void *stream);
+extern "C" const double *ax_gs_inverse_multiplicity(const ax_gs *g);
+
+namespace {
+
+using ax::kRedBlocks;
+using ax::kRedThreads;
+
+// Device-side scalars of one CG run.
+struct CgScalars {
+  double rz, rz_new, rr, rr0, pap, alpha, beta;
+  int status;  // 0 ok, 1 breakdown (p.Ap <= 0 or non-finite)
+};
+
+// ---------------------------------------------------------------- kernels
+__global__ void jacobi_diag_kernel(double *__restrict__ diag, const double *__restrict__ dx,
+                                   const double *__restrict__ h1, const double *__restrict__ g11,
+                                   const double *__restrict__ g22, const double *__restrict__ g33,
+                                   const double *__restrict__ g12, const double *__restrict__ g13,
+                                   const double *__restrict__ g23, int lx, int64_t n) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int n2 = lx * lx, n3 = n2 * lx;
+  const int64_t e = q / n3;
+  const int p = (int)(q - e * n3);
+  const int k = p / n2, j = (p / lx) % lx, i = p % lx;
+  const int64_t b = e * n3;
+  // D_{ab} = dx[b*lx + a]
+  double s = 0.0;
+  for (int l = 0; l < lx; ++l) {
+    const double dli = dx[i * lx + l], dlj = dx[j * lx + l], dlk = dx[k * lx + l];
+    const int64_t qi = b + (k * lx + j) * lx + l, qj = b + (k * lx + l) * lx + i,
+                  qk = b + (l * lx + j) * lx + i;
+    s += dli * dli * h1[qi] * g11[qi] + dlj * dlj * h1[qj] * g22[qj] +
+         dlk * dlk * h1[qk] * g33[qk];
+  }
+  const double di = dx[i * lx + i], dj = dx[j * lx + j], dk = dx[k * lx + k];
+  s += 2.0 * h1[q] * (di * dj * g12[q] + di * dk * g13[q] + dj * dk * g23[q]);
+  diag[q] = s;
+}
+
+// minv = mask / diag (0 where masked); cm = c * minv; also fp32 copies.
+__global__ void precond_kernel(double *__restrict__ minv, double *__restrict__ cm,
+                               const double *__restrict__ diag, const double *__restrict__ mask,
+                               const double *__restrict__ c, int64_t n) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const double m = (mask[q] != 0.0 && diag[q] != 0.0) ? 1.0 / diag[q] : 0.0;
+  minv[q] = m;
+  cm[q] = c[q] * m;
+}
+
+// r = b (masked), p = minv r; partials: rz = sum cm r^2, rr = sum c r^2
+template <typename T>
+__global__ void cg_init_kernel(T *__restrict__ x, T *__restrict__ r, T *__restrict__ p,
+                               const T *__restrict__ b, const T *__restrict__ mask,
+                               const T *__restrict__ minv, const T *__restrict__ c,
+                               double *__restrict__ partials, int64_t n) {
+  __shared__ double sh[2 * kRedThreads / 32];
+  T a_rz = 0, a_rr = 0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const T rv = b[q] * mask[q];
+    x[q] = T(0);
+    r[q] = rv;
+    const T z = minv[q] * rv;
+    p[q] = z;
+    const T cq = c[q];
+    a_rz += cq * rv * z;
+    a_rr += cq * rv * rv;
+  }
+  double v[2] = {(double)a_rz, (double)a_rr};
+  ax::block_sum<2>(v, sh);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = v[0];
+    partials[gridDim.x + blockIdx.x] = v[1];
+  }
+}
+
+// w = mask .* w; partial sum of c p w
+template <typename T>
+__global__ void mask_dot_kernel(T *__restrict__ w, const T *__restrict__ p,
+                                const T *__restrict__ mask, const T *__restrict__ c,
+                                double *__restrict__ partials, int64_t n) {
+  __shared__ double sh[kRedThreads / 32];
+  T a = 0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const T wv = w[q] * mask[q];
+    w[q] = wv;
+    a += c[q] * p[q] * wv;
+  }
+  double v[1] = {(double)a};
+  ax::block_sum<1>(v, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+}
+
+__global__ void cg_alpha_kernel(const double *__restrict__ partials, int nblk,
+                                CgScalars *__restrict__ s) {
+  __shared__ double t[1];
+  ax::warp_sum_partials<1>(partials, nblk, t);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double pap = t[0];
+    s->pap = pap;
+    if (!(pap > 0.0) || !isfinite(pap) || !isfinite(s->rz)) {
+      s->status = 1;
+      s->alpha = 0.0;
+    } else {
+      s->alpha = s->rz / pap;
+    }
+  }
+}
+
+// x += alpha p; r -= alpha w; partials rz' = sum cm r^2, rr' = sum c r^2
+template <typename T>
+__global__ void cg_update_kernel(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
+                                 const T *__restrict__ w, const T *__restrict__ cm,
+                                 const T *__restrict__ c, const CgScalars *__restrict__ s,
+                                 double *__restrict__ partials, int64_t n) {
+  __shared__ double sh[2 * kRedThreads / 32];
+  const T alpha = (T)s->alpha;
+  T a_rz = 0, a_rr = 0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    x[q] += alpha * p[q];
+    const T rv = r[q] - alpha * w[q];
+    r[q] = rv;
+    const T r2 = rv * rv;
+    a_rz += cm[q] * r2;
+    a_rr += c[q] * r2;
+  }
+  double v[2] = {(double)a_rz, (double)a_rr};
+  ax::block_sum<2>(v, sh);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = v[0];
+    partials[gridDim.x + blockIdx.x] = v[1];
+  }
+}
+
+// first=1: rz = partial sums, rr0 = rr.  Otherwise beta = rz'/rz.
+__global__ void cg_beta_kernel(const double *__restrict__ partials, int nblk,
+                               CgScalars *__restrict__ s, int first) {
+  __shared__ double t[2];
+  ax::warp_sum_partials<2>(partials, nblk, t);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (first) {
+      s->rz = t[0];
+      s->rr = t[1];
+      s->rr0 = t[1];
+      s->beta = 0.0;
+      s->status = 0;
+    } else {
+      s->beta = (s->rz != 0.0) ? t[0] / s->rz : 0.0;
+      s->rz = t[0];
+      s->rr = t[1];
+      if (!isfinite(t[0]) || !isfinite(t[1])) s->status = 1;
+    }
+  }
+}
+
+// p = minv r + beta p
+template <typename T>
+__global__ void cg_p_kernel(T *__restrict__ p, const T *__restrict__ r,
+                            const T *__restrict__ minv, const CgScalars *__restrict__ s,
+                            int64_t n) {
+  const T beta = (T)s->beta;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    p[q] = minv[q] * r[q] + beta * p[q];
+}
+
+// fp64 -> fp32 / bf16 conversions and the fp64 refinement updates
+__global__ void to_f32_kernel(float *__restrict__ out, const double *__restrict__ in, int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    out[q] = (float)in[q];
+}
+__global__ void to_bf16_kernel(__nv_bfloat16 *__restrict__ out, const double *__restrict__ in,
+                               int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    out[q] = __double2bfloat16(in[q]);
+}
+// r = mask .* (b - w) (fp64), r32 = fp32(r) scaled by 1/s; partial rr = sum c r^2
+__global__ void residual_kernel(double *__restrict__ r, float *__restrict__ r32,
+                                const double *__restrict__ b, const double *__restrict__ w,
+                                const double *__restrict__ mask, const double *__restrict__ c,
+                                double *__restrict__ partials, int64_t n) {
+  __shared__ double sh[kRedThreads / 32];
+  double a = 0.0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const double rv = (b[q] - w[q]) * mask[q];
+    r[q] = rv;
+    r32[q] = (float)rv;
+    a += c[q] * rv * rv;
+  }
+  double v[1] = {a};
+  ax::block_sum<1>(v, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+}
+__global__ void sum_partials_kernel(const double *__restrict__ partials, int nblk,
+                                    double *__restrict__ out) {
+  ax::warp_sum_partials<1>(partials, nblk, out);
+}
+// x += d (fp32 correction added in fp64)
+__global__ void add_correction_kernel(double *__restrict__ x, const float *__restrict__ d,
+                                      int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    x[q] += (double)d[q];
+}
+
+inline unsigned blocks_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- handle
+struct ax_poisson {
+  int lx = 0, nelv = 0;
+  int64_t n = 0;
+  const double *dx = nullptr, *dxt = nullptr, *h1 = nullptr, *g[6] = {};
+  const double *mask = nullptr;
+  ax_gs *gs = nullptr;
+  const double *c = nullptr;  // 1/multiplicity (owned by gs)
+  // owned fp64 work
+  double *minv = nullptr, *cm = nullptr, *w = nullptr, *r = nullptr, *p = nullptr;
+  double *partials = nullptr;
+  CgScalars *scal = nullptr;
+  CgScalars *scal_host = nullptr;  // pinned
+  // owned fp32 data of the refinement solve (lazily allocated)
+  int lowp_mode = 0;  // 0 none, 1 fp32, 2 bf16 operator data
+  float *minv32 = nullptr, *mask32 = nullptr, *x32 = nullptr, *r32 = nullptr, *p32 = nullptr,
+        *w32 = nullptr, *q32 = nullptr, *c32 = nullptr, *cm32 = nullptr, *dx32 = nullptr,
+        *dxt32 = nullptr;
+  void *h1lp = nullptr, *glp[6] = {};
+  double *r64 = nullptr;  // outer residual
+  int check_every = 1;
+};
+
+namespace {
+
+template <typename T>
+int alloc(T **p, size_t count) {
+  if (cudaMalloc((void **)p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    *p = nullptr;
+    return AX_ENOMEM;
+  }
+  return AX_OK;
+}
+
+int apply_f64(ax_poisson *P, double *w, const double *u, cudaStream_t st) {
+  int rc = ax::dispatch_df64(P->lx, w, u, P->dx, P->dxt, P->h1, P->g[0], P->g[1], P->g[2],
+                             P->g[3], P->g[4], P->g[5], P->nelv, 0, st);
+  if (P->lx > ax::AX_DF64_LX_MAX)
+    rc = ax::dispatch_kstep_f64(P->lx, w, u, P->dx, P->dxt, P->h1, P->g[0], P->g[1], P->g[2],
+                                P->g[3], P->g[4], P->g[5], P->nelv, 0, st);
+  if (rc) return rc;
+  return ax_gs_sum(P->gs, w, st);
+}
+
+int apply_lowp(ax_poisson *P, float *w, const float *u, cudaStream_t st) {
+  int rc;
+  if (P->lowp_mode == 2) {
+    auto b = [](const void *x) { return reinterpret_cast<const __nv_bfloat16 *>(x); };
+    // u is fp32: the bf16 mode keeps vectors in fp32 and only G, h1 in bf16
+    rc = ax::dispatch_kstep_f32u_bf16(P->lx, w, u, P->dx32, P->dxt32, b(P->h1lp), b(P->glp[0]),
+                                      b(P->glp[1]), b(P->glp[2]), b(P->glp[3]), b(P->glp[4]),
+                                      b(P->glp[5]), P->nelv, 0, st);
+  } else {
+    auto f = [](const void *x) { return reinterpret_cast<const float *>(x); };
+    rc = ax::dispatch_kstep_f32(P->lx, w, u, P->dx32, P->dxt32, f(P->h1lp), f(P->glp[0]),
+                                f(P->glp[1]), f(P->glp[2]), f(P->glp[3]), f(P->glp[4]),
+                                f(P->glp[5]), P->nelv, 0, st);
+  }
+  if (rc) return rc;
+  return ax_gs_sum_f32(P->gs, w, st);
+}
+
+// Generic PCG loop on vectors of type T (fp64 with the fp64 operator, or
+// fp32 with the low-precision operator).  x0 = 0.  Returns AX_OK when
+// sqrt(rr/rr0) <= tol, AX_ENOTCONV at maxit, AX_EBREAKDOWN on breakdown.
+template <typename T, typename Apply>
+int pcg_loop(ax_poisson *P, T *x, const T *b, T *r, T *p, T *w, const T *mask, const T *minv,
+             const T *c, const T *cm, Apply apply, double tol, int maxit, int *iters,
+             double *relres, cudaStream_t st) {
+  const int64_t n = P->n;
+  const unsigned nb = kRedBlocks;
+  cg_init_kernel<T><<<nb, kRedThreads, 0, st>>>(x, r, p, b, mask, minv, c, P->partials, n);
+  cg_beta_kernel<<<1, 64, 0, st>>>(P->partials, nb, P->scal, 1);
+  if (ax::launch_status()) return AX_ELAUNCH;
+  if (cudaMemcpyAsync(P->scal_host, P->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return AX_ELAUNCH;
+  const double rr0 = P->scal_host->rr0;
+  int it = 0;
+  double rel = rr0 > 0 ? 1.0 : 0.0;
+  if (rr0 == 0.0 || tol >= 1.0) {
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return AX_OK;
+  }
+  int status = AX_ENOTCONV;
+  while (it < maxit) {
+    int rc = apply(w, p, st);
+    if (rc) return rc;
+    mask_dot_kernel<T><<<nb, kRedThreads, 0, st>>>(w, p, mask, c, P->partials, n);
+    cg_alpha_kernel<<<1, 32, 0, st>>>(P->partials, nb, P->scal);
+    cg_update_kernel<T><<<nb, kRedThreads, 0, st>>>(x, r, p, w, cm, c, P->scal, P->partials,
+                                                    n);
+    cg_beta_kernel<<<1, 64, 0, st>>>(P->partials, nb, P->scal, 0);
+    ++it;
+    if (it % P->check_every == 0 || it == maxit) {
+      if (cudaMemcpyAsync(P->scal_host, P->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                          st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return AX_ELAUNCH;
+      if (P->scal_host->status) {
+        status = AX_EBREAKDOWN;
+        break;
+      }
+      rel = std::sqrt(std::max(P->scal_host->rr, 0.0) / rr0);
+      if (rel <= tol) {
+        status = AX_OK;
+        break;
+      }
+    }
+    cg_p_kernel<T><<<nb, kRedThreads, 0, st>>>(p, r, minv, P->scal, n);
+  }
+  if (ax::launch_status()) return AX_ELAUNCH;
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  return status;
+}
+
+int ensure_lowp(ax_poisson *P, int mode, cudaStream_t st) {
+  if (P->lowp_mode == mode) return AX_OK;
+  if (P->lowp_mode != 0) {  // switch modes: drop the old operator copies
+    cudaFree(P->h1lp);
+    for (auto &q : P->glp) cudaFree(q), q = nullptr;
+    P->h1lp = nullptr;
+  }
+  const int64_t n = P->n;
+  const size_t lx2 = (size_t)P->lx * P->lx;
+  int rc = AX_OK;
+  if (!P->x32) {
+    rc |= alloc(&P->minv32, n) | alloc(&P->mask32, n) | alloc(&P->x32, n) | alloc(&P->r32, n) |
+          alloc(&P->p32, n) | alloc(&P->w32, n) | alloc(&P->q32, n) | alloc(&P->c32, n) |
+          alloc(&P->cm32, n) | alloc(&P->dx32, lx2) | alloc(&P->dxt32, lx2) | alloc(&P->r64, n);
+    if (rc) return AX_ENOMEM;
+  }
+  const size_t es = mode == 2 ? sizeof(__nv_bfloat16) : sizeof(float);
+  if (cudaMalloc(&P->h1lp, n * es) != cudaSuccess) return AX_ENOMEM;
+  for (auto &q : P->glp)
+    if (cudaMalloc(&q, n * es) != cudaSuccess) return AX_ENOMEM;
+  const unsigned nb = kRedBlocks;
+  auto conv = [&](void *out, const double *in, int64_t m) {
+    if (mode == 2)
+      to_bf16_kernel<<<nb, kRedThreads, 0, st>>>((__nv_bfloat16 *)out, in, m);
+    else
+      to_f32_kernel<<<nb, kRedThreads, 0, st>>>((float *)out, in, m);
+  };
+  conv(P->h1lp, P->h1, n);
+  for (int k = 0; k < 6; ++k) conv(P->glp[k], P->g[k], n);
+  to_f32_kernel<<<nb, kRedThreads, 0, st>>>(P->mask32, P->mask, n);
+  to_f32_kernel<<<nb, kRedThreads, 0, st>>>(P->minv32, P->minv, n);
+  to_f32_kernel<<<nb, kRedThreads, 0, st>>>(P->c32, P->c, n);
+  to_f32_kernel<<<nb, kRedThreads, 0, st>>>(P->cm32, P->cm, n);
+  to_f32_kernel<<<1, 256, 0, st>>>(P->dx32, P->dx, (int64_t)lx2);
+  to_f32_kernel<<<1, 256, 0, st>>>(P->dxt32, P->dxt, (int64_t)lx2);
+  if (ax::launch_status()) return AX_ELAUNCH;
+  P->lowp_mode = mode;
+  return AX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ax_poisson_destroy(ax_poisson *P) {
+  if (!P) return AX_OK;
+  double *d64[] = {P->minv, P->cm, P->w, P->r, P->p, P->partials, P->r64};
+  for (double *q : d64) cudaFree(q);
+  float *d32[] = {P->minv32, P->mask32, P->x32, P->r32, P->p32, P->w32,
+                  P->q32,    P->c32,    P->cm32, P->dx32, P->dxt32};
+  for (float *q : d32) cudaFree(q);
+  cudaFree(P->h1lp);
+  for (void *q : P->glp) cudaFree(q);
+  cudaFree(P->scal);
+  if (P->scal_host) cudaFreeHost(P->scal_host);
+  delete P;
+  return AX_OK;
+}
+
+int ax_poisson_create(ax_poisson **out, int lx, int nelv, const double *dx, const double *dxt,
+                      const double *h1, const double *g11, const double *g22, const double *g33,
+                      const double *g12, const double *g13, const double *g23,
+                      const double *mask, ax_gs *gs, void *stream) {
+  if (!out || !ax::lx_ok(lx) || nelv <= 0 ||
+      !ax::all_nonnull(dx, dxt, h1, g11, g22, g33, g12, g13, g23, mask, gs))
+    return AX_EINVAL;
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  ax_poisson *P = new (std::nothrow) ax_poisson();
+  if (!P) return AX_ENOMEM;
+  P->lx = lx;
+  P->nelv = nelv;
+  P->n = (int64_t)nelv * lx * lx * lx;
+  P->dx = dx;
+  P->dxt = dxt;
+  P->h1 = h1;
+  const double *gg[6] = {g11, g22, g33, g12, g13, g23};
+  for (int k = 0; k < 6; ++k) P->g[k] = gg[k];
+  P->mask = mask;
+  P->gs = gs;
+  P->c = ax_gs_inverse_multiplicity(gs);
+  const int64_t n = P->n;
+  int rc = alloc(&P->minv, n) | alloc(&P->cm, n) | alloc(&P->w, n) | alloc(&P->r, n) |
+           alloc(&P->p, n) | alloc(&P->partials, 4 * (size_t)kRedBlocks) |
+           alloc(&P->scal, 1);
+  if (rc == AX_OK && cudaMallocHost((void **)&P->scal_host, sizeof(CgScalars)) != cudaSuccess)
+    rc = AX_ENOMEM;
+  if (rc) {
+    ax_poisson_destroy(P);
+    return AX_ENOMEM;
+  }
+  // exact Jacobi diagonal, assembled, then the masked inverse
+  jacobi_diag_kernel<<<blocks_for(n, 256), 256, 0, st>>>(P->w, dx, h1, g11, g22, g33, g12, g13,
+                                                         g23, lx, n);
+  rc = ax_gs_sum(gs, P->w, st);
+  precond_kernel<<<blocks_for(n, 256), 256, 0, st>>>(P->minv, P->cm, P->w, mask, P->c, n);
+  if (rc == AX_OK) rc = ax::launch_status();
+  if (rc == AX_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = AX_ELAUNCH;
+  if (rc) {
+    ax_poisson_destroy(P);
+    return rc;
+  }
+  *out = P;
+  return AX_OK;
+}
+
+int ax_poisson_set_check_every(ax_poisson *P, int every) {
+  if (!P || every < 1) return AX_EINVAL;
+  P->check_every = every;
+  return AX_OK;
+}
+
+int ax_poisson_apply(ax_poisson *P, double *w, const double *u, void *stream) {
+  if (!P || !w || !u) return AX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = apply_f64(P, w, u, st);
+  if (rc) return rc;
+  // w = mask .* w (partials discarded)
+  mask_dot_kernel<double><<<kRedBlocks, kRedThreads, 0, st>>>(w, u, P->mask, P->c, P->partials,
+                                                              P->n);
+  return ax::launch_status();
+}
+
+int ax_poisson_jacobi(const ax_poisson *P, const double **minv) {
+  if (!P || !minv) return AX_EINVAL;
+  *minv = P->minv;
+  return AX_OK;
+}
+
+int ax_cg_solve(ax_poisson *P, double *x, const double *b, double tol, int maxit, int *iters,
+                double *relres, void *stream) {
+  if (!P || !x || !b || maxit < 0 || !(tol >= 0)) return AX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  auto A = [P](double *w, const double *u, cudaStream_t s) { return apply_f64(P, w, u, s); };
+  return pcg_loop<double>(P, x, b, P->r, P->p, P->w, P->mask, P->minv, P->c, P->cm, A, tol,
+                          maxit, iters, relres, st);
+}
+
+int ax_mpcg_solve(ax_poisson *P, int mode, double *x, const double *b, double tol,
+                  double inner_tol, int max_outer, int max_inner, int *outer_iters,
+                  int *inner_iters, double *relres, void *stream) {
+  if (!P || !x || !b || (mode != AX_PREC_F32 && mode != AX_PREC_BF16) || max_outer < 1 ||
+      max_inner < 1 || !(tol >= 0) || !(inner_tol > 0))
+    return AX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = ensure_lowp(P, mode == AX_PREC_BF16 ? 2 : 1, st);
+  if (rc) return rc;
+  const int64_t n = P->n;
+  const unsigned nb = kRedBlocks;
+  double *sc = reinterpret_cast<double *>(P->scal);  // scratch scalar
+  auto norm_r = [&](double *out_host) -> int {
+    sum_partials_kernel<<<1, 32, 0, st>>>(P->partials, nb, sc);
+    if (cudaMemcpyAsync(out_host, sc, sizeof(double), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return AX_ELAUNCH;
+    return AX_OK;
+  };
+  // x = 0; r = mask .* b
+  cudaMemsetAsync(x, 0, n * sizeof(double), st);
+  cudaMemsetAsync(P->w, 0, n * sizeof(double), st);
+  double rr0 = 0.0, rr = 0.0;
+  residual_kernel<<<nb, kRedThreads, 0, st>>>(P->r64, P->r32, b, P->w, P->mask, P->c,
+                                              P->partials, n);
+  if ((rc = norm_r(&rr0))) return rc;
+  int outer = 0, inner_total = 0;
+  double rel = rr0 > 0 ? 1.0 : 0.0;
+  int status = rr0 == 0.0 ? AX_OK : AX_ENOTCONV;
+  auto A32 = [P](float *w, const float *u, cudaStream_t s) { return apply_lowp(P, w, u, s); };
+  while (status != AX_OK && outer < max_outer) {
+    // inner fp32 PCG on A d = r (r32 holds fp32(r))
+    int its = 0;
+    double irel = 0.0;
+    // inner vectors: rhs r32, residual w32, direction p32, operator output q32
+    rc = pcg_loop<float>(P, P->x32, P->r32, P->w32, P->p32, P->q32, P->mask32, P->minv32,
+                         P->c32, P->cm32, A32, inner_tol, max_inner, &its, &irel, st);
+    inner_total += its;
+    if (rc != AX_OK && rc != AX_ENOTCONV) return rc;
+    add_correction_kernel<<<nb, kRedThreads, 0, st>>>(x, P->x32, n);
+    ++outer;
+    // fp64 residual r = mask .* (b - A x)
+    if ((rc = apply_f64(P, P->w, x, st))) return rc;
+    residual_kernel<<<nb, kRedThreads, 0, st>>>(P->r64, P->r32, b, P->w, P->mask, P->c,
+                                                P->partials, n);
+    if ((rc = norm_r(&rr))) return rc;
+    rel = std::sqrt(std::max(rr, 0.0) / rr0);
+    if (!std::isfinite(rel)) return AX_EBREAKDOWN;
+    if (rel <= tol) status = AX_OK;
+  }
+  if (outer_iters) *outer_iters = outer;
+  if (inner_iters) *inner_iters = inner_total;
+  if (relres) *relres = rel;
+  return status;
+}
+
+}  // extern "C"

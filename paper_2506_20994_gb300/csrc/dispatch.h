@@ -7,6 +7,9 @@
 
 namespace ax {
 
+// Tuned elements per block for (AX_BATCH_F64 | AX_BATCH_F32, lx); 0 if untuned.
+int tuned_epb(int dtype, int lx);
+
 // Largest lx with a double-float instantiation.
 constexpr int AX_DF64_LX_MAX = 12;
 
@@ -27,6 +30,12 @@ int dispatch_kstep_bf16(int lx, float *w, const __nv_bfloat16 *u, const float *d
                         const __nv_bfloat16 *g12, const __nv_bfloat16 *g13,
                         const __nv_bfloat16 *g23, int nelv, int epb, cudaStream_t st);
 
+// k-loop kernel: fp32 u, bf16 h1 and G; fp32 D, arithmetic and w.
+int dispatch_kstep_f32u_bf16(int lx, float *w, const float *u, const float *dx, const float *dxt,
+                             const __nv_bfloat16 *h1, const __nv_bfloat16 *g11,
+                             const __nv_bfloat16 *g22, const __nv_bfloat16 *g33,
+                             const __nv_bfloat16 *g12, const __nv_bfloat16 *g13,
+                             const __nv_bfloat16 *g23, int nelv, int epb, cudaStream_t st);
 // fp64-accurate double-float kernel, lx in 2..7 (a), 8..10 (b), 11..12 (c);
 // AX_EINVAL above AX_DF64_LX_MAX.
 #define AX_DF64_DECL(X)                                                                        \

@@ -1,0 +1,115 @@
+"""GPU checks of the batched multi-mesh launch and the autotuner.
+
+Uneven meshes of mixed lx in one persistent launch (and its CUDA-graph
+replay) must give, for every mesh, exactly the bits of the single-mesh
+kernel with the same elements per block, and match the oracle within the
+fp64 (1e-12) or fp32 (1e-6) relative L2 tolerance.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import paper_2506_20994_gb300 as ax  # noqa: E402
+from paper_2506_20994_gb300 import synth  # noqa: E402
+
+from _cases import GKEYS, rel_l2  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ax.build()
+
+
+def _meshes(dtype, count=10, seed=0):
+    """Small uneven batch: element counts log-uniform in [1, 150], lx from
+    {5, 6, 8, 10} plus two extra orders; oracle w per mesh."""
+    tdt = torch.float64 if dtype == ax.AX_BATCH_F64 else torch.float32
+    g = synth.rng(seed)
+    out = []
+    lxs = [5, 6, 8, 10, 3, 12]
+    for q in range(count):
+        ne = int(np.exp(g.uniform(0, np.log(150))))
+        lx = lxs[q % len(lxs)]
+        dims = synth.box_dims(ne)
+        v = synth.box_vertices(*dims, seed=seed + q)
+        geo = oracle.box_geometry(v, lx)
+        u = synth.uniform(geo["jac"].shape, seed=seed + 100 + q)
+        h1 = synth.uniform(geo["jac"].shape, seed=seed + 200 + q, lo=0.5, hi=2.0)
+        dx, dxt = oracle.d_buffers(lx)
+        ref = oracle.ax_helm(u, dx, dxt, h1, *[geo[k] for k in GKEYS], lx)
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda", dtype=tdt)
+        m = {"lx": lx, "u": t(u), "dx": t(dx), "dxt": t(dxt), "h1": t(h1), "ref": ref}
+        for k in GKEYS:
+            m[k] = t(geo[k])
+        m["w"] = torch.full_like(m["u"], float("nan"))
+        out.append(m)
+    return out
+
+
+@pytest.mark.parametrize("dtype", [ax.AX_BATCH_F64, ax.AX_BATCH_F32])
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_matches_oracle_and_single_launch(dtype, graph):
+    meshes = _meshes(dtype, seed=3 if graph else 1)
+    B = ax.Batch(meshes, dtype=dtype)
+    info = B.info()
+    assert info["items"] > 0 and info["blocks"] > 0
+    B.launch(graph=graph)
+    if graph:  # replay twice more: same bits
+        B.launch(graph=True)
+    torch.cuda.synchronize()
+    tol = 1e-12 if dtype == ax.AX_BATCH_F64 else 1e-6
+    for m in meshes:
+        w = m["w"].double().cpu().numpy()
+        assert rel_l2(w, m["ref"]) <= tol, m["lx"]
+        # the single-mesh kernel with default elements per block: same bits
+        w1 = torch.empty_like(m["u"])
+        if dtype == ax.AX_BATCH_F64:
+            ax.ax_helm(w1, m["u"], m["dx"], m["dxt"], m["h1"], *[m[k] for k in GKEYS], m["lx"])
+        else:
+            ax.ax_helm_f32(w1, m["u"], m["dx"], m["dxt"], m["h1"], *[m[k] for k in GKEYS],
+                           m["lx"])
+        torch.cuda.synchronize()
+        assert torch.equal(w1, m["w"])
+
+
+def test_batch_empty_and_bad_meshes():
+    B = ax.Batch([], dtype=ax.AX_BATCH_F64)
+    B.launch()
+    torch.cuda.synchronize()
+    m = _meshes(ax.AX_BATCH_F64, count=1)[0]
+    m["lx"] = 13  # outside the batched range
+    with pytest.raises(ax.AxError):
+        ax.Batch([m], dtype=ax.AX_BATCH_F64)
+
+
+@pytest.mark.parametrize("dtype", [ax.AX_BATCH_F64, ax.AX_BATCH_F32])
+def test_tuner_records_choice_and_parity_holds(dtype):
+    lx = 6
+    m = _meshes(dtype, count=1, seed=9)[0]
+    m["lx"] = lx
+    # a larger synthetic mesh so timings mean something
+    tdt = m["u"].dtype
+    nel = 2048
+    f = {k: torch.rand(nel * lx ** 3, device="cuda", dtype=tdt) for k in
+         ("w", "u", "h1") + GKEYS}
+    dx, dxt = oracle.d_buffers(lx)
+    f["dx"] = torch.as_tensor(dx, device="cuda", dtype=tdt)
+    f["dxt"] = torch.as_tensor(dxt, device="cuda", dtype=tdt)
+    epb, ms = ax.tune(dtype, lx, f, reps=3)
+    assert 1 <= epb <= 256 // lx ** 2 and ms > 0
+    assert ax.tune_get(dtype, lx) == epb
+    try:
+        meshes = _meshes(dtype, count=6, seed=11)
+        B = ax.Batch(meshes, dtype=dtype)
+        B.launch()
+        torch.cuda.synchronize()
+        tol = 1e-12 if dtype == ax.AX_BATCH_F64 else 1e-6
+        for mm in meshes:
+            assert rel_l2(mm["w"].double().cpu().numpy(), mm["ref"]) <= tol
+    finally:
+        ax.tune_set(dtype, lx, 0)
