@@ -147,6 +147,26 @@ int ax_poisson_jacobi(const ax_poisson *P, const double **minv);
 /* How often the solvers read the residual norm back (default 1). */
 int ax_poisson_set_check_every(ax_poisson *P, int every);
 
+/* Allocation-free refresh of the masked inverse Jacobi diagonal (the paper
+ * has no counterpart; it serves callers that may not allocate device memory
+ * where they need it: work recorded into a CUDA graph, a time loop with a
+ * fixed memory budget, a host framework that owns all device allocations).
+ * Writes into minv[nelv*lx^3] (caller's device memory) the same array that
+ * ax_poisson_create computes (ax_poisson_jacobi) for the given dx, h1, G,
+ * mask (1 interior / 0 Dirichlet) and gather-scatter handle.  Its scratch is
+ * a fixed device array inside the library of AX_NOALLOC_MAX_POINTS doubles
+ * (4 MiB, reserved on every GPU that loads the library until exit); larger
+ * problems return AX_EINVAL, as does a gs handle of another size.  Calls no
+ * cudaMalloc/cudaFree.  The first call on a device resolves the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * race and must be serialised by the caller.  Asynchronous on stream. */
+#define AX_NOALLOC_MAX_POINTS (1 << 19)
+int ax_jacobi_noalloc(double *minv, const double *dx, const double *h1, const double *g11,
+                      const double *g22, const double *g33, const double *g12,
+                      const double *g13, const double *g23, const double *mask, ax_gs *gs,
+                      int lx, int nelv, void *stream);
+
 /* Jacobi-preconditioned CG in fp64 from x0 = 0 until ||r|| <= tol ||b||
  * (b is masked first).  Writes the iteration count and the final relative
  * residual.  Synchronises stream.  Returns AX_OK, AX_ENOTCONV (maxit

@@ -52,6 +52,7 @@ PROTOTYPES = {
     "ax_tune_run": (c_int, [c_int, c_int, c_int] + [P] * 11 + [c_int, P, P, c_void_p]),
     "ax_tune_set": (c_int, [c_int, c_int, c_int]),
     "ax_tune_get": (c_int, [c_int, c_int, P]),
+    "ax_jacobi_noalloc": (c_int, [P] * 10 + [c_void_p, c_int, c_int, c_void_p]),
 }
 
 

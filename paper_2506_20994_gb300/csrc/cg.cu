@@ -562,3 +562,91 @@ int ax_mpcg_solve(ax_poisson *P, int mode, double *x, const double *b, double to
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free Jacobi refresh.
+//
+// Some callers must not allocate device memory at the point where they need
+// the preconditioner: code that records work into a CUDA graph or runs
+// inside a time-stepping loop with a fixed memory budget, or a host
+// framework that owns every device allocation through its own pool.  When
+// such a caller changes h1 (a variable coefficient) it still needs a fresh
+// masked inverse Jacobi diagonal.  ax_poisson_create computes one, but it
+// allocates; ax_jacobi_noalloc computes the same array into caller memory
+// with its scratch (the un-assembled diagonal) in the fixed device array
+// below, so it performs no allocation at all.
+//
+// The scratch holds at most AX_NOALLOC_MAX_POINTS doubles (4 MiB).  It is a
+// file-scope __device__ array, so every GPU that loads this library keeps
+// those 4 MiB reserved until the process exits.  Every call on a device
+// shares the one array, and it keeps the previous call's contents; the
+// kernel overwrites all n entries it later reads, so nothing needs clearing.
+// Calls whose work overlaps on the GPU (two streams, or two host threads)
+// race on the array and must be serialised by the caller.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+static __device__ __align__(256) double g_noalloc_diag[AX_NOALLOC_MAX_POINTS];
+
+namespace {
+
+__global__ void noalloc_minv_kernel(double *__restrict__ minv, const double *__restrict__ diag,
+                                    const double *__restrict__ mask, int64_t n) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  minv[q] = (mask[q] != 0.0 && diag[q] != 0.0) ? 1.0 / diag[q] : 0.0;
+}
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kNoallocMaxDevices];  // device address of the array, per device
+
+// Device address of the scratch array on the current device; resolved once
+// per device (host code cannot use the symbol itself as an address).
+int noalloc_scratch(double **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return AX_ELAUNCH;
+  }
+  if (dev < 0 || dev >= kNoallocMaxDevices) return AX_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_diag) != cudaSuccess || !p) {
+      (void)cudaGetLastError();
+      return AX_ELAUNCH;
+    }
+    g_noalloc_ptr[dev] = static_cast<double *>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return AX_OK;
+}
+
+}  // namespace
+
+extern "C" int ax_gs_info(const ax_gs *g, int64_t *n_local, int64_t *n_shared,
+                          int64_t *n_copies);
+
+extern "C" int ax_jacobi_noalloc(double *minv, const double *dx, const double *h1,
+                                 const double *g11, const double *g22, const double *g33,
+                                 const double *g12, const double *g13, const double *g23,
+                                 const double *mask, ax_gs *gs, int lx, int nelv, void *stream) {
+  if (!ax::lx_ok(lx) || nelv < 0) return AX_EINVAL;
+  const int64_t n = (int64_t)nelv * lx * lx * lx;
+  if (n > AX_NOALLOC_MAX_POINTS) return AX_EINVAL;  // larger than the fixed scratch
+  if (n == 0) return AX_OK;
+  if (!ax::all_nonnull(minv, dx, h1, g11, g22, g33, g12, g13, g23, mask, gs)) return AX_EINVAL;
+  int64_t n_gs = -1;
+  if (ax_gs_info(gs, &n_gs, nullptr, nullptr) != AX_OK || n_gs != n) return AX_EINVAL;
+  double *scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  jacobi_diag_kernel<<<blocks_for(n, 256), 256, 0, st>>>(scratch, dx, h1, g11, g22, g33, g12,
+                                                         g13, g23, lx, n);
+  if ((rc = ax::launch_status())) return rc;
+  if ((rc = ax_gs_sum(gs, scratch, st))) return rc;
+  noalloc_minv_kernel<<<blocks_for(n, 256), 256, 0, st>>>(minv, scratch, mask, n);
+  return ax::launch_status();
+}
