@@ -185,6 +185,53 @@ int ax_mpcg_solve(ax_poisson *P, int mode, double *x, const double *b, double to
                   int *inner_iters, double *relres, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Learned element preconditioner.  The paper has no learned component (it
+ * studies the operator only); this is the project's learned form:
+ *   z = minv .* r + gs(mask .* (1/mult) .* s_e * MLP(x_e)),
+ *   x_e = (minv .* r)_e / s_e,  s_e = ||(minv .* r)_e||_2,
+ *   MLP(x) = tanh(x W1 + b1) W2 + b2   (n_in = n_out = lx^3 per element),
+ * applied with bf16 weights on the tensor cores (fp32 accumulation) and
+ * trained with fp32 kernels on pairs (x_e, (err_e - (minv .* r)_e)/s_e)
+ * of element residuals and errors.  Parameters are one flat fp32 vector
+ * [W1 (n_in x n_hid, row-major), b1, W2 (n_hid x n_in), b2].
+ * ------------------------------------------------------------------------ */
+typedef struct ax_mlp ax_mlp;
+
+/* Allocates the network (device; parameters start at zero, which makes the
+ * preconditioner exactly Jacobi).  n_in in [1, 4096], n_hid in [1, 64]. */
+int ax_mlp_create(ax_mlp **M, int n_in, int n_hid);
+int ax_mlp_destroy(ax_mlp *M);
+int ax_mlp_nparams(const ax_mlp *M, int64_t *n);
+/* Host fp32 parameter vector in / out (count must equal nparams); set
+ * resets the Adam state and refreshes the bf16 inference copy.  Both
+ * synchronise stream. */
+int ax_mlp_set_params(ax_mlp *M, const float *host, int64_t count, void *stream);
+int ax_mlp_get_params(const ax_mlp *M, float *host, int64_t count, void *stream);
+/* Training pieces on device fp32 batches X, T [B x n_in]: loss (mean
+ * squared error, written to *loss on the host) and its gradient (copied to
+ * grad_host if not NULL); then one Adam step on the last gradient.
+ * loss_grad allocates the batch workspace when B grows; synchronises. */
+int ax_mlp_loss_grad(ax_mlp *M, const float *X, const float *T, int B, double *loss,
+                     float *grad_host, void *stream);
+int ax_mlp_adam(ax_mlp *M, float lr, float beta1, float beta2, float eps, void *stream);
+/* Sample set from fp64 local vectors: for each idx[s] (element id, device
+ * int32) writes X[s] = (minv .* r)_e / s_e and T[s] = (err - minv .* r)_e / s_e
+ * (device fp32 [nsamples x n_in]). */
+int ax_mlp_gather_pairs(const ax_mlp *M, const double *r, const double *err, const double *minv,
+                        const int *idx, int nsamples, float *X, float *T, void *stream);
+/* Minibatch Adam over a sample set: epoch e visits rows perm[e*nsamples ..]
+ * (device int32, epochs*nsamples entries, any order) in batches of `batch`;
+ * lr fixed, beta1 0.9, beta2 0.999, eps 1e-8.  Writes the last batch loss;
+ * synchronises stream. */
+int ax_mlp_train(ax_mlp *M, const float *X_all, const float *T_all, int nsamples,
+                 const int *perm, int epochs, int batch, float lr, double *final_loss,
+                 void *stream);
+/* corr = mask .* c .* s_e * MLP(x_e) for fp32 local vectors (no gs);
+ * the element-local part of the preconditioner, asynchronous. */
+int ax_mlp_forward(const ax_mlp *M, const float *r, const float *minv, const float *mask,
+                   const float *c, float *corr, int nelv, void *stream);
+
+/* ------------------------------------------------------------------------
  * Batched operator over many independent meshes of uneven size and mixed
  * lx in one persistent launch.  The paper applies Listing 2 to one mesh per
  * launch and Neko picks its kernel variant by run-time timing (Sec.
@@ -231,6 +278,37 @@ int ax_tune_run(int dtype, int lx, int nelv, void *w, const void *u, const void 
                 int *best_epb, float *best_ms, void *stream);
 int ax_tune_set(int dtype, int lx, int elems_per_block);
 int ax_tune_get(int dtype, int lx, int *elems_per_block);
+
+/* y = a x + b y on device fp64 vectors of n values (asynchronous). */
+int ax_axpby(double *y, double a, const double *x, double b, int64_t n, void *stream);
+
+/* Preconditioner application z = minv .* r (+ learned correction if M is
+ * not NULL; M's n_in must be lx^3) for fp64 local vectors; synchronises. */
+int ax_precondition(ax_poisson *P, const ax_mlp *M, double *z, const double *r, void *stream);
+
+/* Flexible CG (Notay 2000: beta = <z_new, r_new - r_old> / <z_old, r_old>)
+ * with the learned preconditioner in fp64 from x0 = 0; M == NULL gives the
+ * Jacobi preconditioner.  A step whose <r, z> is not positive or finite
+ * falls back to Jacobi (counted in *fallbacks).  Status codes as
+ * ax_cg_solve; allocates its work vectors on first use; synchronises. */
+int ax_fcg_solve(ax_poisson *P, const ax_mlp *M, double *x, const double *b, double tol,
+                 int maxit, int *iters, double *relres, int *fallbacks, void *stream);
+
+/* Energy-norm training of the learned preconditioner on K residual/error
+ * pairs of the operator P (device fp64, K consecutive local vectors each in
+ * r_set and e_set, e.g. CG iterates r_k = b - A x_k and e_k = x* - x_k):
+ * Adam (fixed lr) on L_k = ||e_k - z(r_k)||_A^2 / ||e_k||_A^2 with z the
+ * preconditioner of ax_precondition, every element one training row, the
+ * K pairs visited in order for `epochs` passes.  Writes the mean L_k of the
+ * last pass.  Allocates scratch (freed on return); synchronises stream. */
+int ax_mlp_train_energy(ax_poisson *P, ax_mlp *M, const double *r_set, const double *e_set,
+                        int K, int epochs, float lr, double *final_loss, void *stream);
+
+/* ax_mpcg_solve with the flexible CG and the learned preconditioner (in
+ * fp32) as the inner solver; fallbacks summed over the inner solves. */
+int ax_mpfcg_solve(ax_poisson *P, const ax_mlp *M, int mode, double *x, const double *b,
+                   double tol, double inner_tol, int max_outer, int max_inner, int *outer_iters,
+                   int *inner_iters, double *relres, int *fallbacks, void *stream);
 
 /* ------------------------------------------------------------------------
  * Host-side discretisation set-up (no GPU needed; plain host memory).

@@ -23,7 +23,8 @@ __all__ = [
     "ax_helm_f32", "ax_helm_bf16", "AX_VARIANT_AUTO", "AX_VARIANT_F64_DF",
     "AX_VARIANT_F64_NATIVE", "df64_roundtrip", "build", "GatherScatter", "Poisson",
     "AX_PREC_F32", "AX_PREC_BF16", "Batch", "tune", "tune_set", "tune_get", "AX_BATCH_F64",
-    "AX_BATCH_F32",
+    "AX_BATCH_F32", "fourier_coefficient", "Mlp", "mlp_init_params", "training_pairs", "train_mlp", "axpby", "iterate_pairs",
+    "train_energy",
 ]
 
 
@@ -216,6 +217,21 @@ class GatherScatter:
             self._h = None
 
 
+def fourier_coefficient(seed: int, lo: float = 0.5, hi: float = 2.0):
+    """Smooth variable coefficient: the sum of 8 random Fourier modes
+    (synth.fourier_modes) rescaled affinely into [lo, hi] over the nodes it
+    is evaluated on.  Returns a callable h1(x, y, z)."""
+    from . import synth
+    a, k, phi = synth.fourier_modes(seed)
+
+    def h1(x, y, z):
+        raw = sum(a[m] * np.sin(k[m, 0] * x + k[m, 1] * y + k[m, 2] * z + phi[m])
+                  for m in range(len(a)))
+        r0, r1 = raw.min(), raw.max()
+        return lo + (hi - lo) * (raw - r0) / max(r1 - r0, 1e-300)
+    return h1
+
+
 class Poisson:
     """Poisson problem -div(h1 grad u) = f on a perturbed box with
     homogeneous Dirichlet boundaries, set up on the host by the library
@@ -241,6 +257,8 @@ class Poisson:
         X, Y, Z = glob % NX, (glob // NX) % NY, glob // (NX * NY)
         on = (X == 0) | (X == NX - 1) | (Y == 0) | (Y == NY - 1) | (Z == 0) | (Z == NZ - 1)
         mask = np.where(on, 0.0, 1.0)
+        if callable(h1):
+            h1 = h1(self.xyz[..., 0], self.xyz[..., 1], self.xyz[..., 2])
         h1v = np.ones_like(mask) if h1 is None else np.broadcast_to(
             np.asarray(h1, dtype=np.float64), mask.shape).copy()
         t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=self.device)
@@ -395,3 +413,217 @@ def tune_get(dtype: int, lx: int) -> int:
     e = ctypes.c_int()
     check("ax_tune_get", lib().ax_tune_get(dtype, lx, ctypes.addressof(e)))
     return e.value
+
+
+# ---------------------------------------------------------------------------
+# learned element preconditioner
+# ---------------------------------------------------------------------------
+def axpby(y, a: float, x, b: float) -> None:
+    """y <- a x + b y (fp64 CUDA tensors, ax_axpby)."""
+    check("ax_axpby", lib().ax_axpby(y.data_ptr(), a, x.data_ptr(), b, y.numel(), _stream()))
+
+
+def mlp_init_params(n_in: int, n_hid: int, seed: int = 0) -> np.ndarray:
+    """Initial parameters: W1 uniform in +-sqrt(6/(n_in+n_hid)) (Glorot),
+    b1 = 0, and a zero output layer, so the untrained preconditioner is
+    exactly Jacobi.  Random numbers come from ``synth``."""
+    from . import synth
+    lim = np.sqrt(6.0 / (n_in + n_hid))
+    W1 = synth.uniform((n_in, n_hid), seed, -lim, lim)
+    return np.concatenate([W1.ravel(), np.zeros(n_hid), np.zeros(n_hid * n_in),
+                           np.zeros(n_in)]).astype(np.float32)
+
+
+class Mlp:
+    """The per-element network of the learned preconditioner (ax_mlp_*)."""
+
+    def __init__(self, n_in: int, n_hid: int = 48, params=None):
+        import ctypes
+        h = ctypes.c_void_p()
+        check("ax_mlp_create", lib().ax_mlp_create(ctypes.addressof(h), n_in, n_hid))
+        self._h, self.n_in, self.n_hid = h, n_in, n_hid
+        n = ctypes.c_int64()
+        check("ax_mlp_nparams", lib().ax_mlp_nparams(h, ctypes.addressof(n)))
+        self.nparams = n.value
+        if params is not None:
+            self.set_params(params)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_params(self, params) -> None:
+        p = np.ascontiguousarray(params, dtype=np.float32).ravel()
+        check("ax_mlp_set_params", lib().ax_mlp_set_params(self._h, _addr(p), p.size, _stream()))
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.nparams, dtype=np.float32)
+        check("ax_mlp_get_params", lib().ax_mlp_get_params(self._h, _addr(p), p.size, _stream()))
+        return p
+
+    def loss_grad(self, X, T):
+        import ctypes
+        B = X.shape[0]
+        loss = ctypes.c_double()
+        g = np.empty(self.nparams, dtype=np.float32)
+        check("ax_mlp_loss_grad", lib().ax_mlp_loss_grad(self._h, X.data_ptr(), T.data_ptr(), B,
+                                                         ctypes.addressof(loss), _addr(g),
+                                                         _stream()))
+        return loss.value, g
+
+    def adam(self, lr: float, beta1=0.9, beta2=0.999, eps=1e-8) -> None:
+        check("ax_mlp_adam", lib().ax_mlp_adam(self._h, lr, beta1, beta2, eps, _stream()))
+
+    def gather_pairs(self, r, err, minv, idx):
+        """(X, T) fp32 CUDA tensors for the element ids idx (int32 tensor)."""
+        import torch
+        n = idx.numel()
+        X = torch.empty((n, self.n_in), dtype=torch.float32, device=r.device)
+        T = torch.empty_like(X)
+        check("ax_mlp_gather_pairs", lib().ax_mlp_gather_pairs(
+            self._h, r.data_ptr(), err.data_ptr(), minv.data_ptr(), idx.data_ptr(), n,
+            X.data_ptr(), T.data_ptr(), _stream()))
+        return X, T
+
+    def train(self, X, T, perm, epochs: int, batch: int, lr: float) -> float:
+        import ctypes
+        loss = ctypes.c_double()
+        check("ax_mlp_train", lib().ax_mlp_train(self._h, X.data_ptr(), T.data_ptr(),
+                                                 X.shape[0], perm.data_ptr(), epochs, batch,
+                                                 lr, ctypes.addressof(loss), _stream()))
+        return loss.value
+
+    def forward(self, corr, r, minv, mask, c, nelv: int) -> None:
+        check("ax_mlp_forward", lib().ax_mlp_forward(self._h, r.data_ptr(), minv.data_ptr(),
+                                                     mask.data_ptr(), c.data_ptr(),
+                                                     corr.data_ptr(), nelv, _stream()))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib._lib is not None:
+            _lib._lib.ax_mlp_destroy(h)
+            self._h = None
+
+
+def _poisson_fcg(self, b, mlp=None, tol=1e-8, maxit=10000, raise_on_error=True):
+    """Flexible CG with the learned preconditioner (Jacobi if mlp is None);
+    returns (x, iterations, relres, fallbacks, status)."""
+    import ctypes
+    import torch
+    x = torch.empty_like(b)
+    it, rel, fb = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+    rc = lib().ax_fcg_solve(self._h, mlp.handle if mlp is not None else None, x.data_ptr(),
+                            b.data_ptr(), tol, maxit, ctypes.addressof(it),
+                            ctypes.addressof(rel), ctypes.addressof(fb), _stream())
+    if raise_on_error and rc not in (0, _lib.AX_ENOTCONV):
+        check("ax_fcg_solve", rc)
+    return x, it.value, rel.value, fb.value, rc
+
+
+def _poisson_mpfcg(self, b, mlp=None, mode=_lib.AX_PREC_F32, tol=1e-8, inner_tol=1e-4,
+                   max_outer=50, max_inner=10000, raise_on_error=True):
+    """fp64 refinement around the fp32 flexible CG with the learned
+    preconditioner; returns (x, outer, inner, relres, fallbacks, status)."""
+    import ctypes
+    import torch
+    x = torch.empty_like(b)
+    no, ni, rel, fb = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+    rc = lib().ax_mpfcg_solve(self._h, mlp.handle if mlp is not None else None, mode,
+                              x.data_ptr(), b.data_ptr(), tol, inner_tol, max_outer, max_inner,
+                              ctypes.addressof(no), ctypes.addressof(ni), ctypes.addressof(rel),
+                              ctypes.addressof(fb), _stream())
+    if raise_on_error and rc not in (0, _lib.AX_ENOTCONV):
+        check("ax_mpfcg_solve", rc)
+    return x, no.value, ni.value, rel.value, fb.value, rc
+
+
+def _poisson_precondition(self, r, mlp=None):
+    import torch
+    z = torch.empty_like(r)
+    check("ax_precondition", lib().ax_precondition(self._h, mlp.handle if mlp is not None
+                                                   else None, z.data_ptr(), r.data_ptr(),
+                                                   _stream()))
+    return z
+
+
+def _poisson_residual(self, b, x):
+    """r = mask .* (b - A x) (fp64)."""
+    import torch
+    w = torch.empty_like(x)
+    self.apply(w, x)
+    r = b.clone()
+    axpby(r, -1.0, w, 1.0)
+    return r
+
+
+Poisson.fcg = _poisson_fcg
+Poisson.mpfcg = _poisson_mpfcg
+Poisson.precondition = _poisson_precondition
+Poisson.residual = _poisson_residual
+
+
+def training_pairs(P: "Poisson", b, mlp: Mlp, n_pairs: int = 10240, iterates=(2, 4, 8, 16,
+                   32, 64, 128), seed: int = 0, xstar=None):
+    """Element training pairs from plain Jacobi-CG iterates x_k of P x = b:
+    r_k = b - A x_k and err_k = x* - x_k with x* solved to 1e-12; n_pairs
+    elements drawn uniformly (synth) across the iterates.  Returns fp32
+    CUDA tensors (X, T)."""
+    import torch
+    from . import synth
+    if xstar is None:
+        xstar, _, _, _ = P.cg(b, tol=1e-12)
+    minv = P.jacobi()
+    per = -(-n_pairs // len(iterates))
+    g = synth.rng(seed)
+    Xs, Ts = [], []
+    for k in iterates:
+        xk, _, _, _ = P.cg(b, tol=0.0, maxit=k, raise_on_error=False)
+        r = P.residual(b, xk)
+        err = xstar.clone()
+        axpby(err, -1.0, xk, 1.0)
+        idx = torch.as_tensor(g.integers(0, P.nelv, size=per).astype(np.int32), device=b.device)
+        X, T = mlp.gather_pairs(r, err, minv, idx)
+        Xs.append(X)
+        Ts.append(T)
+    return torch.cat(Xs)[:n_pairs].contiguous(), torch.cat(Ts)[:n_pairs].contiguous()
+
+
+def train_mlp(mlp: Mlp, X, T, epochs: int = 30, batch: int = 512, lr: float = 1e-3,
+              seed: int = 0) -> float:
+    """Adam over the sample set with per-epoch permutations from synth."""
+    import torch
+    from . import synth
+    g = synth.rng(seed)
+    n = X.shape[0]
+    perm = np.concatenate([g.permutation(n) for _ in range(epochs)]).astype(np.int32)
+    perm_t = torch.as_tensor(perm, device=X.device)
+    return mlp.train(X, T, perm_t, epochs, batch, lr)
+
+
+def iterate_pairs(P: "Poisson", b, iterates=(2, 4, 8, 16, 32, 64, 128, 256), xstar=None):
+    """Residual/error pairs of plain Jacobi-CG on P x = b: for every k in
+    iterates, r_k = mask .* (b - A x_k) and e_k = x* - x_k (x* solved to
+    1e-12).  Returns two fp64 CUDA tensors of shape (K, n)."""
+    import torch
+    if xstar is None:
+        xstar, _, _, _ = P.cg(b, tol=1e-12)
+    R = torch.empty((len(iterates), b.numel()), dtype=torch.float64, device=b.device)
+    E = torch.empty_like(R)
+    for q, k in enumerate(iterates):
+        xk, _, _, _ = P.cg(b, tol=0.0, maxit=k, raise_on_error=False)
+        R[q] = P.residual(b, xk).reshape(-1)
+        e = xstar.clone()
+        axpby(e, -1.0, xk, 1.0)
+        E[q] = e.reshape(-1)
+    return R, E
+
+
+def train_energy(P: "Poisson", mlp: Mlp, R, E, epochs: int = 50, lr: float = 1e-3) -> float:
+    """Energy-norm training on the pairs (R[k], E[k]) (ax_mlp_train_energy);
+    returns the mean relative energy error of the last pass."""
+    import ctypes
+    loss = ctypes.c_double()
+    check("ax_mlp_train_energy", lib().ax_mlp_train_energy(
+        P._h, mlp.handle, R.data_ptr(), E.data_ptr(), R.shape[0], epochs, lr,
+        ctypes.addressof(loss), _stream()))
+    return loss.value

@@ -53,6 +53,23 @@ PROTOTYPES = {
     "ax_tune_set": (c_int, [c_int, c_int, c_int]),
     "ax_tune_get": (c_int, [c_int, c_int, P]),
     "ax_jacobi_noalloc": (c_int, [P] * 10 + [c_void_p, c_int, c_int, c_void_p]),
+    "ax_mlp_create": (c_int, [P, c_int, c_int]),
+    "ax_mlp_destroy": (c_int, [c_void_p]),
+    "ax_mlp_nparams": (c_int, [c_void_p, P]),
+    "ax_mlp_set_params": (c_int, [c_void_p, P, c_int64, c_void_p]),
+    "ax_mlp_get_params": (c_int, [c_void_p, P, c_int64, c_void_p]),
+    "ax_mlp_loss_grad": (c_int, [c_void_p, P, P, c_int, P, P, c_void_p]),
+    "ax_mlp_adam": (c_int, [c_void_p, c_float, c_float, c_float, c_float, c_void_p]),
+    "ax_mlp_gather_pairs": (c_int, [c_void_p, P, P, P, P, c_int, P, P, c_void_p]),
+    "ax_mlp_train": (c_int, [c_void_p, P, P, c_int, P, c_int, c_int, c_float, P, c_void_p]),
+    "ax_mlp_forward": (c_int, [c_void_p, P, P, P, P, P, c_int, c_void_p]),
+    "ax_axpby": (c_int, [P, c_double, P, c_double, c_int64, c_void_p]),
+    "ax_mlp_train_energy": (c_int, [c_void_p, c_void_p, P, P, c_int, c_int, c_float, P,
+                                    c_void_p]),
+    "ax_precondition": (c_int, [c_void_p, c_void_p, P, P, c_void_p]),
+    "ax_fcg_solve": (c_int, [c_void_p, c_void_p, P, P, c_double, c_int, P, P, P, c_void_p]),
+    "ax_mpfcg_solve": (c_int, [c_void_p, c_void_p, c_int, P, P, c_double, c_double, c_int,
+                               c_int, P, P, P, P, c_void_p]),
 }
 
 

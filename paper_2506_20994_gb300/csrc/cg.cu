@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "dispatch.h"
+#include "mlp.cuh"
 #include "reduce.cuh"
 
 struct ax_gs;
@@ -35,7 +36,9 @@ using ax::kRedThreads;
 // Device-side scalars of one CG run.
 struct CgScalars {
   double rz, rz_new, rr, rr0, pap, alpha, beta;
-  int status;  // 0 ok, 1 breakdown (p.Ap <= 0 or non-finite)
+  int status;     // 0 ok, 1 breakdown (p.Ap <= 0 or non-finite)
+  int use_corr;   // flexible CG: 1 if the learned correction is in z
+  int fallbacks;  // flexible CG: steps that fell back to Jacobi
 };
 
 // ---------------------------------------------------------------- kernels
@@ -267,6 +270,9 @@ struct ax_poisson {
   void *h1lp = nullptr, *glp[6] = {};
   double *r64 = nullptr;  // outer residual
   int check_every = 1;
+  // flexible-CG work (lazily allocated): previous residual, learned correction
+  double *r_old = nullptr, *corr = nullptr;
+  float *r_old32 = nullptr, *corr32 = nullptr;
 };
 
 namespace {
@@ -419,6 +425,10 @@ int ax_poisson_destroy(ax_poisson *P) {
   for (float *q : d32) cudaFree(q);
   cudaFree(P->h1lp);
   for (void *q : P->glp) cudaFree(q);
+  cudaFree(P->r_old);
+  cudaFree(P->corr);
+  cudaFree(P->r_old32);
+  cudaFree(P->corr32);
   cudaFree(P->scal);
   if (P->scal_host) cudaFreeHost(P->scal_host);
   delete P;
@@ -649,4 +659,480 @@ extern "C" int ax_jacobi_noalloc(double *minv, const double *dx, const double *h
   if ((rc = ax_gs_sum(gs, scratch, st))) return rc;
   noalloc_minv_kernel<<<blocks_for(n, 256), 256, 0, st>>>(minv, scratch, mask, n);
   return ax::launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// Flexible CG with the learned element preconditioner.
+//
+//   z = minv .* r + corr,   corr = gs(mask .* (1/mult) .* s_e * MLP(x_e))
+//
+// (mlp.cu).  A nonlinear preconditioner needs the flexible form of CG:
+// beta_k = <z_{k+1}, r_{k+1} - r_k> / <z_k, r_k> (Notay 2000, "Flexible
+// conjugate gradients").  If <r, z> is not positive or not finite the step
+// falls back to z = minv .* r (counted); with no network every step is the
+// Jacobi step.  All decisions are taken on the device; the host only reads
+// the residual norm every check_every iterations.
+// ---------------------------------------------------------------------------
+namespace {
+
+// x += alpha p; r_old = r; r -= alpha w; partial rr = sum c r^2
+template <typename T>
+__global__ void fcg_update_kernel(T *__restrict__ x, T *__restrict__ r, T *__restrict__ r_old,
+                                  const T *__restrict__ p, const T *__restrict__ w,
+                                  const T *__restrict__ c, const CgScalars *__restrict__ s,
+                                  double *__restrict__ partials, int64_t n) {
+  __shared__ double sh[kRedThreads / 32];
+  const T alpha = (T)s->alpha;
+  T a_rr = 0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    x[q] += alpha * p[q];
+    const T ro = r[q];
+    r_old[q] = ro;
+    const T rv = ro - alpha * w[q];
+    r[q] = rv;
+    a_rr += c[q] * rv * rv;
+  }
+  double v[1] = {(double)a_rr};
+  ax::block_sum<1>(v, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+}
+
+// partials of <zj, r>, <corr, r>, <zj, r_old>, <corr, r_old> (zj = minv r)
+template <typename T>
+__global__ void fcg_dots_kernel(const T *__restrict__ r, const T *__restrict__ r_old,
+                                const T *__restrict__ corr, const T *__restrict__ minv,
+                                const T *__restrict__ c, int have_corr,
+                                double *__restrict__ partials, int64_t n) {
+  __shared__ double sh[4 * kRedThreads / 32];
+  T d0 = 0, d1 = 0, d2 = 0, d3 = 0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const T cq = c[q], rv = r[q], ro = r_old[q];
+    const T zj = minv[q] * rv;
+    const T co = have_corr ? corr[q] : T(0);
+    d0 += cq * zj * rv;
+    d1 += cq * co * rv;
+    d2 += cq * zj * ro;
+    d3 += cq * co * ro;
+  }
+  double v[4] = {(double)d0, (double)d1, (double)d2, (double)d3};
+  ax::block_sum<4>(v, sh);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) partials[k * gridDim.x + blockIdx.x] = v[k];
+}
+
+// first: rz from <z0, r0>; otherwise Notay's beta; choose learned or Jacobi
+__global__ void fcg_beta_kernel(const double *__restrict__ partials, int nblk,
+                                CgScalars *__restrict__ s, int first, int have_corr) {
+  __shared__ double t[4];
+  ax::warp_sum_partials<4>(partials, nblk, t);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double rz_l = t[0] + t[1], rz_j = t[0];
+    const double num_l = rz_l - (t[2] + t[3]), num_j = t[0] - t[2];
+    const bool ok_l = have_corr && rz_l > 0.0 && isfinite(rz_l) && isfinite(num_l);
+    if (have_corr && !ok_l) s->fallbacks += 1;
+    const double rz = ok_l ? rz_l : rz_j;
+    const double num = ok_l ? num_l : num_j;
+    s->use_corr = ok_l ? 1 : 0;
+    if (first) {
+      s->beta = 0.0;
+    } else {
+      s->beta = (s->rz != 0.0) ? num / s->rz : 0.0;
+    }
+    s->rz = rz;
+    if (!isfinite(rz)) s->status = 1;
+  }
+}
+
+// p = minv r + use_corr * corr + beta p   (first: p = z)
+template <typename T>
+__global__ void fcg_p_kernel(T *__restrict__ p, const T *__restrict__ r,
+                             const T *__restrict__ minv, const T *__restrict__ corr,
+                             const CgScalars *__restrict__ s, int first, int64_t n) {
+  const T beta = first ? T(0) : (T)s->beta;
+  const bool uc = s->use_corr != 0;
+  // explicit roundings: the Jacobi-only step is the same bits whether or not
+  // a (zero) correction is present
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    T z = ax::mul_rn(minv[q], r[q]);
+    if (uc) z = ax::add_rn(z, corr[q]);
+    p[q] = first ? z : ax::fma_rn(beta, p[q], z);
+  }
+}
+
+// init: x = 0, r = mask b, partial rr
+template <typename T>
+__global__ void fcg_init_kernel(T *__restrict__ x, T *__restrict__ r, T *__restrict__ r_old,
+                                const T *__restrict__ b, const T *__restrict__ mask,
+                                const T *__restrict__ c, double *__restrict__ partials,
+                                int64_t n) {
+  __shared__ double sh[kRedThreads / 32];
+  T a = 0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const T rv = b[q] * mask[q];
+    x[q] = T(0);
+    r[q] = rv;
+    r_old[q] = T(0);
+    a += c[q] * rv * rv;
+  }
+  double v[1] = {(double)a};
+  ax::block_sum<1>(v, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+}
+
+__global__ void fcg_rr_kernel(const double *__restrict__ partials, int nblk,
+                              CgScalars *__restrict__ s, int first) {
+  __shared__ double t[1];
+  ax::warp_sum_partials<1>(partials, nblk, t);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s->rr = t[0];
+    if (first) {
+      s->rr0 = t[0];
+      s->status = 0;
+      s->fallbacks = 0;
+      s->use_corr = 0;
+    }
+  }
+}
+
+template <typename T>
+int gs_sum_t(ax_gs *g, T *v, cudaStream_t st);
+template <>
+int gs_sum_t<double>(ax_gs *g, double *v, cudaStream_t st) {
+  return ax_gs_sum(g, v, st);
+}
+template <>
+int gs_sum_t<float>(ax_gs *g, float *v, cudaStream_t st) {
+  return ax_gs_sum_f32(g, v, st);
+}
+
+// Flexible PCG loop (x0 = 0) with the learned correction when M != NULL.
+template <typename T, typename Apply>
+int fcg_loop(ax_poisson *P, const ax_mlp *M, T *x, const T *b, T *r, T *r_old, T *p, T *w,
+             T *corr, const T *mask, const T *minv, const T *c, Apply apply, double tol,
+             int maxit, int *iters, double *relres, int *fallbacks, cudaStream_t st) {
+  const int64_t n = P->n;
+  const unsigned nb = kRedBlocks;
+  const int have = M != nullptr;
+  auto precondition = [&](int first) -> int {
+    if (have) {
+      int rc = ax::mlp_correction<T>(M, corr, r, minv, mask, c, P->nelv, st);
+      if (rc) return rc;
+      if ((rc = gs_sum_t<T>(P->gs, corr, st))) return rc;
+    }
+    fcg_dots_kernel<T><<<nb, kRedThreads, 0, st>>>(r, r_old, corr, minv, c, have, P->partials,
+                                                   n);
+    fcg_beta_kernel<<<1, 128, 0, st>>>(P->partials, nb, P->scal, first, have);
+    fcg_p_kernel<T><<<nb, kRedThreads, 0, st>>>(p, r, minv, corr, P->scal, first, n);
+    return ax::launch_status();
+  };
+  auto read_scalars = [&]() -> int {
+    if (cudaMemcpyAsync(P->scal_host, P->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return AX_ELAUNCH;
+    return AX_OK;
+  };
+  fcg_init_kernel<T><<<nb, kRedThreads, 0, st>>>(x, r, r_old, b, mask, c, P->partials, n);
+  fcg_rr_kernel<<<1, 32, 0, st>>>(P->partials, nb, P->scal, 1);
+  int rc = precondition(1);
+  if (rc) return rc;
+  if ((rc = read_scalars())) return rc;
+  const double rr0 = P->scal_host->rr0;
+  double rel = rr0 > 0 ? 1.0 : 0.0;
+  int it = 0, status = AX_ENOTCONV;
+  if (rr0 == 0.0 || tol >= 1.0) status = AX_OK;
+  while (status != AX_OK && it < maxit) {
+    if ((rc = apply(w, p, st))) return rc;
+    mask_dot_kernel<T><<<nb, kRedThreads, 0, st>>>(w, p, mask, c, P->partials, n);
+    cg_alpha_kernel<<<1, 32, 0, st>>>(P->partials, nb, P->scal);
+    fcg_update_kernel<T><<<nb, kRedThreads, 0, st>>>(x, r, r_old, p, w, c, P->scal, P->partials,
+                                                     n);
+    fcg_rr_kernel<<<1, 32, 0, st>>>(P->partials, nb, P->scal, 0);
+    ++it;
+    if (it % P->check_every == 0 || it == maxit) {
+      if ((rc = read_scalars())) return rc;
+      if (P->scal_host->status) {
+        status = AX_EBREAKDOWN;
+        break;
+      }
+      rel = std::sqrt(std::max(P->scal_host->rr, 0.0) / rr0);
+      if (rel <= tol) {
+        status = AX_OK;
+        break;
+      }
+    }
+    if ((rc = precondition(0))) return rc;
+  }
+  if ((rc = read_scalars())) return rc;
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  if (fallbacks) *fallbacks = P->scal_host->fallbacks;
+  return status;
+}
+
+int ensure_fcg64(ax_poisson *P) {
+  if (P->r_old) return AX_OK;
+  return alloc(&P->r_old, P->n) | alloc(&P->corr, P->n) ? AX_ENOMEM : AX_OK;
+}
+
+}  // namespace
+
+extern "C" int ax_fcg_solve(ax_poisson *P, const ax_mlp *M, double *x, const double *b,
+                            double tol, int maxit, int *iters, double *relres, int *fallbacks,
+                            void *stream) {
+  if (!P || !x || !b || maxit < 0 || !(tol >= 0)) return AX_EINVAL;
+  if (M && M->n_in != P->lx * P->lx * P->lx) return AX_EINVAL;
+  int rc = ensure_fcg64(P);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  auto A = [P](double *w, const double *u, cudaStream_t s) { return apply_f64(P, w, u, s); };
+  return fcg_loop<double>(P, M, x, b, P->r, P->r_old, P->p, P->w, P->corr, P->mask, P->minv,
+                          P->c, A, tol, maxit, iters, relres, fallbacks, st);
+}
+
+extern "C" int ax_precondition(ax_poisson *P, const ax_mlp *M, double *z, const double *r,
+                               void *stream) {
+  if (!P || !z || !r) return AX_EINVAL;
+  if (M && M->n_in != P->lx * P->lx * P->lx) return AX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = ensure_fcg64(P);
+  if (rc) return rc;
+  if (M) {
+    if ((rc = ax::mlp_correction<double>(M, P->corr, r, P->minv, P->mask, P->c, P->nelv, st)))
+      return rc;
+    if ((rc = ax_gs_sum(P->gs, P->corr, st))) return rc;
+  }
+  // z = minv r (+ corr): reuse the p-update kernel with beta = 0 (first = 1)
+  cudaMemsetAsync(P->scal, 0, sizeof(CgScalars), st);
+  if (M) {
+    const int one = 1;
+    cudaMemcpyAsync(&P->scal->use_corr, &one, sizeof(int), cudaMemcpyHostToDevice, st);
+  }
+  fcg_p_kernel<double><<<kRedBlocks, kRedThreads, 0, st>>>(z, r, P->minv, P->corr, P->scal, 1,
+                                                           P->n);
+  rc = ax::launch_status();
+  if (rc == AX_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = AX_ELAUNCH;
+  return rc;
+}
+
+extern "C" int ax_mpfcg_solve(ax_poisson *P, const ax_mlp *M, int mode, double *x,
+                              const double *b, double tol, double inner_tol, int max_outer,
+                              int max_inner, int *outer_iters, int *inner_iters, double *relres,
+                              int *fallbacks, void *stream) {
+  if (!P || !x || !b || (mode != AX_PREC_F32 && mode != AX_PREC_BF16) || max_outer < 1 ||
+      max_inner < 1 || !(tol >= 0) || !(inner_tol > 0))
+    return AX_EINVAL;
+  if (M && M->n_in != P->lx * P->lx * P->lx) return AX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = ensure_lowp(P, mode == AX_PREC_BF16 ? 2 : 1, st);
+  if (rc) return rc;
+  if (!P->r_old32 && (alloc(&P->r_old32, P->n) | alloc(&P->corr32, P->n))) return AX_ENOMEM;
+  const int64_t n = P->n;
+  const unsigned nb = kRedBlocks;
+  double *sc = reinterpret_cast<double *>(P->scal);
+  auto norm_r = [&](double *out_host) -> int {
+    sum_partials_kernel<<<1, 32, 0, st>>>(P->partials, nb, sc);
+    if (cudaMemcpyAsync(out_host, sc, sizeof(double), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return AX_ELAUNCH;
+    return AX_OK;
+  };
+  cudaMemsetAsync(x, 0, n * sizeof(double), st);
+  cudaMemsetAsync(P->w, 0, n * sizeof(double), st);
+  double rr0 = 0.0, rr = 0.0;
+  residual_kernel<<<nb, kRedThreads, 0, st>>>(P->r64, P->r32, b, P->w, P->mask, P->c,
+                                              P->partials, n);
+  if ((rc = norm_r(&rr0))) return rc;
+  int outer = 0, inner_total = 0, fb_total = 0;
+  double rel = rr0 > 0 ? 1.0 : 0.0;
+  int status = rr0 == 0.0 ? AX_OK : AX_ENOTCONV;
+  auto A32 = [P](float *w, const float *u, cudaStream_t s) { return apply_lowp(P, w, u, s); };
+  while (status != AX_OK && outer < max_outer) {
+    int its = 0, fb = 0;
+    double irel = 0.0;
+    rc = fcg_loop<float>(P, M, P->x32, P->r32, P->w32, P->r_old32, P->p32, P->q32, P->corr32,
+                         P->mask32, P->minv32, P->c32, A32, inner_tol, max_inner, &its, &irel,
+                         &fb, st);
+    inner_total += its;
+    fb_total += fb;
+    if (rc != AX_OK && rc != AX_ENOTCONV) return rc;
+    add_correction_kernel<<<nb, kRedThreads, 0, st>>>(x, P->x32, n);
+    ++outer;
+    if ((rc = apply_f64(P, P->w, x, st))) return rc;
+    residual_kernel<<<nb, kRedThreads, 0, st>>>(P->r64, P->r32, b, P->w, P->mask, P->c,
+                                                P->partials, n);
+    if ((rc = norm_r(&rr))) return rc;
+    rel = std::sqrt(std::max(rr, 0.0) / rr0);
+    if (!std::isfinite(rel)) return AX_EBREAKDOWN;
+    if (rel <= tol) status = AX_OK;
+  }
+  if (outer_iters) *outer_iters = outer;
+  if (inner_iters) *inner_iters = inner_total;
+  if (relres) *relres = rel;
+  if (fallbacks) *fallbacks = fb_total;
+  return status;
+}
+
+// y = a x + b y on device vectors (training-data preparation and utilities).
+namespace {
+__global__ void axpby_kernel(double *__restrict__ y, double a, const double *__restrict__ x,
+                             double b, int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    y[q] = a * x[q] + b * y[q];
+}
+}  // namespace
+
+extern "C" int ax_axpby(double *y, double a, const double *x, double b, int64_t n,
+                        void *stream) {
+  if (n < 0 || (n > 0 && (!y || !x))) return AX_EINVAL;
+  if (n == 0) return AX_OK;
+  axpby_kernel<<<kRedBlocks, kRedThreads, 0, (cudaStream_t)stream>>>(y, a, x, b, n);
+  return ax::launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// Energy-norm training of the learned preconditioner.
+//
+// For CG iterates with residual r_k and error e_k the network is trained to
+// make z(r_k) = minv .* r_k + corr(r_k) close to e_k in the energy norm,
+//   L_k = ||e_k - z(r_k)||_A^2 / ||e_k||_A^2,
+// the norm in which CG measures error.  Every element of the mesh is one
+// training row (so each step uses nelv residual/error element pairs).  With
+// d = e - z and q = mask .* gs(A_L d) the gradient with respect to the
+// network output of element e is dL/dy_e = -2 mask .* c .* s_e .* q_e / ||e||_A^2
+// (gs is self-adjoint, so the adjoint of z = gs(W y) is W gs(.)).
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void energy_features_kernel(float *__restrict__ X, double *__restrict__ s_out,
+                                       const double *__restrict__ r,
+                                       const double *__restrict__ minv, int N) {
+  __shared__ double sh[kRedThreads / 32];
+  __shared__ double s_b;
+  const size_t base = (size_t)blockIdx.x * N;
+  double ss = 0.0;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const double z = minv[base + k] * r[base + k];
+    ss += z * z;
+  }
+  double v[1] = {ss};
+  ax::block_sum<1>(v, sh);
+  if (threadIdx.x == 0) {
+    s_b = sqrt(v[0]);
+    s_out[blockIdx.x] = s_b;
+  }
+  __syncthreads();
+  const double inv = s_b > 0.0 ? 1.0 / s_b : 0.0;
+  for (int k = threadIdx.x; k < N; k += blockDim.x)
+    X[base + k] = (float)(minv[base + k] * r[base + k] * inv);
+}
+
+// d = e - minv r - corr, with corr = mask c s_e Y (corr assembled by gs before)
+__global__ void energy_corr_kernel(double *__restrict__ corr, const float *__restrict__ Y,
+                                   const double *__restrict__ s, const double *__restrict__ mask,
+                                   const double *__restrict__ c, int N, int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    corr[q] = mask[q] * c[q] * s[q / N] * (double)Y[q];
+}
+
+__global__ void energy_diff_kernel(double *__restrict__ d, const double *__restrict__ e,
+                                   const double *__restrict__ r, const double *__restrict__ minv,
+                                   const double *__restrict__ corr, int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    d[q] = e[q] - minv[q] * r[q] - corr[q];
+}
+
+__global__ void energy_dy_kernel(float *__restrict__ dY, const double *__restrict__ q,
+                                 const double *__restrict__ s, const double *__restrict__ mask,
+                                 const double *__restrict__ c, const double *__restrict__ eA,
+                                 int N, int64_t n) {
+  const double scale = eA[0] > 0.0 ? -2.0 / eA[0] : 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x)
+    dY[p] = (float)(scale * mask[p] * c[p] * s[p / N] * q[p]);
+}
+
+__global__ void store_partial_sum_kernel(const double *__restrict__ partials, int nblk,
+                                         double *__restrict__ out) {
+  ax::warp_sum_partials<1>(partials, nblk, out);
+}
+
+}  // namespace
+
+extern "C" int ax_mlp_train_energy(ax_poisson *P, ax_mlp *M, const double *r_set,
+                                   const double *e_set, int K, int epochs, float lr,
+                                   double *final_loss, void *stream) {
+  if (!P || !M || !r_set || !e_set || K < 1 || epochs < 1 || !(lr > 0)) return AX_EINVAL;
+  const int N = P->lx * P->lx * P->lx;
+  if (M->n_in != N) return AX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = P->n;
+  const unsigned nb = kRedBlocks;
+  int rc = ax::mlp_reserve(M, P->nelv);
+  if (rc) return rc;
+  double *s = nullptr, *d = nullptr, *q = nullptr, *corr = nullptr, *eA = nullptr, *Lk = nullptr;
+  rc = alloc(&s, P->nelv) | alloc(&d, n) | alloc(&q, n) | alloc(&corr, n) | alloc(&eA, K) |
+       alloc(&Lk, K);
+  auto cleanup = [&]() {
+    cudaFree(s);
+    cudaFree(d);
+    cudaFree(q);
+    cudaFree(corr);
+    cudaFree(eA);
+    cudaFree(Lk);
+  };
+  if (rc) {
+    cleanup();
+    return AX_ENOMEM;
+  }
+  // ||e_k||_A^2 once per pair
+  for (int k = 0; k < K && rc == AX_OK; ++k) {
+    const double *e = e_set + (size_t)k * n;
+    rc = apply_f64(P, q, e, st);
+    if (rc) break;
+    mask_dot_kernel<double><<<nb, kRedThreads, 0, st>>>(q, e, P->mask, P->c, P->partials, n);
+    store_partial_sum_kernel<<<1, 32, 0, st>>>(P->partials, nb, eA + k);
+  }
+  for (int ep = 0; ep < epochs && rc == AX_OK; ++ep) {
+    for (int k = 0; k < K && rc == AX_OK; ++k) {
+      const double *r = r_set + (size_t)k * n, *e = e_set + (size_t)k * n;
+      energy_features_kernel<<<P->nelv, kRedThreads, 0, st>>>(M->X, s, r, P->minv, N);
+      if ((rc = ax::mlp_train_forward(M, P->nelv, st))) break;
+      energy_corr_kernel<<<nb, kRedThreads, 0, st>>>(corr, M->Y, s, P->mask, P->c, N, n);
+      if ((rc = ax_gs_sum(P->gs, corr, st))) break;
+      energy_diff_kernel<<<nb, kRedThreads, 0, st>>>(d, e, r, P->minv, corr, n);
+      if ((rc = apply_f64(P, q, d, st))) break;
+      mask_dot_kernel<double><<<nb, kRedThreads, 0, st>>>(q, d, P->mask, P->c, P->partials, n);
+      store_partial_sum_kernel<<<1, 32, 0, st>>>(P->partials, nb, Lk + k);
+      energy_dy_kernel<<<nb, kRedThreads, 0, st>>>(M->dY, q, s, P->mask, P->c, eA + k, N, n);
+      if ((rc = ax::mlp_train_backward(M, P->nelv, st))) break;
+      if ((rc = ax::mlp_adam_step(M, lr, st))) break;
+    }
+  }
+  if (rc == AX_OK) rc = ax::mlp_refresh(M, st);
+  std::vector<double> hl(K), he(K);
+  if (rc == AX_OK &&
+      (cudaMemcpyAsync(hl.data(), Lk, K * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+           cudaSuccess ||
+       cudaMemcpyAsync(he.data(), eA, K * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+           cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
+    rc = AX_ELAUNCH;
+  if (rc == AX_OK && final_loss) {
+    double m = 0.0;
+    for (int k = 0; k < K; ++k) m += he[k] > 0 ? hl[k] / he[k] : 0.0;
+    *final_loss = m / K;  // mean relative energy error of the last epoch
+  }
+  cleanup();
+  return rc;
 }

@@ -54,4 +54,12 @@ inline bool ensure_smem(K kernel, size_t bytes) {
   return true;
 }
 
+// Explicitly rounded arithmetic (never contracted by the compiler).
+AX_D double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+AX_D float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+AX_D double add_rn(double a, double b) { return __dadd_rn(a, b); }
+AX_D float add_rn(float a, float b) { return __fadd_rn(a, b); }
+AX_D double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+AX_D float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 }  // namespace ax
