@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--n", type=int, default=32, help="elements per box edge")
     p.add_argument("--lx", type=int, default=8)
     p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--extras", default="modes,sweep,cg,learned,batch",
+                   help="comma list of extra sections to run")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -128,6 +130,8 @@ def source_hash(files):
 
 
 KERNEL_SOURCES = {
+    "ax_df64eo_kernel": ["paper_2506_20994_gb300/csrc/ax_df64_eo.cuh",
+                         "paper_2506_20994_gb300/csrc/df64.cuh"],
     "ax_df64_kernel": ["paper_2506_20994_gb300/csrc/ax_df64.cuh",
                        "paper_2506_20994_gb300/csrc/df64.cuh"],
     "ax_kstep_kernel": ["paper_2506_20994_gb300/csrc/ax_kstep.cuh"],
@@ -283,7 +287,8 @@ def main():
     hbm_peak, peak_src = measured_peaks()
     bytes_alg = 72.0 * lx ** 3 * nel
     achieved = bytes_alg / t_launch / 1e9
-    kname = "ax_df64_kernel" if lx <= 12 else "ax_kstep_kernel"
+    kname = ("ax_df64eo_kernel" if lx in (8, 10, 12) else
+             "ax_df64_kernel" if lx <= 12 else "ax_kstep_kernel")
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
             "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
             "traffic": ncu_traffic(kname, lx, nel), "kernel": kname,
@@ -309,8 +314,10 @@ def main():
     del dd, hp
 
     extras = {}
-    if not args.no_extras:
-        extras = run_extras(ax, host, d, lx, nel, stream, hbm_peak)
+    if not args.no_extras and rank == 0:
+        from bench_extras import run_extras
+        extras = run_extras(ax, host, d, lx, nel, stream, hbm_peak,
+                            set(x for x in args.extras.split(",") if x))
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "GDOF/s", "n_gpus": world,
@@ -337,39 +344,6 @@ def main():
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
-
-
-def run_extras(ax, host, d, lx, nel, stream, hbm_peak):
-    """fp32 / bf16 storage modes and the fp64-unit kernel on the same mesh."""
-    import torch
-    out = {}
-    npts = nel * lx ** 3
-    G = [d[k] for k in GKEYS]
-    w64 = torch.empty_like(d["u"])
-
-    def native():
-        ax.ax_helm(w64, d["u"], d["dx"], d["dxt"], d["h1"], *G, lx,
-                   variant=ax.AX_VARIANT_F64_NATIVE)
-    ms, _ = time_region(native, 20, 3, stream)
-    t = ms / 20 * 1e-3
-    out["f64_native"] = {"gdofs": round(npts / t / 1e9, 3), "ms": round(t * 1e3, 4),
-                         "hbm_frac": round(72.0 * lx ** 3 * nel / t / 1e9 / hbm_peak, 4)}
-    del w64
-    for mode, dt, bpp in (("f32", torch.float32, 36), ("bf16", torch.bfloat16, 20)):
-        f = {k: d[k].to(dt) for k in ("u", "h1") + GKEYS}
-        dx32, dxt32 = d["dx"].float(), d["dxt"].float()
-        w = torch.empty(f["u"].shape, dtype=torch.float32, device=d["u"].device)
-        fn = ax.ax_helm_f32 if mode == "f32" else ax.ax_helm_bf16
-
-        def run():
-            fn(w, f["u"], dx32, dxt32, f["h1"], *[f[k] for k in GKEYS], lx)
-        ms, _ = time_region(run, 50, 5, stream)
-        t = ms / 50 * 1e-3
-        out[mode] = {"gdofs": round(npts / t / 1e9, 3), "ms": round(t * 1e3, 4),
-                     "hbm_frac": round(bpp * lx ** 3 * nel / t / 1e9 / hbm_peak, 4),
-                     "bytes_per_point": bpp}
-        del f, w
-    return out
 
 
 if __name__ == "__main__":

@@ -1,0 +1,227 @@
+"""Secondary measurements reported in bench.py's JSON line under "extras".
+
+Each section times one row of the hot path on synthetic, seeded inputs with
+CUDA events (kernels) or wall time around a synchronising solve (solvers):
+
+  modes    fp64-unit, fp32 and bf16 operator kernels on the main mesh
+  sweep    fp64 ax_helm at E in {4096, 32768} x lx in {6, 8, 10, 12}
+  cg       Poisson solve to a 1e-8 relative residual at E = 32768, lx = 8:
+           fp64 Jacobi-CG against fp64 iterative refinement around fp32 and
+           bf16-data inner CG
+  learned  the same target on the variable-coefficient problem: Jacobi
+           flexible CG against the learned element preconditioner (trained
+           here by the library's kernels on residual/error pairs of plain
+           CG on an 8^3 mesh), in fp64 and inside mixed refinement
+  batch    64 meshes, E log-uniform in [64, 8192], lx in {5, 6, 8, 10}: one
+           persistent launch (and its CUDA-graph replay) against one launch
+           per mesh, fp64 and fp32
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+GKEYS = ("g11", "g22", "g33", "g12", "g13", "g23")
+
+
+def _events_ms(fn, reps, warm=2):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _wall(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, out
+
+
+def _mesh_tensors(ax, synth, n, lx, dev, seed=0):
+    import torch
+    v = synth.box_vertices(n, seed=seed)
+    g = ax.box_geometry(v, lx)
+    sh = g["g11"].shape
+    t = lambda a: torch.as_tensor(a, device=dev)
+    d = {"u": t(synth.uniform(sh, seed=seed + 1)), "h1": t(np.ones(sh))}
+    d["dx"], d["dxt"] = (t(a) for a in ax.dmat(lx))
+    for k in GKEYS:
+        d[k] = t(g[k])
+    return d, sh[0]
+
+
+def modes(ax, d, lx, nel, hbm_peak):
+    import torch
+    out = {}
+    npts = nel * lx ** 3
+    G = [d[k] for k in GKEYS]
+    w64 = torch.empty_like(d["u"])
+    for name, var in (("f64_native", ax.AX_VARIANT_F64_NATIVE), ("f64_df", ax.AX_VARIANT_F64_DF),
+                      ("f64_df_eo", ax.AX_VARIANT_F64_DF_EO)):
+        try:
+            ms = _events_ms(lambda: ax.ax_helm(w64, d["u"], d["dx"], d["dxt"], d["h1"], *G, lx,
+                                               variant=var), 10)
+        except ax.AxError:
+            continue
+        out[name] = {"gdofs": round(npts / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 4),
+                     "hbm_frac": round(72.0 * npts / (ms * 1e-3) / 1e9 / hbm_peak, 4)}
+    del w64
+    for mode, dt, bpp in (("f32", torch.float32, 36), ("bf16", torch.bfloat16, 20)):
+        f = {k: d[k].to(dt) for k in ("u", "h1") + GKEYS}
+        dx32, dxt32 = d["dx"].float(), d["dxt"].float()
+        w = torch.empty(f["u"].shape, dtype=torch.float32, device=d["u"].device)
+        fn = ax.ax_helm_f32 if mode == "f32" else ax.ax_helm_bf16
+        ms = _events_ms(lambda: fn(w, f["u"], dx32, dxt32, f["h1"], *[f[k] for k in GKEYS], lx),
+                        30)
+        out[mode] = {"gdofs": round(npts / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 4),
+                     "hbm_frac": round(bpp * npts / (ms * 1e-3) / 1e9 / hbm_peak, 4),
+                     "bytes_per_point": bpp}
+        del f, w
+    return out
+
+
+def sweep(ax, synth, dev, hbm_peak):
+    import torch
+    out = {}
+    for n in (16, 32):
+        for lx in (6, 8, 10, 12):
+            d, nel = _mesh_tensors(ax, synth, n, lx, dev)
+            w = torch.empty_like(d["u"])
+            G = [d[k] for k in GKEYS]
+            ms = _events_ms(lambda: ax.ax_helm(w, d["u"], d["dx"], d["dxt"], d["h1"], *G, lx), 10)
+            npts = nel * lx ** 3
+            out[f"E{nel}_lx{lx}"] = {"gdofs": round(npts / (ms * 1e-3) / 1e9, 2),
+                                     "ms": round(ms, 4),
+                                     "hbm_frac": round(72.0 * npts / (ms * 1e-3) / 1e9 / hbm_peak,
+                                                       4),
+                                     "gdofs_paper_convention": round(
+                                         nel * (lx - 1) ** 3 / (ms * 1e-3) / 1e9, 2)}
+            del d, w
+    return out
+
+
+def cg(ax, synth, oracle_f, dev):
+    v = synth.box_vertices(32, seed=0)
+    P = ax.Poisson(v, 8, device=dev)
+    P.set_check_every(8)
+    b = P.rhs(oracle_f)
+    out = {"workload": "Poisson, f = 3 pi^2 sin sin sin, Dirichlet, E=32768, lx=8, tol 1e-8"}
+    t, (x, its, rel, rc) = _wall(lambda: P.cg(b, tol=1e-8))
+    out["f64_jacobi_cg"] = {"s": round(t, 4), "iters": its, "relres": rel, "status": rc}
+    for name, mode, itol in (("f32_ir", ax.AX_PREC_F32, 1e-4), ("bf16_ir", ax.AX_PREC_BF16, 1e-2)):
+        t2, (x2, no, ni, rel2, rc2) = _wall(lambda: P.mpcg(b, mode=mode, tol=1e-8,
+                                                           inner_tol=itol))
+        t2b, (x2, no, ni, rel2, rc2) = _wall(lambda: P.mpcg(b, mode=mode, tol=1e-8,
+                                                            inner_tol=itol))
+        out[name] = {"s": round(t2b, 4), "first_call_s": round(t2, 4), "outer": no,
+                     "inner_iters": ni, "relres": rel2, "status": rc2,
+                     "speedup_vs_f64_cg": round(t / t2b, 3)}
+    return out
+
+
+def learned(ax, synth, oracle_f, dev):
+    lx = 8
+    coef = ax.fourier_coefficient(1)
+    out = {"workload": "Poisson, variable h1 in [0.5, 2] (8 Fourier modes), E=32768, lx=8, "
+                       "tol 1e-8"}
+    # train on residual/error pairs of plain CG on an 8^3 mesh (element-local
+    # network: it transfers to the larger mesh)
+    Ps = ax.Poisson(synth.box_vertices(8, seed=0), lx, h1=coef, device=dev)
+    bs = Ps.rhs(oracle_f)
+    M = ax.Mlp(lx ** 3, 48, params=ax.mlp_init_params(lx ** 3, 48, seed=1))
+    t_pairs, (R, E) = _wall(lambda: ax.iterate_pairs(Ps, bs))
+    t_train, loss = _wall(lambda: ax.train_energy(Ps, M, R, E, epochs=100, lr=1e-3))
+    out["training"] = {"pairs": int(R.shape[0] * Ps.nelv), "pair_s": round(t_pairs, 3),
+                       "train_s": round(t_train, 3), "final_rel_energy_err": loss}
+    del Ps, R, E
+    P = ax.Poisson(synth.box_vertices(32, seed=0), lx, h1=coef, device=dev)
+    P.set_check_every(8)
+    b = P.rhs(oracle_f)
+    t0, (x, i0, r0, f0, s0) = _wall(lambda: P.fcg(b, None, tol=1e-8))
+    out["f64_jacobi_fcg"] = {"s": round(t0, 4), "iters": i0, "status": s0}
+    t1, (x, i1, r1, f1, s1) = _wall(lambda: P.fcg(b, M, tol=1e-8))
+    out["f64_learned_fcg"] = {"s": round(t1, 4), "iters": i1, "fallbacks": f1, "status": s1}
+    P.mpfcg(b, None, tol=1e-8)  # converts the fp32 operator data once
+    t2, (x, no, ni, r2, f2, s2) = _wall(lambda: P.mpfcg(b, None, tol=1e-8, inner_tol=1e-4))
+    out["f32_ir_jacobi"] = {"s": round(t2, 4), "outer": no, "inner_iters": ni, "status": s2,
+                            "speedup_vs_f64_jacobi": round(t0 / t2, 3)}
+    t3, (x, no, ni, r3, f3, s3) = _wall(lambda: P.mpfcg(b, M, tol=1e-8, inner_tol=1e-4))
+    out["f32_ir_learned"] = {"s": round(t3, 4), "outer": no, "inner_iters": ni,
+                             "fallbacks": f3, "status": s3,
+                             "speedup_vs_f64_jacobi": round(t0 / t3, 3)}
+    return out
+
+
+def batch(ax, synth, dev, hbm_peak):
+    import torch
+    specs = synth.batch_meshes(seed=0)
+    out = {"meshes": len(specs), "elements": int(sum(a * b * c for a, b, c, _ in specs)),
+           "lx_set": sorted({s[3] for s in specs})}
+    for dtype, name, tdt, bpp in ((ax.AX_BATCH_F64, "f64", torch.float64, 72),
+                                  (ax.AX_BATCH_F32, "f32", torch.float32, 36)):
+        meshes = []
+        for q, (nx, ny, nz, lx) in enumerate(specs):
+            v = synth.box_vertices(nx, ny, nz, seed=q)
+            g = ax.box_geometry(v, lx)
+            sh = g["g11"].shape
+            t = lambda a: torch.as_tensor(a, device=dev, dtype=tdt)
+            m = {"lx": lx, "u": t(synth.uniform(sh, seed=100 + q)), "h1": t(np.ones(sh))}
+            m["dx"], m["dxt"] = (t(a) for a in ax.dmat(lx))
+            for k in GKEYS:
+                m[k] = t(g[k])
+            m["w"] = torch.empty_like(m["u"])
+            meshes.append(m)
+        B = ax.Batch(meshes, dtype=dtype)
+        info = B.info()
+        ms_p = _events_ms(lambda: B.launch(), 10)
+        ms_g = _events_ms(lambda: B.launch(graph=True), 10)
+
+        def separate():
+            for m in meshes:
+                args = (m["w"], m["u"], m["dx"], m["dxt"], m["h1"], *[m[k] for k in GKEYS],
+                        m["lx"])
+                (ax.ax_helm if dtype == ax.AX_BATCH_F64 else ax.ax_helm_f32)(*args)
+        ms_s = _events_ms(separate, 5)
+        pts = sum(m["u"].numel() for m in meshes)
+        out[name] = {"persistent_ms": round(ms_p, 4), "graph_ms": round(ms_g, 4),
+                     "separate_launches_ms": round(ms_s, 4),
+                     "gdofs_graph": round(pts / (ms_g * 1e-3) / 1e9, 2),
+                     "hbm_frac_graph": round(bpp * pts / (ms_g * 1e-3) / 1e9 / hbm_peak, 4),
+                     "items": info["items"], "blocks": info["blocks"], "graph_launches": 1,
+                     "kernels_in_graph": len({m["lx"] for m in meshes})}
+        del B, meshes
+    return out
+
+
+def run_extras(ax, host, d, lx, nel, stream, hbm_peak, which):
+    from paper_2506_20994_gb300 import synth
+    dev = d["u"].device
+    out = {}
+    sections = {
+        "modes": lambda: modes(ax, d, lx, nel, hbm_peak),
+        "sweep": lambda: sweep(ax, synth, dev, hbm_peak),
+        "cg": lambda: cg(ax, synth, synth.poisson_source, dev),
+        "learned": lambda: learned(ax, synth, synth.poisson_source, dev),
+        "batch": lambda: batch(ax, synth, dev, hbm_peak),
+    }
+    for name, fn in sections.items():
+        if name not in which:
+            continue
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as exc:  # report, do not lose the main line
+            out[name] = {"error": f"{type(exc).__name__}: {exc}"}
+        out[name + "_wall_s"] = round(time.perf_counter() - t0, 2)
+    return out

@@ -78,6 +78,8 @@ int ax_helm(double *w, const double *u, const double *dx, const double *dxt,
 #define AX_VARIANT_AUTO 0
 #define AX_VARIANT_F64_NATIVE 1 /* fp64 FMA units                           */
 #define AX_VARIANT_F64_DF 2     /* pairs of fp32 (double-float) arithmetic   */
+#define AX_VARIANT_F64_DF_EO 3  /* double-float with the even-odd split of D  */
+                                /* (even lx in 4..12; AX_EINVAL otherwise)    */
 int ax_helm_variant(int variant, double *w, const double *u, const double *dx,
                     const double *dxt, const double *h1, const double *g11,
                     const double *g22, const double *g33, const double *g12,

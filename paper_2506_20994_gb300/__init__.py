@@ -14,14 +14,14 @@ import numpy as np
 
 from . import _lib
 from ._lib import (AX_BATCH_F32, AX_BATCH_F64, AX_PREC_BF16, AX_PREC_F32, AX_VARIANT_AUTO,
-                   AX_VARIANT_F64_DF,
+                   AX_VARIANT_F64_DF, AX_VARIANT_F64_DF_EO,
                    AX_VARIANT_F64_NATIVE, AxError,
                    check, lib)
 
 __all__ = [
     "lib", "AxError", "gll", "dmat", "box_geometry", "box_numbering", "ax_helm",
     "ax_helm_f32", "ax_helm_bf16", "AX_VARIANT_AUTO", "AX_VARIANT_F64_DF",
-    "AX_VARIANT_F64_NATIVE", "df64_roundtrip", "build", "GatherScatter", "Poisson",
+    "AX_VARIANT_F64_NATIVE", "AX_VARIANT_F64_DF_EO", "df64_roundtrip", "build", "GatherScatter", "Poisson",
     "AX_PREC_F32", "AX_PREC_BF16", "Batch", "tune", "tune_set", "tune_get", "AX_BATCH_F64",
     "AX_BATCH_F32", "fourier_coefficient", "Mlp", "mlp_init_params", "training_pairs", "train_mlp", "axpby", "iterate_pairs",
     "train_energy",

@@ -88,6 +88,7 @@ AX_EBREAKDOWN = -6
 AX_VARIANT_AUTO = 0
 AX_VARIANT_F64_NATIVE = 1
 AX_VARIANT_F64_DF = 2
+AX_VARIANT_F64_DF_EO = 3
 AX_PREC_F32 = 1
 AX_PREC_BF16 = 2
 AX_BATCH_F64 = 1

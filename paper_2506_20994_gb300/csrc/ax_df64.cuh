@@ -58,6 +58,12 @@ __device__ __forceinline__ void df64_body(double *__restrict__ w, const double *
   }
   const bool active = own && le < nel;
   const size_t base = (size_t)(active ? e0 + le : 0) * N3 + p;
+  // the geometry is read plane by plane in the k-loop: start all of it towards L2
+  if (active && p < 7 && (N3 * sizeof(double)) % 16 == 0) {
+    const double *f = p == 0 ? g11 : p == 1 ? g22 : p == 2 ? g33 : p == 3 ? g12 : p == 4 ? g13
+                    : p == 5 ? g23 : h1;
+    prefetch_l2(f + (base - p), (unsigned)(N3 * sizeof(double)));
+  }
 
   df2 uk[LX];
   if (own) {

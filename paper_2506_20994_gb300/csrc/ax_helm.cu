@@ -41,12 +41,20 @@ int ax_helm_variant(int variant, double *w, const double *u, const double *dx,
   int rc = check_args(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx, nelv);
   if (rc != AX_OK) return rc > 0 ? AX_OK : rc;
   cudaStream_t st = (cudaStream_t)stream;
+  // measured on GB300 at E = 32768 / 13824 / 8000: the even-odd kernel wins
+  // for lx 8, 10, 12; the k-loop double-float kernel below that; fp64 units
+  // above the double-float instantiations
   if (variant == AX_VARIANT_AUTO)
-    variant = lx <= ax::AX_DF64_LX_MAX ? AX_VARIANT_F64_DF : AX_VARIANT_F64_NATIVE;
+    variant = (lx == 8 || lx == 10 || lx == 12) ? AX_VARIANT_F64_DF_EO
+              : lx <= ax::AX_DF64_LX_MAX        ? AX_VARIANT_F64_DF
+                                                : AX_VARIANT_F64_NATIVE;
   switch (variant) {
     case AX_VARIANT_F64_NATIVE:
       return ax::dispatch_kstep_f64(lx, w, u, dx, dxt, h1, g11, g22, g33, g12,
                                                     g13, g23, nelv, elems_per_block, st);
+    case AX_VARIANT_F64_DF_EO:
+      return ax::dispatch_df64eo(lx, w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nelv,
+                                 elems_per_block, st);
     case AX_VARIANT_F64_DF:
       if (elems_per_block <= 0) elems_per_block = ax::tuned_epb(AX_BATCH_F64, lx);
       return ax::dispatch_df64(lx, w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nelv,

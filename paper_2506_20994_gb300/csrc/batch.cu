@@ -1,81 +1,69 @@
 // Batched element operator over many independent meshes of uneven size and
-// mixed polynomial order in ONE persistent launch (optionally replayed as a
-// CUDA graph), and the autotuner that picks elements per block for each lx.
+// mixed polynomial order, launched as one persistent kernel per polynomial
+// order present (all recorded into one CUDA graph on first replay), and the
+// autotuner that picks elements per block for each lx.
 //
 // The paper's kernel (Listing 2) runs one mesh per launch, and Neko chooses
 // its kernel variant by timing at run time (Sec. "Methodology"); here a
 // host-built plan cuts every mesh into work items of `epb` elements (epb
-// tuned per lx), and a static longest-processing-time-first assignment
-// gives every persistent block a contiguous list of items of about equal
-// cost (cost ~ elements * lx^4).  Blocks walk their own list; there are no
-// atomics and no inter-block waits.  Each item runs the same device body
-// as the single-mesh kernels (ax_df64.cuh / ax_kstep.cuh).
+// tuned per lx), groups the items by lx, and assigns each group's items
+// longest-processing-time-first (cost ~ elements * lx^4) to a fixed set of
+// persistent blocks sized by the occupancy of that group's kernel.  Blocks
+// walk their own contiguous item list; there are no atomics and no
+// inter-block waits.  Each item runs the same device body as the
+// single-mesh kernel (ax_df64.cuh / ax_df64_eo.cuh / ax_kstep.cuh), so the
+// results are bit-identical to ax_helm / ax_helm_f32.  One kernel per lx
+// (rather than one kernel switching over lx) keeps each kernel's register
+// footprint, and so its occupancy, that of its single-mesh counterpart.
 #include <algorithm>
 #include <cstring>
 #include <new>
 #include <queue>
 #include <vector>
 
-#include "ax_df64.cuh"
-#include "ax_kstep.cuh"
+#include "batch_kernels.cuh"
 #include "dispatch.h"
+
+namespace ax {
+int batch_lx_launch_f64(int, int, size_t, const BatchMeshDev *, const BatchItem *, const int *,
+                        cudaStream_t);
+int batch_lx_launch_f32(int, int, size_t, const BatchMeshDev *, const BatchItem *, const int *,
+                        cudaStream_t);
+int batch_lx_setup_f64(int, size_t, int *);
+int batch_lx_setup_f32(int, size_t, int *);
+int batch_lx_launch(bool f64, int lx, int nblocks, size_t smem, const BatchMeshDev *m,
+                    const BatchItem *it, const int *bs, cudaStream_t st) {
+  return f64 ? batch_lx_launch_f64(lx, nblocks, smem, m, it, bs, st)
+             : batch_lx_launch_f32(lx, nblocks, smem, m, it, bs, st);
+}
+int batch_lx_setup(bool f64, int lx, size_t smem, int *bps) {
+  return f64 ? batch_lx_setup_f64(lx, smem, bps) : batch_lx_setup_f32(lx, smem, bps);
+}
+}  // namespace ax
 
 namespace {
 
-struct MeshDev {
-  int lx, epb;
-  void *w;
-  const void *u, *dx, *dxt, *h1, *g[6];
-};
-
-struct Item {
-  int mesh, nel;
-  long long e0;
-};
-
-constexpr int kBatchThreads = 256;
+using ax::BatchItem;
+using ax::BatchMeshDev;
+using ax::kBatchThreads;
 constexpr int kBatchLxMin = 2, kBatchLxMax = 12;
-
-#define AX_BATCH_LX(M) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12)
-
-template <bool F64>
-__global__ void __launch_bounds__(kBatchThreads)
-batch_kernel(const MeshDev *__restrict__ meshes, const Item *__restrict__ items,
-             const int *__restrict__ block_start) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int b0 = block_start[blockIdx.x], b1 = block_start[blockIdx.x + 1];
-  for (int it = b0; it < b1; ++it) {
-    const Item itm = items[it];
-    const MeshDev m = meshes[itm.mesh];
-    switch (m.lx) {
-#define AX_BODY(L)                                                                            \
-  case L:                                                                                     \
-    if (F64)                                                                                  \
-      ax::df64_body<L>((double *)m.w, (const double *)m.u, (const double *)m.dx,              \
-                       (const double *)m.dxt, (const double *)m.h1, (const double *)m.g[0],   \
-                       (const double *)m.g[1], (const double *)m.g[2], (const double *)m.g[3],\
-                       (const double *)m.g[4], (const double *)m.g[5], itm.e0, itm.nel,       \
-                       m.epb, smem_raw);                                                      \
-    else                                                                                      \
-      ax::kstep_body<L, float, float, float, float>(                                          \
-          (float *)m.w, (const float *)m.u, (const float *)m.dx, (const float *)m.dxt,        \
-          (const float *)m.h1, (const float *)m.g[0], (const float *)m.g[1],                  \
-          (const float *)m.g[2], (const float *)m.g[3], (const float *)m.g[4],                \
-          (const float *)m.g[5], itm.e0, itm.nel, m.epb, smem_raw);                           \
-    break;
-      AX_BATCH_LX(AX_BODY)
-#undef AX_BODY
-      default:
-        break;
-    }
-    __syncthreads();  // the next item reuses shared memory
-  }
-}
 
 size_t body_smem(bool f64, int lx, int epb) {
   const size_t n2 = (size_t)lx * lx, n3 = n2 * lx;
+  if (f64 && ax::batch_uses_eo(lx)) {
+    const size_t h = lx / 2;
+    return 2 * h * h * 24 + (size_t)epb * 3 * n2 * (h + 1) * 16;
+  }
   return (2 * n2 + (size_t)epb * 3 * n3) * (f64 ? 8 : 4);
 }
+
+int default_epb(int lx) { return std::max(1, kBatchThreads / (lx * lx)); }
+
+struct Group {
+  int lx = 0, nblocks = 0;
+  size_t smem = 0;
+  int item_off = 0, start_off = 0;  // into d_items / d_start
+};
 
 }  // namespace
 
@@ -93,8 +81,9 @@ struct ax_batch {
   int dtype = 0;
   int nmesh = 0, nitems = 0, nblocks = 0;
   size_t smem = 0;
-  MeshDev *d_mesh = nullptr;
-  Item *d_items = nullptr;
+  std::vector<Group> groups;
+  BatchMeshDev *d_mesh = nullptr;
+  BatchItem *d_items = nullptr;
   int *d_start = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -104,17 +93,14 @@ struct ax_batch {
 namespace {
 
 int batch_launch_raw(ax_batch *B, cudaStream_t st) {
-  if (B->nitems == 0) return AX_OK;
-  if (B->dtype == AX_BATCH_F64)
-    batch_kernel<true><<<B->nblocks, kBatchThreads, B->smem, st>>>(B->d_mesh, B->d_items,
-                                                                   B->d_start);
-  else
-    batch_kernel<false><<<B->nblocks, kBatchThreads, B->smem, st>>>(B->d_mesh, B->d_items,
-                                                                    B->d_start);
-  return ax::launch_status();
+  const bool f64 = B->dtype == AX_BATCH_F64;
+  for (const Group &g : B->groups) {
+    int rc = ax::batch_lx_launch(f64, g.lx, g.nblocks, g.smem, B->d_mesh,
+                                 B->d_items + g.item_off, B->d_start + g.start_off, st);
+    if (rc) return rc;
+  }
+  return AX_OK;
 }
-
-int default_epb(int lx) { return std::max(1, kBatchThreads / (lx * lx)); }
 
 }  // namespace
 
@@ -138,10 +124,10 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
     return AX_EINVAL;
   *out = nullptr;
   const bool f64 = dtype == AX_BATCH_F64;
-  std::vector<MeshDev> mh(nmesh);
-  std::vector<Item> items;
-  std::vector<double> cost;
-  size_t smem = 0;
+  std::vector<BatchMeshDev> mh(nmesh);
+  std::vector<std::vector<BatchItem>> items(kBatchLxMax + 1);
+  std::vector<std::vector<double>> cost(kBatchLxMax + 1);
+  std::vector<size_t> smem(kBatchLxMax + 1, 0);
   double flops = 0, bytes = 0;
   for (int m = 0; m < nmesh; ++m) {
     const ax_batch_mesh &s = meshes[m];
@@ -149,17 +135,24 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
     if (s.nelv > 0 && !ax::all_nonnull(s.w, s.u, s.dx, s.dxt, s.h1, s.g11, s.g22, s.g33, s.g12,
                                        s.g13, s.g23))
       return AX_EINVAL;
-    int epb = ax::tuned_epb(dtype, s.lx);
-    if (epb <= 0) epb = default_epb(s.lx);
-    epb = std::min(epb, kBatchThreads / (s.lx * s.lx));
-    mh[m] = MeshDev{s.lx, epb, s.w, s.u, s.dx, s.dxt, s.h1,
-                    {s.g11, s.g22, s.g33, s.g12, s.g13, s.g23}};
-    smem = std::max(smem, body_smem(f64, s.lx, epb));
+    int epb;
+    if (f64 && ax::batch_uses_eo(s.lx)) {
+      // even-odd body: (lx/2)^3 threads per element, same choice as ax_helm
+      const int h = s.lx / 2;
+      epb = std::max(1, kBatchThreads / (h * h * h));
+    } else {
+      epb = ax::tuned_epb(dtype, s.lx);
+      if (epb <= 0) epb = default_epb(s.lx);
+      epb = std::min(epb, kBatchThreads / (s.lx * s.lx));
+    }
+    mh[m] = BatchMeshDev{s.lx, epb, s.w, s.u, s.dx, s.dxt, s.h1,
+                         {s.g11, s.g22, s.g33, s.g12, s.g13, s.g23}};
+    smem[s.lx] = std::max(smem[s.lx], body_smem(f64, s.lx, epb));
     const double l = s.lx, l3 = l * l * l;
     for (long long e = 0; e < s.nelv; e += epb) {
       const int nel = (int)std::min<long long>(epb, s.nelv - e);
-      items.push_back(Item{m, nel, e});
-      cost.push_back(nel * (l3 * l + 2.0 * l3));
+      items[s.lx].push_back(BatchItem{m, nel, e});
+      cost[s.lx].push_back(nel * (l3 * l + 2.0 * l3));
     }
     flops += (double)s.nelv * (12.0 * l3 * l + 18.0 * l3);
     bytes += (double)s.nelv * 9.0 * l3 * (f64 ? 8 : 4);
@@ -167,60 +160,76 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (blocks_per_sm <= 0) blocks_per_sm = f64 ? 2 : 4;
-  int nblocks = std::max(1, std::min<int>(nsm * blocks_per_sm, (int)items.size()));
-  // longest processing time first onto the least-loaded block
-  std::vector<int> order(items.size());
-  for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-  using Load = std::pair<double, int>;
-  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-  for (int b = 0; b < nblocks; ++b) heap.push({0.0, b});
-  std::vector<std::vector<int>> per(nblocks);
-  for (int q : order) {
-    Load l = heap.top();
-    heap.pop();
-    per[l.second].push_back(q);
-    heap.push({l.first + cost[q], l.second});
-  }
-  std::vector<Item> flat;
-  flat.reserve(items.size());
-  std::vector<int> start(nblocks + 1, 0);
-  for (int b = 0; b < nblocks; ++b) {
-    std::sort(per[b].begin(), per[b].end());  // memory order inside a block
-    for (int q : per[b]) flat.push_back(items[q]);
-    start[b + 1] = (int)flat.size();
+  std::vector<Group> groups;
+  std::vector<BatchItem> flat;
+  std::vector<int> start;
+  size_t smem_max = 0;
+  for (int lx = kBatchLxMin; lx <= kBatchLxMax; ++lx) {
+    if (items[lx].empty()) continue;
+    int bps = 0;
+    int rc = ax::batch_lx_setup(f64, lx, smem[lx], &bps);
+    if (rc) return rc;
+    if (bps < 1) return AX_EINVAL;
+    if (blocks_per_sm > 0) bps = std::min(bps, blocks_per_sm);
+    const int nb = std::max(1, std::min<int>(nsm * bps, (int)items[lx].size()));
+    // longest processing time first onto the least-loaded block
+    std::vector<int> order(items[lx].size());
+    for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return cost[lx][a] > cost[lx][b]; });
+    using Load = std::pair<double, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int b = 0; b < nb; ++b) heap.push({0.0, b});
+    std::vector<std::vector<int>> per(nb);
+    for (int q : order) {
+      Load ld = heap.top();
+      heap.pop();
+      per[ld.second].push_back(q);
+      heap.push({ld.first + cost[lx][q], ld.second});
+    }
+    Group g;
+    g.lx = lx;
+    g.nblocks = nb;
+    g.smem = smem[lx];
+    g.item_off = (int)flat.size();
+    g.start_off = (int)start.size();
+    int cnt = 0;
+    for (int b = 0; b < nb; ++b) {
+      std::sort(per[b].begin(), per[b].end());  // memory order inside a block
+      start.push_back(cnt);
+      for (int q : per[b]) flat.push_back(items[lx][q]), ++cnt;
+    }
+    start.push_back(cnt);
+    groups.push_back(g);
+    smem_max = std::max(smem_max, g.smem);
   }
   ax_batch *B = new (std::nothrow) ax_batch();
   if (!B) return AX_ENOMEM;
   B->dtype = dtype;
   B->nmesh = nmesh;
   B->nitems = (int)flat.size();
-  B->nblocks = nblocks;
-  B->smem = smem;
+  B->groups = groups;
+  for (const Group &g : groups) B->nblocks += g.nblocks;
+  B->smem = smem_max;
   B->flops = flops;
   B->bytes = bytes;
   cudaStream_t st = (cudaStream_t)stream;
-  bool ok = cudaMalloc(&B->d_mesh, std::max<size_t>(1, mh.size()) * sizeof(MeshDev)) ==
+  bool ok = cudaMalloc(&B->d_mesh, std::max<size_t>(1, mh.size()) * sizeof(BatchMeshDev)) ==
                 cudaSuccess &&
-            cudaMalloc(&B->d_items, std::max<size_t>(1, flat.size()) * sizeof(Item)) ==
+            cudaMalloc(&B->d_items, std::max<size_t>(1, flat.size()) * sizeof(BatchItem)) ==
                 cudaSuccess &&
-            cudaMalloc(&B->d_start, start.size() * sizeof(int)) == cudaSuccess;
+            cudaMalloc(&B->d_start, std::max<size_t>(1, start.size()) * sizeof(int)) ==
+                cudaSuccess;
   if (ok && !mh.empty())
-    ok = cudaMemcpyAsync(B->d_mesh, mh.data(), mh.size() * sizeof(MeshDev),
+    ok = cudaMemcpyAsync(B->d_mesh, mh.data(), mh.size() * sizeof(BatchMeshDev),
                          cudaMemcpyHostToDevice, st) == cudaSuccess;
   if (ok && !flat.empty())
-    ok = cudaMemcpyAsync(B->d_items, flat.data(), flat.size() * sizeof(Item),
+    ok = cudaMemcpyAsync(B->d_items, flat.data(), flat.size() * sizeof(BatchItem),
                          cudaMemcpyHostToDevice, st) == cudaSuccess;
-  if (ok)
+  if (ok && !start.empty())
     ok = cudaMemcpyAsync(B->d_start, start.data(), start.size() * sizeof(int),
-                         cudaMemcpyHostToDevice, st) == cudaSuccess &&
-         cudaStreamSynchronize(st) == cudaSuccess;
-  if (ok && smem > 48 * 1024) {
-    ok = cudaFuncSetAttribute(f64 ? batch_kernel<true> : batch_kernel<false>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem) == cudaSuccess;
-  }
+                         cudaMemcpyHostToDevice, st) == cudaSuccess;
+  if (ok) ok = cudaStreamSynchronize(st) == cudaSuccess;
   if (!ok) {
     (void)cudaGetLastError();
     ax_batch_destroy(B);
@@ -243,7 +252,8 @@ int ax_batch_graph_launch(ax_batch *B, void *stream) {
     cudaStream_t cap;
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return AX_ELAUNCH;
     int rc = AX_OK;
-    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = AX_ELAUNCH;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      rc = AX_ELAUNCH;
     if (rc == AX_OK) rc = batch_launch_raw(B, cap);
     cudaGraph_t g = nullptr;
     if (cudaStreamEndCapture(cap, &g) != cudaSuccess) rc = AX_ELAUNCH;

@@ -288,11 +288,8 @@ int alloc(T **p, size_t count) {
 }
 
 int apply_f64(ax_poisson *P, double *w, const double *u, cudaStream_t st) {
-  int rc = ax::dispatch_df64(P->lx, w, u, P->dx, P->dxt, P->h1, P->g[0], P->g[1], P->g[2],
-                             P->g[3], P->g[4], P->g[5], P->nelv, 0, st);
-  if (P->lx > ax::AX_DF64_LX_MAX)
-    rc = ax::dispatch_kstep_f64(P->lx, w, u, P->dx, P->dxt, P->h1, P->g[0], P->g[1], P->g[2],
-                                P->g[3], P->g[4], P->g[5], P->nelv, 0, st);
+  int rc = ax_helm(w, u, P->dx, P->dxt, P->h1, P->g[0], P->g[1], P->g[2], P->g[3], P->g[4],
+                   P->g[5], P->lx, P->nelv, st);
   if (rc) return rc;
   return ax_gs_sum(P->gs, w, st);
 }

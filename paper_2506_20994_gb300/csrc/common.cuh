@@ -54,6 +54,12 @@ inline bool ensure_smem(K kernel, size_t bytes) {
   return true;
 }
 
+// Asks the memory system to bring [p, p + bytes) into L2 (bulk copy engine;
+// p 16-byte aligned, bytes a multiple of 16).  No data is returned.
+AX_D void prefetch_l2(const void *p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Explicitly rounded arithmetic (never contracted by the compiler).
 AX_D double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 AX_D float mul_rn(float a, float b) { return __fmul_rn(a, b); }

@@ -182,5 +182,82 @@ DF_HD df2 mul2(df2 a, df2 b) {
   return o;
 }
 
+// --- packed pairs: two independent double-float lanes per 64-bit register --
+// sm_100-class parts issue add/sub/mul/fma.rn.f32x2 at the fp32 lane rate but
+// in half the issue slots; lane x and lane y are unrelated values.
+#ifdef __CUDACC__
+#define DF_D __device__ __forceinline__
+typedef unsigned long long u64;
+DF_D u64 pk(float x, float y) {
+  return (u64)__float_as_uint(x) | ((u64)__float_as_uint(y) << 32);
+}
+DF_D float lx_(u64 v) { return __uint_as_float((unsigned)(v & 0xFFFFFFFFull)); }
+DF_D float ly_(u64 v) { return __uint_as_float((unsigned)(v >> 32)); }
+DF_D u64 add2(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+DF_D u64 sub2(u64 a, u64 b) {
+  u64 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+DF_D u64 mul2p(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+DF_D u64 fma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// Two double-float values, lane by lane: value_x = lx(hi)+lx(lo), etc.
+struct __align__(16) dd2 {
+  u64 hi, lo;
+};
+// Two running sums of products (heads s, tails c), lane by lane.
+struct acc2 {
+  u64 s, c;
+};
+
+// acc = d * u per lane (first term); nd = -d.hi (precomputed)
+DF_D acc2 prod2(dd2 d, u64 nd, dd2 u) {
+  acc2 a;
+  a.s = mul2p(d.hi, u.hi);
+  const u64 q = fma2(nd, u.hi, a.s);  // s - d.hi*u.hi = -(rounding error)
+  u64 c = fma2(d.hi, u.lo, sub2(pk(0.f, 0.f), q));
+  a.c = fma2(d.lo, u.hi, c);
+  return a;
+}
+
+// acc += d * u per lane: TwoProduct by FMA, TwoSum on the heads, cross terms
+// and both rounding errors into the tails.  nd = -d.hi.
+DF_D void mac2(acc2 &a, dd2 d, u64 nd, dd2 u) {
+  const u64 p = mul2p(d.hi, u.hi);
+  const u64 q = fma2(nd, u.hi, p);  // p - d.hi*u.hi = -(error of p)
+  u64 c = fma2(d.hi, u.lo, a.c);
+  c = fma2(d.lo, u.hi, c);
+  const u64 s = add2(a.s, p);
+  const u64 bp = sub2(s, a.s);
+  const u64 err = add2(sub2(a.s, sub2(s, bp)), sub2(p, bp));
+  a.c = sub2(add2(c, err), q);
+  a.s = s;
+}
+
+// (a + b) per lane, heads by TwoSum, not renormalised
+DF_D dd2 dsum2(dd2 a, dd2 b) {
+  const u64 s = add2(a.hi, b.hi);
+  const u64 bp = sub2(s, a.hi);
+  const u64 err = add2(sub2(a.hi, sub2(s, bp)), sub2(b.hi, bp));
+  dd2 r;
+  r.hi = s;
+  r.lo = add2(add2(a.lo, b.lo), err);
+  return r;
+}
+#endif
+
 }  // namespace df
 }  // namespace ax

@@ -36,6 +36,13 @@ int dispatch_kstep_f32u_bf16(int lx, float *w, const float *u, const float *dx, 
                              const __nv_bfloat16 *g22, const __nv_bfloat16 *g33,
                              const __nv_bfloat16 *g12, const __nv_bfloat16 *g13,
                              const __nv_bfloat16 *g23, int nelv, int epb, cudaStream_t st);
+// Even-odd double-float kernel (lx in {4, 6, 8, 10, 12}; AX_EINVAL otherwise).
+int dispatch_df64eo(int lx, double *w, const double *u, const double *dx, const double *dxt,
+                    const double *h1, const double *g11, const double *g22, const double *g33,
+                    const double *g12, const double *g13, const double *g23, int nelv, int epb,
+                    cudaStream_t st);
+inline bool df64eo_supported(int lx) { return lx >= 4 && lx <= 12 && lx % 2 == 0; }
+
 // fp64-accurate double-float kernel, lx in 2..7 (a), 8..10 (b), 11..12 (c);
 // AX_EINVAL above AX_DF64_LX_MAX.
 #define AX_DF64_DECL(X)                                                                        \

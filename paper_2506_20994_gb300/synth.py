@@ -29,6 +29,7 @@ __all__ = [
     "fourier_modes",
     "batch_meshes",
     "box_dims",
+    "poisson_source",
 ]
 
 
@@ -110,6 +111,13 @@ def fourier_modes(seed: int, n_modes: int = 8, kmax: int = 3):
     k = g.integers(1, kmax + 1, size=(n_modes, 3)).astype(np.float64) * np.pi
     phi = g.uniform(0.0, 2.0 * np.pi, size=n_modes)
     return a, k, phi
+
+
+def poisson_source(x, y, z):
+    """The benchmark's Poisson source f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)
+    (homogeneous Dirichlet data on the unit cube; exact solution
+    sin(pi x) sin(pi y) sin(pi z))."""
+    return 3.0 * np.pi ** 2 * np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
 
 
 def batch_meshes(seed: int, count: int = 64, emin: int = 64, emax: int = 8192,

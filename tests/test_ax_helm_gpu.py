@@ -166,3 +166,40 @@ def test_bad_elements_per_block_rejected():
     case = operator_case((1, 1, 1), 8, seed=1)
     with pytest.raises(ax.AxError):
         _run_f64(case, ax.AX_VARIANT_F64_DF, epb=5)
+
+
+@pytest.mark.parametrize("lx", [4, 6, 8, 10, 12])
+@pytest.mark.parametrize("dims", DIMS, ids=lambda d: "E%d" % (d[0] * d[1] * d[2]))
+def test_f64_even_odd_parity(lx, dims):
+    """The even-odd split of D (even lx) against the oracle."""
+    case = operator_case(dims, lx, seed=50 + lx)
+    w = _run_f64(case, ax.AX_VARIANT_F64_DF_EO)
+    assert rel_l2(w, case["w"]) <= TOL["f64"]
+    assert np.abs(w - case["w"]).max() <= 1e-11 * np.abs(case["w"]).max()
+
+
+def test_f64_even_odd_rejects_odd_lx():
+    case = operator_case((1, 1, 1), 5, seed=1)
+    with pytest.raises(ax.AxError):
+        _run_f64(case, ax.AX_VARIANT_F64_DF_EO)
+
+
+def test_f64_even_odd_adversarial():
+    lx = 8
+    case = operator_case((3, 3, 3), lx, seed=61)
+    const = dict(case)
+    const["u"] = np.full_like(case["u"], -1.5)
+    w = _run_f64(const, ax.AX_VARIANT_F64_DF_EO)
+    assert np.abs(w).max() <= 1e-13 * np.abs(case["w"]).max() * 1.5
+    wide = dict(case)
+    scale = 10.0 ** synth.uniform((case["u"].shape[0], 1, 1, 1), seed=62, lo=-6, hi=6)
+    wide["u"] = case["u"] * scale
+    wide["u"][::4] = 0.0
+    ref = oracle.ax_helm(wide["u"], case["dx"], case["dxt"], case["h1"],
+                         *[case[k] for k in GKEYS], lx)
+    w = _run_f64(wide, ax.AX_VARIANT_F64_DF_EO)
+    per_el = np.linalg.norm((w - ref).reshape(len(ref), -1), axis=1)
+    per_ref = np.linalg.norm(ref.reshape(len(ref), -1), axis=1)
+    nz = per_ref > 0
+    assert np.all(per_el[nz] <= 1e-12 * per_ref[nz])
+    assert np.all(w[::4] == 0.0)
