@@ -23,6 +23,9 @@
 
 namespace ax {
 
+// Bulk L2 prefetch of an element's geometry at the start of the element.
+constexpr bool kPrefetchGeometry = true;
+
 AX_D double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
 AX_D float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
@@ -53,6 +56,12 @@ __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restri
   }
   const bool active = own && le < nel;
   const size_t base = (size_t)(active ? e0 + le : 0) * N3 + p;
+  // the geometry is read plane by plane in the k-loop: start all of it towards L2
+  if (kPrefetchGeometry && active && p < 7 && (N3 * sizeof(S)) % 16 == 0) {
+    const S *f = p == 0 ? g11 : p == 1 ? g22 : p == 2 ? g33 : p == 3 ? g12 : p == 4 ? g13
+               : p == 5 ? g23 : h1;
+    prefetch_l2(f + (base - p), (unsigned)(N3 * sizeof(S)));
+  }
 
   T uk[LX];
   if (own) {

@@ -54,9 +54,12 @@ inline bool ensure_smem(K kernel, size_t bytes) {
   return true;
 }
 
-// Asks the memory system to bring [p, p + bytes) into L2 (bulk copy engine;
-// p 16-byte aligned, bytes a multiple of 16).  No data is returned.
+// Asks the memory system to bring [p, p + bytes) into L2 (bulk copy engine).
+// No data is returned.  The bulk unit needs a 16-byte aligned address and
+// size; anything else (a caller's offset view) is skipped, since a prefetch
+// is only a hint.
 AX_D void prefetch_l2(const void *p, unsigned bytes) {
+  if (((reinterpret_cast<uintptr_t>(p) | bytes) & 15u) != 0) return;
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
