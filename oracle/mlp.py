@@ -99,3 +99,62 @@ def precondition(theta, r, minv, mask, mult, glob, lx, n_hid, gs_sum):
     Y = forward(theta, X, n_hid) * s[:, None]
     corr = (Y.reshape(np.shape(r)) * mask) / mult
     return zr + gs_sum(corr, glob)
+
+
+# ---------------------------------------------------------------------------
+# Symmetric linear form: one shared basis W (n_in x n_hid) per element,
+#   z = D^-1 r + gs(mask * S * W W^T * S * r_e),   S = sqrt(D^-1),
+# a sum over elements of positive semi-definite terms, so z = B r with B
+# symmetric positive definite (usable in plain CG).  Parameters use the same
+# flat layout as above with W1 = W, b1 = 0, W2 = W^T, b2 = 0.
+# ---------------------------------------------------------------------------
+def tie(theta, n_in, n_hid):
+    """Parameters with W2 = W1^T and zero biases (the symmetric form)."""
+    t = np.array(theta, dtype=np.float64)
+    W1, b1, W2, b2 = unpack(t, n_in, n_hid)
+    W2[...] = W1.T
+    b1[...] = 0.0
+    b2[...] = 0.0
+    return t
+
+
+def forward_sym(theta, X, n_hid):
+    """Y = (X W) W^T."""
+    X = np.asarray(X, dtype=np.float64)
+    W1 = unpack(np.asarray(theta, dtype=np.float64), X.shape[1], n_hid)[0]
+    return (X @ W1) @ W1.T
+
+
+def precondition_sym(theta, r, minv, mask, glob, lx, n_hid, gs_sum):
+    """z = D^-1 r + gs(mask * S * (W W^T) (S r)_e), S = sqrt(D^-1)."""
+    n3 = lx ** 3
+    S = np.sqrt(np.asarray(minv))
+    X = (S * np.asarray(r)).reshape(-1, n3)
+    Y = forward_sym(theta, X, n_hid).reshape(np.shape(r))
+    return np.asarray(minv) * np.asarray(r) + gs_sum(mask * S * Y, glob)
+
+
+def energy_loss_grad_sym(theta, pairs, apply_A, dot, minv, mask, glob, lx, n_hid, gs_sum):
+    """Mean relative energy error of the symmetric form over (r, e) pairs,
+    L = mean_k ||e_k - z(r_k)||_A^2 / ||e_k||_A^2, and its gradient with
+    respect to W (returned in the flat layout, zero in b1, W2, b2)."""
+    n3 = lx ** 3
+    n_in = n3
+    W = unpack(np.asarray(theta, dtype=np.float64), n_in, n_hid)[0]
+    S = np.sqrt(np.asarray(minv))
+    L = 0.0
+    gW = np.zeros_like(W)
+    for r, e in pairs:
+        z = precondition_sym(theta, r, minv, mask, glob, lx, n_hid, gs_sum)
+        d = e - z
+        q = apply_A(d)                 # assembled, masked A d
+        eA = dot(e, apply_A(e))
+        L += dot(d, q) / eA
+        X = (S * r).reshape(-1, n3)    # rows: elements
+        G = (-2.0 / eA) * (mask * S * q).reshape(-1, n3)   # dL/dY
+        H = X @ W
+        gW += X.T @ (G @ W) + G.T @ H
+    k = len(pairs)
+    grad = np.zeros(nparams(n_in, n_hid))
+    grad[:n_in * n_hid] = (gW / k).ravel()
+    return L / k, grad
