@@ -9,9 +9,10 @@ CUDA events (kernels) or wall time around a synchronising solve (solvers):
            fp64 Jacobi-CG against fp64 iterative refinement around fp32 and
            bf16-data inner CG
   learned  the same target on the variable-coefficient problem: Jacobi
-           flexible CG against the learned element preconditioner (trained
-           here by the library's kernels on residual/error pairs of plain
-           CG on an 8^3 mesh), in fp64 and inside mixed refinement
+           flexible CG against the learned element preconditioner in its
+           symmetric linear form (trained here by the library's kernels on
+           residual/error pairs of plain CG on an 8^3 mesh), in fp64 and
+           inside mixed refinement
   batch    64 meshes, E log-uniform in [64, 8192], lx in {5, 6, 8, 10}: one
            persistent launch (and its CUDA-graph replay) against one launch
            per mesh, fp64 and fp32
@@ -139,10 +140,13 @@ def learned(ax, synth, oracle_f, dev):
     # network: it transfers to the larger mesh)
     Ps = ax.Poisson(synth.box_vertices(8, seed=0), lx, h1=coef, device=dev)
     bs = Ps.rhs(oracle_f)
-    M = ax.Mlp(lx ** 3, 48, params=ax.mlp_init_params(lx ** 3, 48, seed=1))
-    t_pairs, (R, E) = _wall(lambda: ax.iterate_pairs(Ps, bs))
-    t_train, loss = _wall(lambda: ax.train_energy(Ps, M, R, E, epochs=100, lr=1e-3))
-    out["training"] = {"pairs": int(R.shape[0] * Ps.nelv), "pair_s": round(t_pairs, 3),
+    n_hid = 48
+    M = ax.Mlp(lx ** 3, n_hid, arch=ax.AX_MLP_SYM,
+               params=ax.mlp_init_params(lx ** 3, n_hid, seed=1, arch=ax.AX_MLP_SYM))
+    t_pairs, (R, E) = _wall(lambda: ax.iterate_pairs(Ps, bs, iterates=(2, 4, 8, 16, 32, 64)))
+    t_train, loss = _wall(lambda: ax.train_energy(Ps, M, R, E, epochs=100, lr=5e-3))
+    out["training"] = {"arch": "symmetric linear, n_hid 48", "pairs": int(R.shape[0]),
+                       "elements_per_pair": Ps.nelv, "pair_s": round(t_pairs, 3),
                        "train_s": round(t_train, 3), "final_rel_energy_err": loss}
     del Ps, R, E
     P = ax.Poisson(synth.box_vertices(32, seed=0), lx, h1=coef, device=dev)

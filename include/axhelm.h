@@ -199,9 +199,23 @@ int ax_mpcg_solve(ax_poisson *P, int mode, double *x, const double *b, double to
  * ------------------------------------------------------------------------ */
 typedef struct ax_mlp ax_mlp;
 
+#define AX_MLP_TANH 0 /* the two-layer tanh network above                  */
+#define AX_MLP_SYM 1  /* symmetric linear form (below)                      */
+
 /* Allocates the network (device; parameters start at zero, which makes the
- * preconditioner exactly Jacobi).  n_in in [1, 4096], n_hid in [1, 64]. */
+ * preconditioner exactly Jacobi).  n_in in [1, 4096], n_hid in [1, 64].
+ * ax_mlp_create makes an AX_MLP_TANH network. */
 int ax_mlp_create(ax_mlp **M, int n_in, int n_hid);
+/* Same, with the architecture chosen.  AX_MLP_SYM is the symmetric linear
+ * form with one basis W = W1 (n_in x n_hid) per element and S = sqrt(minv):
+ *   z = minv .* r + gs(mask .* S .* s_e * (x_e W) W^T),
+ *   x_e = (S .* r)_e / s_e,  s_e = ||(S .* r)_e||_2,
+ * i.e. z = B r with B = diag(minv) + sum_e (R_e S)^T W W^T (R_e S), which is
+ * symmetric positive definite for every W (s_e cancels: the map is linear).
+ * It keeps the parameter layout; set_params, adam and train keep W2 = W1^T
+ * and b1 = b2 = 0, and gradients are folded onto W1 (tied weights).
+ * Returns AX_EINVAL for an unknown arch. */
+int ax_mlp_create_ex(ax_mlp **M, int n_in, int n_hid, int arch);
 int ax_mlp_destroy(ax_mlp *M);
 int ax_mlp_nparams(const ax_mlp *M, int64_t *n);
 /* Host fp32 parameter vector in / out (count must equal nparams); set

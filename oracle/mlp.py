@@ -125,6 +125,23 @@ def forward_sym(theta, X, n_hid):
     return (X @ W1) @ W1.T
 
 
+def mse_loss_grad_sym(theta, X, T, n_hid):
+    """Mean-squared loss of Y = (X W) W^T against T and its gradient with
+    respect to the tied W (flat layout; zero in b1, W2, b2)."""
+    X = np.asarray(X, dtype=np.float64)
+    T = np.asarray(T, dtype=np.float64)
+    B, n_in = X.shape
+    W = unpack(np.asarray(theta, dtype=np.float64), n_in, n_hid)[0]
+    H = X @ W
+    R = H @ W.T - T
+    L = float(np.sum(R * R) / (B * n_in))
+    dY = 2.0 * R / (B * n_in)
+    gW = X.T @ (dY @ W) + dY.T @ H      # W appears in both layers
+    grad = np.zeros(nparams(n_in, n_hid))
+    grad[:n_in * n_hid] = gW.ravel()
+    return L, grad
+
+
 def precondition_sym(theta, r, minv, mask, glob, lx, n_hid, gs_sum):
     """z = D^-1 r + gs(mask * S * (W W^T) (S r)_e), S = sqrt(D^-1)."""
     n3 = lx ** 3

@@ -13,7 +13,8 @@ from __future__ import annotations
 import numpy as np
 
 from . import _lib
-from ._lib import (AX_BATCH_F32, AX_BATCH_F64, AX_PREC_BF16, AX_PREC_F32, AX_VARIANT_AUTO,
+from ._lib import (AX_BATCH_F32, AX_BATCH_F64, AX_MLP_SYM, AX_MLP_TANH, AX_PREC_BF16,
+                   AX_PREC_F32, AX_VARIANT_AUTO,
                    AX_VARIANT_F64_DF, AX_VARIANT_F64_DF_EO,
                    AX_VARIANT_F64_NATIVE, AxError,
                    check, lib)
@@ -24,7 +25,7 @@ __all__ = [
     "AX_VARIANT_F64_NATIVE", "AX_VARIANT_F64_DF_EO", "df64_roundtrip", "build", "GatherScatter", "Poisson",
     "AX_PREC_F32", "AX_PREC_BF16", "Batch", "tune", "tune_set", "tune_get", "AX_BATCH_F64",
     "AX_BATCH_F32", "fourier_coefficient", "Mlp", "mlp_init_params", "training_pairs", "train_mlp", "axpby", "iterate_pairs",
-    "train_energy",
+    "train_energy", "AX_MLP_TANH", "AX_MLP_SYM",
 ]
 
 
@@ -423,11 +424,19 @@ def axpby(y, a: float, x, b: float) -> None:
     check("ax_axpby", lib().ax_axpby(y.data_ptr(), a, x.data_ptr(), b, y.numel(), _stream()))
 
 
-def mlp_init_params(n_in: int, n_hid: int, seed: int = 0) -> np.ndarray:
-    """Initial parameters: W1 uniform in +-sqrt(6/(n_in+n_hid)) (Glorot),
-    b1 = 0, and a zero output layer, so the untrained preconditioner is
-    exactly Jacobi.  Random numbers come from ``synth``."""
+def mlp_init_params(n_in: int, n_hid: int, seed: int = 0, arch: int = AX_MLP_TANH,
+                    scale: float = 0.05) -> np.ndarray:
+    """Initial parameters.  Tanh form: W1 uniform in +-sqrt(6/(n_in+n_hid))
+    (Glorot), b1 = 0 and a zero output layer, so the untrained preconditioner
+    is exactly Jacobi.  Symmetric form: W = W1 = W2^T uniform in
+    +-scale/sqrt(n_hid) (the gradient vanishes at W = 0, so W starts small but
+    not zero).  Random numbers come from ``synth``."""
     from . import synth
+    if arch == AX_MLP_SYM:
+        lim = scale / np.sqrt(n_hid)
+        W1 = synth.uniform((n_in, n_hid), seed, -lim, lim)
+        return np.concatenate([W1.ravel(), np.zeros(n_hid), W1.T.ravel(),
+                               np.zeros(n_in)]).astype(np.float32)
     lim = np.sqrt(6.0 / (n_in + n_hid))
     W1 = synth.uniform((n_in, n_hid), seed, -lim, lim)
     return np.concatenate([W1.ravel(), np.zeros(n_hid), np.zeros(n_hid * n_in),
@@ -437,11 +446,11 @@ def mlp_init_params(n_in: int, n_hid: int, seed: int = 0) -> np.ndarray:
 class Mlp:
     """The per-element network of the learned preconditioner (ax_mlp_*)."""
 
-    def __init__(self, n_in: int, n_hid: int = 48, params=None):
+    def __init__(self, n_in: int, n_hid: int = 48, params=None, arch: int = AX_MLP_TANH):
         import ctypes
         h = ctypes.c_void_p()
-        check("ax_mlp_create", lib().ax_mlp_create(ctypes.addressof(h), n_in, n_hid))
-        self._h, self.n_in, self.n_hid = h, n_in, n_hid
+        check("ax_mlp_create_ex", lib().ax_mlp_create_ex(ctypes.addressof(h), n_in, n_hid, arch))
+        self._h, self.n_in, self.n_hid, self.arch = h, n_in, n_hid, arch
         n = ctypes.c_int64()
         check("ax_mlp_nparams", lib().ax_mlp_nparams(h, ctypes.addressof(n)))
         self.nparams = n.value

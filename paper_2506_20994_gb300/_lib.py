@@ -54,6 +54,7 @@ PROTOTYPES = {
     "ax_tune_get": (c_int, [c_int, c_int, P]),
     "ax_jacobi_noalloc": (c_int, [P] * 10 + [c_void_p, c_int, c_int, c_void_p]),
     "ax_mlp_create": (c_int, [P, c_int, c_int]),
+    "ax_mlp_create_ex": (c_int, [P, c_int, c_int, c_int]),
     "ax_mlp_destroy": (c_int, [c_void_p]),
     "ax_mlp_nparams": (c_int, [c_void_p, P]),
     "ax_mlp_set_params": (c_int, [c_void_p, P, c_int64, c_void_p]),
@@ -93,6 +94,8 @@ AX_PREC_F32 = 1
 AX_PREC_BF16 = 2
 AX_BATCH_F64 = 1
 AX_BATCH_F32 = 2
+AX_MLP_TANH = 0
+AX_MLP_SYM = 1
 
 _lib = None
 _lock = threading.Lock()

@@ -1011,13 +1011,14 @@ namespace {
 
 __global__ void energy_features_kernel(float *__restrict__ X, double *__restrict__ s_out,
                                        const double *__restrict__ r,
-                                       const double *__restrict__ minv, int N) {
+                                       const double *__restrict__ minv, int N, int sym) {
   __shared__ double sh[kRedThreads / 32];
   __shared__ double s_b;
   const size_t base = (size_t)blockIdx.x * N;
   double ss = 0.0;
+  auto scale = [&](double mv) { return sym ? sqrt(mv) : mv; };
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    const double z = minv[base + k] * r[base + k];
+    const double z = scale(minv[base + k]) * r[base + k];
     ss += z * z;
   }
   double v[1] = {ss};
@@ -1029,16 +1030,24 @@ __global__ void energy_features_kernel(float *__restrict__ X, double *__restrict
   __syncthreads();
   const double inv = s_b > 0.0 ? 1.0 / s_b : 0.0;
   for (int k = threadIdx.x; k < N; k += blockDim.x)
-    X[base + k] = (float)(minv[base + k] * r[base + k] * inv);
+    X[base + k] = (float)(scale(minv[base + k]) * r[base + k] * inv);
 }
 
 // d = e - minv r - corr, with corr = mask c s_e Y (corr assembled by gs before)
+// output scale of the correction: 1/multiplicity (tanh form) or sqrt(minv)
+// (symmetric form)
+__device__ __forceinline__ double energy_out_scale(const double *c, const double *minv,
+                                                   int64_t q, int sym) {
+  return sym ? sqrt(minv[q]) : c[q];
+}
+
 __global__ void energy_corr_kernel(double *__restrict__ corr, const float *__restrict__ Y,
                                    const double *__restrict__ s, const double *__restrict__ mask,
-                                   const double *__restrict__ c, int N, int64_t n) {
+                                   const double *__restrict__ c, const double *__restrict__ minv,
+                                   int sym, int N, int64_t n) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x)
-    corr[q] = mask[q] * c[q] * s[q / N] * (double)Y[q];
+    corr[q] = mask[q] * energy_out_scale(c, minv, q, sym) * s[q / N] * (double)Y[q];
 }
 
 __global__ void energy_diff_kernel(double *__restrict__ d, const double *__restrict__ e,
@@ -1051,12 +1060,12 @@ __global__ void energy_diff_kernel(double *__restrict__ d, const double *__restr
 
 __global__ void energy_dy_kernel(float *__restrict__ dY, const double *__restrict__ q,
                                  const double *__restrict__ s, const double *__restrict__ mask,
-                                 const double *__restrict__ c, const double *__restrict__ eA,
-                                 int N, int64_t n) {
+                                 const double *__restrict__ c, const double *__restrict__ minv,
+                                 int sym, const double *__restrict__ eA, int N, int64_t n) {
   const double scale = eA[0] > 0.0 ? -2.0 / eA[0] : 0.0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x)
-    dY[p] = (float)(scale * mask[p] * c[p] * s[p / N] * q[p]);
+    dY[p] = (float)(scale * mask[p] * energy_out_scale(c, minv, p, sym) * s[p / N] * q[p]);
 }
 
 __global__ void store_partial_sum_kernel(const double *__restrict__ partials, int nblk,
@@ -1103,17 +1112,22 @@ extern "C" int ax_mlp_train_energy(ax_poisson *P, ax_mlp *M, const double *r_set
   for (int ep = 0; ep < epochs && rc == AX_OK; ++ep) {
     for (int k = 0; k < K && rc == AX_OK; ++k) {
       const double *r = r_set + (size_t)k * n, *e = e_set + (size_t)k * n;
-      energy_features_kernel<<<P->nelv, kRedThreads, 0, st>>>(M->X, s, r, P->minv, N);
+      const int sym = M->arch == AX_MLP_SYM;
+      energy_features_kernel<<<P->nelv, kRedThreads, 0, st>>>(M->X, s, r, P->minv, N, sym);
       if ((rc = ax::mlp_train_forward(M, P->nelv, st))) break;
-      energy_corr_kernel<<<nb, kRedThreads, 0, st>>>(corr, M->Y, s, P->mask, P->c, N, n);
+      energy_corr_kernel<<<nb, kRedThreads, 0, st>>>(corr, M->Y, s, P->mask, P->c, P->minv, sym,
+                                                     N, n);
       if ((rc = ax_gs_sum(P->gs, corr, st))) break;
       energy_diff_kernel<<<nb, kRedThreads, 0, st>>>(d, e, r, P->minv, corr, n);
       if ((rc = apply_f64(P, q, d, st))) break;
       mask_dot_kernel<double><<<nb, kRedThreads, 0, st>>>(q, d, P->mask, P->c, P->partials, n);
       store_partial_sum_kernel<<<1, 32, 0, st>>>(P->partials, nb, Lk + k);
-      energy_dy_kernel<<<nb, kRedThreads, 0, st>>>(M->dY, q, s, P->mask, P->c, eA + k, N, n);
+      energy_dy_kernel<<<nb, kRedThreads, 0, st>>>(M->dY, q, s, P->mask, P->c, P->minv, sym,
+                                                   eA + k, N, n);
       if ((rc = ax::mlp_train_backward(M, P->nelv, st))) break;
+      if (sym && (rc = ax::mlp_tie_grad(M, st))) break;
       if ((rc = ax::mlp_adam_step(M, lr, st))) break;
+      if (sym && (rc = ax::mlp_tie_params(M, st))) break;
     }
   }
   if (rc == AX_OK) rc = ax::mlp_refresh(M, st);

@@ -12,6 +12,7 @@
 // * Training: fp32 SIMT kernels with one thread per output and a fixed
 //   summation order (deterministic, no atomics): forward, mean-squared loss,
 //   backpropagation, Adam (Kingma & Ba 2015).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -68,7 +69,7 @@ AX_D void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t 
 // zeros): W1T [HP][NP] (k contiguous per hidden unit), b1 [HP] (fp32),
 // W2T [NP][HP] (k contiguous per output), b2 [NP] (fp32).
 // Shared memory: xs [kTE][kKC+8] bf16, hs [kTE][HP+8] bf16, s[kTE] fp32.
-template <typename T>
+template <typename T, bool SYM>
 __global__ void __launch_bounds__(kThreads)
 mlp_apply_kernel(T *__restrict__ corr, const T *__restrict__ r, const T *__restrict__ minv,
                  const T *__restrict__ mask, const T *__restrict__ cw,
@@ -84,6 +85,9 @@ mlp_apply_kernel(T *__restrict__ corr, const T *__restrict__ r, const T *__restr
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t4 = lane & 3;
   const long long e0 = (long long)blockIdx.x * kTE;
+  // input scale of the residual and activation of the hidden layer
+  auto in_scale = [](float mv) { return SYM ? sqrtf(mv) : mv; };
+  auto act = [](float a) { return SYM ? a : tanhf(a); };
   const int nel = (int)min((long long)kTE, nelv - e0);
 
   // ---- layer 1: acc = (minv r) W1 over k chunks; also ||minv r||^2 per row
@@ -107,8 +111,9 @@ mlp_apply_kernel(T *__restrict__ corr, const T *__restrict__ r, const T *__restr
       for (int q = 0; q < 16; q += 2) {
         const int k = kc + lcol + q;
         float v0 = 0.f, v1 = 0.f;
-        if (rok && k < N) v0 = to_f32(minv[base + k]) * to_f32(r[base + k]);
-        if (rok && k + 1 < N) v1 = to_f32(minv[base + k + 1]) * to_f32(r[base + k + 1]);
+        if (rok && k < N) v0 = in_scale(to_f32(minv[base + k])) * to_f32(r[base + k]);
+        if (rok && k + 1 < N)
+          v1 = in_scale(to_f32(minv[base + k + 1])) * to_f32(r[base + k + 1]);
         ss += v0 * v0 + v1 * v1;
         *reinterpret_cast<uint32_t *>(&xs[lrow * XS + lcol + q]) = pack_bf16(v0, v1);
       }
@@ -151,9 +156,9 @@ mlp_apply_kernel(T *__restrict__ corr, const T *__restrict__ r, const T *__restr
       const float i1 = s_sh[r1] > 0.f ? 1.f / s_sh[r1] : 0.f;
       const float bb0 = b1[col], bb1 = b1[col + 1];
       *reinterpret_cast<uint32_t *>(&hs[r0 * HS + col]) =
-          pack_bf16(tanhf(acc1[j][0] * i0 + bb0), tanhf(acc1[j][1] * i0 + bb1));
+          pack_bf16(act(acc1[j][0] * i0 + bb0), act(acc1[j][1] * i0 + bb1));
       *reinterpret_cast<uint32_t *>(&hs[r1 * HS + col]) =
-          pack_bf16(tanhf(acc1[j][2] * i1 + bb0), tanhf(acc1[j][3] * i1 + bb1));
+          pack_bf16(act(acc1[j][2] * i1 + bb0), act(acc1[j][3] * i1 + bb1));
     }
   }
   __syncthreads();
@@ -205,7 +210,8 @@ mlp_apply_kernel(T *__restrict__ corr, const T *__restrict__ r, const T *__restr
           if (o >= N) continue;
           const float y = acc2[j][2 * h + c2] + b2[o];
           const size_t q = qb + o;
-          corr[q] = from_f32<T>(to_f32(mask[q]) * to_f32(cw[q]) * sc * y);
+          const float osc = SYM ? sqrtf(to_f32(minv[q])) : to_f32(cw[q]);
+          corr[q] = from_f32<T>(to_f32(mask[q]) * osc * sc * y);
         }
       }
     }
@@ -241,14 +247,15 @@ __global__ void gather_pairs_kernel(float *__restrict__ X, float *__restrict__ T
 
 // H[b][h] = tanh(sum_k X[b][k] W1[k][h] + b1[h])
 __global__ void fwd_hidden_kernel(float *__restrict__ H, const float *__restrict__ X,
-                                  const float *__restrict__ theta, int B, int N, int Hd) {
+                                  const float *__restrict__ theta, int B, int N, int Hd,
+                                  int sym) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (int64_t)B * Hd) return;
   const int b = (int)(q / Hd), h = (int)(q % Hd);
   const float *W1 = theta, *b1 = theta + (size_t)N * Hd;
   float a = 0.f;
   for (int k = 0; k < N; ++k) a = fmaf(X[(size_t)b * N + k], W1[(size_t)k * Hd + h], a);
-  H[q] = tanhf(a + b1[h]);
+  H[q] = sym ? a + b1[h] : tanhf(a + b1[h]);
 }
 
 // Y = H W2 + b2; dY = 2 (Y - T) / (B N); per-block partial of sum (Y-T)^2
@@ -308,7 +315,7 @@ __global__ void grad_w2_kernel(float *__restrict__ grad, const float *__restrict
 // dP[b][h] = (sum_o dY[b][o] W2[h][o]) (1 - H[b][h]^2)
 __global__ void back_hidden_kernel(float *__restrict__ dP, const float *__restrict__ dY,
                                    const float *__restrict__ H, const float *__restrict__ theta,
-                                   int B, int N, int Hd) {
+                                   int B, int N, int Hd, int sym) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (int64_t)B * Hd) return;
   const int b = (int)(q / Hd), h = (int)(q % Hd);
@@ -316,7 +323,7 @@ __global__ void back_hidden_kernel(float *__restrict__ dP, const float *__restri
   float a = 0.f;
   for (int o = 0; o < N; ++o) a = fmaf(dY[(size_t)b * N + o], W2[(size_t)h * N + o], a);
   const float hv = H[q];
-  dP[q] = a * (1.f - hv * hv);
+  dP[q] = sym ? a : a * (1.f - hv * hv);
 }
 
 // gW1[k][h] = sum_b X[b][k] dP[b][h]; gb1[h] = sum_b dP[b][h]
@@ -423,6 +430,34 @@ int ensure_capacity(ax_mlp *M, int B) {
   return AX_OK;
 }
 
+// tied weights: gW1[k][h] += gW2[h][k]; gb1 = 0
+__global__ void tie_grad_kernel(float *__restrict__ grad, int N, int Hd) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const float *gW2 = grad + (size_t)N * Hd + Hd;
+  if (q < (int64_t)N * Hd) {
+    const int k = (int)(q / Hd), h = (int)(q % Hd);
+    grad[q] += gW2[(size_t)h * N + k];
+  } else if (q < (int64_t)N * Hd + Hd) {
+    grad[q] = 0.f;
+  }
+}
+// zero the W2 and b2 gradients (after tie_grad_kernel has read them)
+__global__ void zero_tail_kernel(float *__restrict__ grad, int64_t from, int64_t n) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n - from) grad[from + q] = 0.f;
+}
+// W2 = W1^T, b1 = b2 = 0
+__global__ void tie_params_kernel(float *__restrict__ theta, int N, int Hd) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float *b1 = theta + (size_t)N * Hd, *W2 = b1 + Hd, *b2 = W2 + (size_t)Hd * N;
+  if (q < (int64_t)N * Hd) {
+    const int k = (int)(q / Hd), h = (int)(q % Hd);
+    W2[(size_t)h * N + k] = theta[q];
+  }
+  if (q < Hd) b1[q] = 0.f;
+  if (q < N) b2[q] = 0.f;
+}
+
 // rows perm[b] of the sample set -> the batch buffers
 __global__ void gather_rows_kernel(float *__restrict__ X, float *__restrict__ Tt,
                                    const float *__restrict__ Xa, const float *__restrict__ Ta,
@@ -443,13 +478,14 @@ int loss_grad_dev(ax_mlp *M, int B, cudaStream_t st) {
   const int N = M->n_in, Hd = M->n_hid;
   auto blocks = [](int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); };
   const int64_t bn = (int64_t)B * N, bh = (int64_t)B * Hd;
-  fwd_hidden_kernel<<<blocks(bh), kThreads, 0, st>>>(M->H, M->X, M->theta, B, N, Hd);
+  fwd_hidden_kernel<<<blocks(bh), kThreads, 0, st>>>(M->H, M->X, M->theta, B, N, Hd, M->arch);
   fwd_out_loss_kernel<<<blocks(bn), kThreads, 0, st>>>(M->Y, M->dY, M->H, M->T, M->theta, B, N,
                                                        Hd, M->partials);
   sum_partials_kernel2<<<1, 32, 0, st>>>(M->partials, (int)blocks(bn), M->loss_dev);
   grad_w2_kernel<<<blocks((int64_t)Hd * N + N), kThreads, 0, st>>>(M->grad, M->H, M->dY, B, N,
                                                                     Hd);
-  back_hidden_kernel<<<blocks(bh), kThreads, 0, st>>>(M->dP, M->dY, M->H, M->theta, B, N, Hd);
+  back_hidden_kernel<<<blocks(bh), kThreads, 0, st>>>(M->dP, M->dY, M->H, M->theta, B, N, Hd,
+                                                     M->arch);
   grad_w1_kernel<<<blocks((int64_t)N * Hd + Hd), kThreads, 0, st>>>(M->grad, M->X, M->dP, B, N,
                                                                     Hd);
   return ax::launch_status();
@@ -475,7 +511,7 @@ int mlp_train_forward(ax_mlp *M, int B, cudaStream_t st) {
   const int N = M->n_in, Hd = M->n_hid;
   auto blocks = [](int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); };
   fwd_hidden_kernel<<<blocks((int64_t)B * Hd), kThreads, 0, st>>>(M->H, M->X, M->theta, B, N,
-                                                                  Hd);
+                                                                  Hd, M->arch);
   fwd_out_kernel<<<blocks((int64_t)B * N), kThreads, 0, st>>>(M->Y, M->H, M->theta, B, N, Hd);
   return launch_status();
 }
@@ -487,7 +523,7 @@ int mlp_train_backward(ax_mlp *M, int B, cudaStream_t st) {
   grad_w2_kernel<<<blocks((int64_t)Hd * N + N), kThreads, 0, st>>>(M->grad, M->H, M->dY, B, N,
                                                                     Hd);
   back_hidden_kernel<<<blocks((int64_t)B * Hd), kThreads, 0, st>>>(M->dP, M->dY, M->H, M->theta,
-                                                                   B, N, Hd);
+                                                                   B, N, Hd, M->arch);
   grad_w1_kernel<<<blocks((int64_t)N * Hd + Hd), kThreads, 0, st>>>(M->grad, M->X, M->dP, B, N,
                                                                     Hd);
   return launch_status();
@@ -499,6 +535,22 @@ int mlp_adam_step(ax_mlp *M, float lr, cudaStream_t st) {
 
 int mlp_refresh(ax_mlp *M, cudaStream_t st) { return refresh_bf16(M, st); }
 
+int mlp_tie_grad(ax_mlp *M, cudaStream_t st) {
+  const int N = M->n_in, Hd = M->n_hid;
+  const int64_t n1 = (int64_t)N * Hd + Hd;
+  tie_grad_kernel<<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(M->grad, N, Hd);
+  const int64_t rest = M->nparam - n1;
+  zero_tail_kernel<<<(unsigned)((rest + 255) / 256), 256, 0, st>>>(M->grad, n1, M->nparam);
+  return launch_status();
+}
+
+int mlp_tie_params(ax_mlp *M, cudaStream_t st) {
+  const int N = M->n_in, Hd = M->n_hid;
+  const int64_t n = std::max<int64_t>((int64_t)N * Hd, N);
+  tie_params_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(M->theta, N, Hd);
+  return launch_status();
+}
+
 template <typename T>
 int mlp_correction(const ax_mlp *M, T *corr, const T *r, const T *minv, const T *mask,
                    const T *c, int nelv, cudaStream_t st) {
@@ -506,17 +558,15 @@ int mlp_correction(const ax_mlp *M, T *corr, const T *r, const T *minv, const T 
   const Layout L = layout(M);
   const char *base = reinterpret_cast<const char *>(M->theta_bf);
   const size_t smem = ((size_t)kTE * (kKC + 8) + (size_t)kTE * (L.HP + 8)) * 2 + kTE * 4;
-  static bool attr_set = false;
-  if (smem > 48 * 1024 && !attr_set) {
-    if (cudaFuncSetAttribute(mlp_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess) {
-      (void)cudaGetLastError();
-      return AX_EINVAL;
-    }
-    attr_set = true;
+  auto kern = M->arch == AX_MLP_SYM ? mlp_apply_kernel<T, true> : mlp_apply_kernel<T, false>;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess) {
+    (void)cudaGetLastError();
+    return AX_EINVAL;
   }
   const unsigned grid = (unsigned)((nelv + kTE - 1) / kTE);
-  mlp_apply_kernel<T><<<grid, kThreads, smem, st>>>(
+  kern<<<grid, kThreads, smem, st>>>(
       corr, r, minv, mask, c, reinterpret_cast<const __nv_bfloat16 *>(base + L.w1t),
       reinterpret_cast<const float *>(base + L.b1p),
       reinterpret_cast<const __nv_bfloat16 *>(base + L.w2t),
@@ -544,13 +594,16 @@ int ax_mlp_destroy(ax_mlp *M) {
   return AX_OK;
 }
 
-int ax_mlp_create(ax_mlp **out, int n_in, int n_hid) {
-  if (!out || n_in < 1 || n_in > 4096 || n_hid < 1 || n_hid > 64) return AX_EINVAL;
+int ax_mlp_create_ex(ax_mlp **out, int n_in, int n_hid, int arch) {
+  if (!out || n_in < 1 || n_in > 4096 || n_hid < 1 || n_hid > 64 ||
+      (arch != AX_MLP_TANH && arch != AX_MLP_SYM))
+    return AX_EINVAL;
   *out = nullptr;
   ax_mlp *M = new (std::nothrow) ax_mlp();
   if (!M) return AX_ENOMEM;
   M->n_in = n_in;
   M->n_hid = n_hid;
+  M->arch = arch;
   M->nparam = (int64_t)n_in * n_hid + n_hid + (int64_t)n_hid * n_in + n_in;
   const Layout L = layout(M);
   const size_t pb = (size_t)M->nparam * 4;
@@ -569,6 +622,10 @@ int ax_mlp_create(ax_mlp **out, int n_in, int n_hid) {
   return AX_OK;
 }
 
+int ax_mlp_create(ax_mlp **out, int n_in, int n_hid) {
+  return ax_mlp_create_ex(out, n_in, n_hid, AX_MLP_TANH);
+}
+
 int ax_mlp_nparams(const ax_mlp *M, int64_t *n) {
   if (!M || !n) return AX_EINVAL;
   *n = M->nparam;
@@ -585,7 +642,8 @@ int ax_mlp_set_params(ax_mlp *M, const float *host, int64_t count, void *stream)
     return AX_ELAUNCH;
   }
   M->adam_step = 0;
-  int rc = refresh_bf16(M, st);
+  int rc = M->arch == AX_MLP_SYM ? ax::mlp_tie_params(M, st) : AX_OK;
+  if (rc == AX_OK) rc = refresh_bf16(M, st);
   if (rc == AX_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = AX_ELAUNCH;
   return rc;
 }
@@ -612,6 +670,7 @@ int ax_mlp_loss_grad(ax_mlp *M, const float *X, const float *T, int B, double *l
       cudaMemcpyAsync(M->T, T, bn, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return AX_ELAUNCH;
   if ((rc = loss_grad_dev(M, B, st))) return rc;
+  if (M->arch == AX_MLP_SYM && (rc = ax::mlp_tie_grad(M, st))) return rc;
   double l = 0.0;
   if (cudaMemcpyAsync(&l, M->loss_dev, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return AX_ELAUNCH;
@@ -628,6 +687,7 @@ int ax_mlp_adam(ax_mlp *M, float lr, float beta1, float beta2, float eps, void *
   cudaStream_t st = (cudaStream_t)stream;
   int rc = adam_dev(M, lr, beta1, beta2, eps, st);
   if (rc) return rc;
+  if (M->arch == AX_MLP_SYM && (rc = ax::mlp_tie_params(M, st))) return rc;
   return refresh_bf16(M, st);
 }
 
@@ -652,7 +712,9 @@ int ax_mlp_train(ax_mlp *M, const float *X_all, const float *T_all, int nsamples
       gather_rows_kernel<<<batch, kThreads, 0, st>>>(M->X, M->T, X_all, T_all,
                                                      perm + (size_t)ep * nsamples + s0, M->n_in);
       if ((rc = loss_grad_dev(M, batch, st))) return rc;
+      if (M->arch == AX_MLP_SYM && (rc = ax::mlp_tie_grad(M, st))) return rc;
       if ((rc = adam_dev(M, lr, 0.9f, 0.999f, 1e-8f, st))) return rc;
+      if (M->arch == AX_MLP_SYM && (rc = ax::mlp_tie_params(M, st))) return rc;
     }
   }
   if ((rc = refresh_bf16(M, st))) return rc;

@@ -169,3 +169,120 @@ def test_energy_training_gain_on_held_out_pairs():
         el = _energy_rel_err(P, P.precondition(r, M), e)
         gains.append(ej - el)
     assert np.mean(gains) > 0.0
+
+
+# ---------------------------------------------------------------------------
+# Symmetric linear form (AX_MLP_SYM)
+# ---------------------------------------------------------------------------
+def _sym_params(n_in, n_hid, seed, scale=1.0):
+    return ax.mlp_init_params(n_in, n_hid, seed=seed, arch=ax.AX_MLP_SYM, scale=scale)
+
+
+@pytest.mark.parametrize("lx,n_hid", [(4, 16), (6, 24), (8, 48)])
+def test_sym_apply_matches_oracle_and_is_symmetric(lx, n_hid):
+    v = synth.box_vertices(3, 2, 2, seed=lx)
+    P = ax.Poisson(v, lx)
+    O = oracle.Problem(v, lx)
+    theta = _sym_params(lx ** 3, n_hid, seed=lx)
+    M = ax.Mlp(lx ** 3, n_hid, params=theta, arch=ax.AX_MLP_SYM)
+    # set_params keeps the tie exactly
+    W1, b1, W2, b2 = omlp.unpack(M.get_params(), lx ** 3, n_hid)
+    assert np.array_equal(W2, W1.T) and not b1.any() and not b2.any()
+    minv = np.where(O.mask > 0, 1.0 / O.diag, 0.0)
+    cs = []
+    for seed in (5, 6):
+        r = O.mask * oracle.gs_sum(synth.uniform(O.mask.shape, seed=seed), O.glob)
+        z_ref = omlp.precondition_sym(theta.astype(np.float64), r, minv, O.mask, O.glob, lx,
+                                      n_hid, oracle.gs_sum)
+        z = P.precondition(torch.as_tensor(r.ravel(), device="cuda"), M).cpu().numpy()
+        corr_ref = (z_ref - minv * r).ravel()
+        assert np.linalg.norm(corr_ref) > 0.1 * np.linalg.norm(minv * r)
+        assert rel_l2(z - (minv * r).ravel(), corr_ref) <= 2e-2
+        cs.append((r.ravel(), z))
+    (a, Ba), (b, Bb) = cs
+    w = 1.0 / O.mult.ravel()
+    lhs, rhs = np.sum(w * Ba * b), np.sum(w * a * Bb)
+    scale = np.sqrt(np.sum(w * Ba * Ba) * np.sum(w * b * b))
+    assert abs(lhs - rhs) <= 1e-2 * scale
+    assert np.sum(w * Ba * a) > 0
+    # fp32 local apply (no gs): mask .* sqrt(minv) .* (x W) W^T * s_e
+    t = lambda q: torch.as_tensor(np.ascontiguousarray(q).ravel(), device="cuda",
+                                  dtype=torch.float32)
+    out = torch.empty(O.mask.size, dtype=torch.float32, device="cuda")
+    M.forward(out, t(a), t(minv), t(O.mask), t(1.0 / O.mult), P.nelv)
+    S = np.sqrt(minv).ravel()
+    local_ref = omlp.forward_sym(theta.astype(np.float64), (S * a).reshape(-1, lx ** 3),
+                                 n_hid).ravel() * S * O.mask.ravel()
+    assert rel_l2(out.cpu().numpy(), local_ref) <= 2e-2
+
+
+@pytest.mark.parametrize("n_in,n_hid,B", [(64, 16, 40), (512, 48, 300)])
+def test_sym_loss_and_tied_gradient_match_oracle(n_in, n_hid, B):
+    g = synth.rng(n_in + B + 1)
+    theta = _sym_params(n_in, n_hid, seed=B)
+    X = g.normal(size=(B, n_in)).astype(np.float32)
+    T = g.normal(size=(B, n_in)).astype(np.float32)
+    M = ax.Mlp(n_in, n_hid, params=theta, arch=ax.AX_MLP_SYM)
+    L, grad = M.loss_grad(torch.as_tensor(X, device="cuda"), torch.as_tensor(T, device="cuda"))
+    L_ref, g_ref = omlp.mse_loss_grad_sym(theta.astype(np.float64), X, T, n_hid)
+    assert abs(L - L_ref) <= 1e-5 * L_ref
+    assert rel_l2(grad, g_ref) <= 1e-4
+    assert not grad[n_in * n_hid:].any()
+    M.adam(1e-3)
+    W1, b1, W2, b2 = omlp.unpack(M.get_params(), n_in, n_hid)
+    assert np.array_equal(W2, W1.T) and not b1.any() and not b2.any()
+    ref, _, _ = omlp.adam_step(theta.astype(np.float64), grad.astype(np.float64),
+                               np.zeros(theta.size), np.zeros(theta.size), 1, lr=1e-3)
+    nw = n_in * n_hid
+    assert rel_l2(W1.ravel(), ref[:nw]) <= 1e-5
+
+
+def test_sym_energy_loss_and_first_step_match_oracle():
+    """One pair, one pass: the reported loss is the oracle's relative energy
+    error at the initial W, and the first Adam step moves W by lr against
+    the sign of the oracle's energy gradient (Adam's first-step closed form)."""
+    lx, n_hid = 4, 8
+    v = synth.box_vertices(3, 3, 2, seed=11)
+    P = ax.Poisson(v, lx)
+    O = oracle.Problem(v, lx)
+    minv = np.where(O.mask > 0, 1.0 / O.diag, 0.0)
+    r = O.mask * oracle.gs_sum(synth.uniform(O.mask.shape, seed=12), O.glob) / O.mult
+    e = O.mask * oracle.gs_sum(synth.uniform(O.mask.shape, seed=13), O.glob) / O.mult
+    theta = _sym_params(lx ** 3, n_hid, seed=3, scale=0.5)
+    M = ax.Mlp(lx ** 3, n_hid, params=theta, arch=ax.AX_MLP_SYM)
+    t = lambda q: torch.as_tensor(q.reshape(1, -1), device="cuda")
+    lr = 1e-4
+    loss = ax.train_energy(P, M, t(r), t(e), epochs=1, lr=lr)
+    L_ref, g_ref = omlp.energy_loss_grad_sym(theta.astype(np.float64), [(r, e)], O.apply, O.dot,
+                                             minv, O.mask, O.glob, lx, n_hid, oracle.gs_sum)
+    assert abs(loss - L_ref) <= 1e-5 * L_ref
+    nw = lx ** 3 * n_hid
+    step = (theta[:nw].astype(np.float64) - M.get_params()[:nw].astype(np.float64)) / lr
+    big = np.abs(g_ref[:nw]) > 1e-2 * np.abs(g_ref[:nw]).max()
+    assert big.sum() > nw // 4
+    assert np.array_equal(np.sign(step[big]), np.sign(g_ref[:nw][big]))
+    np.testing.assert_allclose(np.abs(step[big]), 1.0, rtol=0, atol=2e-2)
+
+
+def test_sym_trained_preconditioner_cuts_iterations():
+    """Trained on CG iterates of one right-hand side, the symmetric form
+    needs clearly fewer flexible-CG iterations than Jacobi on another
+    right-hand side, in fp64 and inside fp32 refinement."""
+    lx, n_hid = 6, 24
+    P = _var_problem(4, lx, seed=6)
+    b = P.rhs(oracle.poisson_rhs_f)
+    R, E = ax.iterate_pairs(P, b, iterates=(2, 4, 8, 16, 32, 64))
+    M = ax.Mlp(lx ** 3, n_hid, params=_sym_params(lx ** 3, n_hid, seed=1, scale=0.05),
+               arch=ax.AX_MLP_SYM)
+    loss = ax.train_energy(P, M, R, E, epochs=100, lr=5e-3)
+    assert loss < 0.7
+    b2 = P.rhs(ax.fourier_coefficient(9, lo=-1.0, hi=1.0))
+    _, ij, _, _, rcj = P.fcg(b2, None, tol=1e-8)
+    x, il, rel, fb, rc = P.fcg(b2, M, tol=1e-8)
+    assert rcj == 0 and rc == 0 and rel <= 1e-8 and fb == 0
+    assert il <= 0.8 * ij
+    x2, no, ni, rel2, fb2, rc2 = P.mpfcg(b2, M, tol=1e-8, inner_tol=1e-4)
+    assert rc2 == 0 and rel2 <= 1e-8
+    r2, bf = P.residual(b2, x2).reshape(-1), b2.reshape(-1)
+    c = P.gs.inverse_multiplicity()
+    assert float(torch.sum(c * r2 * r2)) <= (1.5e-8) ** 2 * float(torch.sum(c * bf * bf))

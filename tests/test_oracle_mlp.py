@@ -188,3 +188,26 @@ def test_sym_energy_gradient_matches_central_differences():
                  - mlp.energy_loss_grad_sym(tm, *args)[0]) / (2 * h)
     assert np.linalg.norm(grad[:nw] - fd) <= 1e-6 * np.linalg.norm(fd)
     assert np.linalg.norm(W1) > 0
+
+
+def test_sym_mse_gradient_matches_central_differences():
+    n_in, n_hid, B = 27, 4, 6
+    g = synth.rng(77)
+    theta = mlp.tie(g.normal(0, 0.3, size=mlp.nparams(n_in, n_hid)), n_in, n_hid)
+    X = g.normal(size=(B, n_in))
+    T = g.normal(size=(B, n_in))
+    L, grad = mlp.mse_loss_grad_sym(theta, X, T, n_hid)
+    assert abs(L - np.mean((mlp.forward_sym(theta, X, n_hid) - T) ** 2)) < 1e-15
+    # the tied form is the general network with W2 = W1^T, b = 0
+    assert abs(L - mlp.loss_and_grad(theta, X, T, n_hid)[0]) > 0  # tanh differs
+    nw = n_in * n_hid
+    fd = np.empty(nw)
+    h = 1e-6
+    for q in range(nw):
+        tp, tm = theta.copy(), theta.copy()
+        tp[q] += h
+        tm[q] -= h
+        fd[q] = (mlp.mse_loss_grad_sym(mlp.tie(tp, n_in, n_hid), X, T, n_hid)[0]
+                 - mlp.mse_loss_grad_sym(mlp.tie(tm, n_in, n_hid), X, T, n_hid)[0]) / (2 * h)
+    assert np.linalg.norm(grad[:nw] - fd) <= 1e-6 * np.linalg.norm(fd)
+    assert not grad[nw:].any()
