@@ -131,10 +131,13 @@ def source_hash(files):
 
 KERNEL_SOURCES = {
     "ax_df64eo_kernel": ["paper_2506_20994_gb300/csrc/ax_df64_eo.cuh",
-                         "paper_2506_20994_gb300/csrc/df64.cuh"],
+                         "paper_2506_20994_gb300/csrc/df64.cuh",
+                         "paper_2506_20994_gb300/csrc/common.cuh"],
     "ax_df64_kernel": ["paper_2506_20994_gb300/csrc/ax_df64.cuh",
-                       "paper_2506_20994_gb300/csrc/df64.cuh"],
-    "ax_kstep_kernel": ["paper_2506_20994_gb300/csrc/ax_kstep.cuh"],
+                       "paper_2506_20994_gb300/csrc/df64.cuh",
+                       "paper_2506_20994_gb300/csrc/common.cuh"],
+    "ax_kstep_kernel": ["paper_2506_20994_gb300/csrc/ax_kstep.cuh",
+                        "paper_2506_20994_gb300/csrc/common.cuh"],
 }
 
 
