@@ -146,6 +146,19 @@ int ax_poisson_destroy(ax_poisson *P);
 int ax_poisson_apply(ax_poisson *P, double *w, const double *u, void *stream);
 /* Device array of the masked inverse Jacobi diagonal, owned by P. */
 int ax_poisson_jacobi(const ax_poisson *P, const double **minv);
+/* The assembled Jacobi diagonal before masking and inversion:
+ * diag = gs(diag_e(A)) over this handle's gather-scatter (exact element
+ * diagonal, reading of the Jacobi preconditioner in the oracle).  diag is a
+ * caller-owned device array of n local points; asynchronous.  With the mesh
+ * split across ranks this is the rank's partial sum at nodes it shares with
+ * another rank; ax_poisson_set_diag takes the fully assembled one back. */
+int ax_poisson_diag(const ax_poisson *P, double *diag, void *stream);
+/* Replaces the handle's inverse Jacobi diagonal by mask ./ diag (0 where
+ * masked or diag == 0) from a caller-assembled diag (device, n points);
+ * also refreshes the fp32 copy if a mixed-precision solve converted it
+ * already.  Asynchronous; the solvers called afterwards on the same stream
+ * use it. */
+int ax_poisson_set_diag(ax_poisson *P, const double *diag, void *stream);
 /* How often the solvers read the residual norm back (default 1). */
 int ax_poisson_set_check_every(ax_poisson *P, int every);
 
@@ -297,6 +310,27 @@ int ax_tune_get(int dtype, int lx, int *elems_per_block);
 
 /* y = a x + b y on device fp64 vectors of n values (asynchronous). */
 int ax_axpby(double *y, double a, const double *x, double b, int64_t n, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Vector kernels of the partitioned solve (the paper runs one mesh on one
+ * device; splitting the element set across ranks couples them only through
+ * the gather-scatter sum at shared nodes and the dot products of CG).
+ * ------------------------------------------------------------------------ */
+#define AX_DOT_WORK 608 /* doubles of device scratch ax_dot_weighted needs */
+
+/* *out = sum_q wgt[q] a[q] b[q] (device arrays of n doubles; out a device
+ * double; work caller-owned device scratch of AX_DOT_WORK doubles).  Fixed
+ * grid and order: bitwise reproducible.  Asynchronous; n == 0 writes 0. */
+int ax_dot_weighted(const double *a, const double *b, const double *wgt, int64_t n,
+                    double *work, double *out, void *stream);
+/* out[q] = v[idx[q]], q < n (device arrays; idx int64 in range).  Packs the
+ * values at shared nodes (one representative local copy each) to send. */
+int ax_gather(double *out, const double *v, const int64_t *idx, int64_t n, void *stream);
+/* v[idx[q]] += vals[pos[q]], q < n (device arrays): adds the received
+ * values of shared nodes to every local copy.  idx must hold distinct
+ * entries (no two threads update one point). */
+int ax_scatter_add(double *v, const double *vals, const int64_t *idx, const int64_t *pos,
+                   int64_t n, void *stream);
 
 /* Preconditioner application z = minv .* r (+ learned correction if M is
  * not NULL; M's n_in must be lx^3) for fp64 local vectors; synchronises. */

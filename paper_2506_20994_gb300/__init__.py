@@ -240,7 +240,11 @@ class Poisson:
 
     GKEYS = ("g11", "g22", "g33", "g12", "g13", "g23")
 
-    def __init__(self, vertices: np.ndarray, lx: int, h1=None, device=None):
+    def __init__(self, vertices: np.ndarray, lx: int, h1=None, device=None,
+                 dirichlet=(True, True, True, True, True, True)):
+        """dirichlet: which faces (x0, x1, y0, y1, z0, z1) carry the
+        homogeneous Dirichlet condition; a face left open is an interface to
+        another partition (see ``dist``)."""
         import ctypes
         import torch
         self.device = torch.device("cuda") if device is None else torch.device(device)
@@ -256,10 +260,14 @@ class Poisson:
         n = lx - 1
         NX, NY, NZ = nx * n + 1, ny * n + 1, nz * n + 1
         X, Y, Z = glob % NX, (glob // NX) % NY, glob // (NX * NY)
-        on = (X == 0) | (X == NX - 1) | (Y == 0) | (Y == NY - 1) | (Z == 0) | (Z == NZ - 1)
+        fx0, fx1, fy0, fy1, fz0, fz1 = dirichlet
+        on = ((fx0 & (X == 0)) | (fx1 & (X == NX - 1)) | (fy0 & (Y == 0)) | (fy1 & (Y == NY - 1))
+              | (fz0 & (Z == 0)) | (fz1 & (Z == NZ - 1)))
         mask = np.where(on, 0.0, 1.0)
         if callable(h1):
             h1 = h1(self.xyz[..., 0], self.xyz[..., 1], self.xyz[..., 2])
+        if h1 is not None and np.size(h1) == mask.size:
+            h1 = np.reshape(h1, mask.shape)
         h1v = np.ones_like(mask) if h1 is None else np.broadcast_to(
             np.asarray(h1, dtype=np.float64), mask.shape).copy()
         t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=self.device)
@@ -300,6 +308,17 @@ class Poisson:
         check("ax_poisson_jacobi", lib().ax_poisson_jacobi(self._h, ctypes.addressof(p)))
         n = int(np.prod(self.shape))
         return torch.as_tensor(_DeviceArray(p.value, n, "<f8", self), device=self.device)
+
+    def diag(self):
+        """Assembled (over this handle's nodes), unmasked Jacobi diagonal."""
+        import torch
+        d = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        check("ax_poisson_diag", lib().ax_poisson_diag(self._h, d.data_ptr(), _stream()))
+        return d
+
+    def set_diag(self, d) -> None:
+        """Use mask ./ d as the inverse Jacobi diagonal (d assembled by the caller)."""
+        check("ax_poisson_set_diag", lib().ax_poisson_set_diag(self._h, d.data_ptr(), _stream()))
 
     def set_check_every(self, k: int) -> None:
         check("ax_poisson_set_check_every", lib().ax_poisson_set_check_every(self._h, k))

@@ -55,6 +55,11 @@ PROTOTYPES = {
     "ax_jacobi_noalloc": (c_int, [P] * 10 + [c_void_p, c_int, c_int, c_void_p]),
     "ax_mlp_create": (c_int, [P, c_int, c_int]),
     "ax_mlp_create_ex": (c_int, [P, c_int, c_int, c_int]),
+    "ax_poisson_diag": (c_int, [P, P, P]),
+    "ax_poisson_set_diag": (c_int, [P, P, P]),
+    "ax_dot_weighted": (c_int, [P, P, P, c_int64, P, P, P]),
+    "ax_gather": (c_int, [P, P, P, c_int64, P]),
+    "ax_scatter_add": (c_int, [P, P, P, P, c_int64, P]),
     "ax_mlp_destroy": (c_int, [c_void_p]),
     "ax_mlp_nparams": (c_int, [c_void_p, P]),
     "ax_mlp_set_params": (c_int, [c_void_p, P, c_int64, c_void_p]),
@@ -96,6 +101,7 @@ AX_BATCH_F64 = 1
 AX_BATCH_F32 = 2
 AX_MLP_TANH = 0
 AX_MLP_SYM = 1
+AX_DOT_WORK = 608
 
 _lib = None
 _lock = threading.Lock()

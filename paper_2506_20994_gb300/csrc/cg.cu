@@ -496,6 +496,30 @@ int ax_poisson_apply(ax_poisson *P, double *w, const double *u, void *stream) {
   return ax::launch_status();
 }
 
+int ax_poisson_diag(const ax_poisson *P, double *diag, void *stream) {
+  if (!P || !diag) return AX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = P->n;
+  jacobi_diag_kernel<<<blocks_for(n, 256), 256, 0, st>>>(diag, P->dx, P->h1, P->g[0], P->g[1],
+                                                         P->g[2], P->g[3], P->g[4], P->g[5],
+                                                         P->lx, n);
+  int rc = ax::launch_status();
+  if (rc == AX_OK) rc = ax_gs_sum(P->gs, diag, st);
+  return rc;
+}
+
+int ax_poisson_set_diag(ax_poisson *P, const double *diag, void *stream) {
+  if (!P || !diag) return AX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = P->n;
+  precond_kernel<<<blocks_for(n, 256), 256, 0, st>>>(P->minv, P->cm, diag, P->mask, P->c, n);
+  if (P->minv32) {  // fp32 copies of the refinement solve, if converted already
+    to_f32_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(P->minv32, P->minv, n);
+    to_f32_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(P->cm32, P->cm, n);
+  }
+  return ax::launch_status();
+}
+
 int ax_poisson_jacobi(const ax_poisson *P, const double **minv) {
   if (!P || !minv) return AX_EINVAL;
   *minv = P->minv;
