@@ -99,6 +99,33 @@ int ax_helm_bf16(float *w, const ax_bf16 *u, const float *dx, const float *dxt,
                  const ax_bf16 *g23, int lx, int nelv, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Operator handle for repeated applies on one mesh (the paper's interface
+ * passes an opaque handle first, Listing 1; here it owns per-mesh state).
+ * The operator is ax_helm's: w = Ax(u) in fp64 (element-local, no gs).
+ * ------------------------------------------------------------------------ */
+typedef struct ax_op ax_op;
+
+/* Creates the handle.  dx, dxt, h1 and G are borrowed device arrays in
+ * ax_helm's conventions and must outlive the handle.  For lx in {6, 8, 10,
+ * 12} the handle also converts the geometry once into the even-odd
+ * kernel's prepared order (device memory of 56 lx^3 bytes per element,
+ * owned; the same 8 bytes per value, split into double-float pairs exactly
+ * as the on-the-fly kernel splits them; results agree with
+ * AX_VARIANT_F64_DF_EO to ~1e-16 relative, the pointwise step running two
+ * points per packed instruction).  Synchronises stream.  Returns
+ * AX_EINVAL on bad arguments, AX_ENOMEM when the copy cannot be allocated. */
+int ax_op_create(ax_op **op, int lx, int nelv, const double *dx, const double *dxt,
+                 const double *h1, const double *g11, const double *g22, const double *g33,
+                 const double *g12, const double *g13, const double *g23, void *stream);
+/* w = Ax(u) (device, nelv lx^3 doubles; w must not alias u); asynchronous. */
+int ax_op_apply(ax_op *op, double *w, const double *u, void *stream);
+/* New coefficient h1 (borrowed; the prepared copy is refreshed on stream). */
+int ax_op_set_h1(ax_op *op, const double *h1, void *stream);
+/* Whether the geometry is prepared and how many device bytes that holds. */
+int ax_op_info(const ax_op *op, int *prepared, int64_t *device_bytes);
+int ax_op_destroy(ax_op *op);
+
+/* ------------------------------------------------------------------------
  * Gather-scatter (direct-stiffness summation; Sec. "Neko and Small Tensor
  * Kernel" names it as the second main ingredient beside the small matrix
  * products): every local copy of a global node receives the sum over all

@@ -25,7 +25,7 @@ __all__ = [
     "AX_VARIANT_F64_NATIVE", "AX_VARIANT_F64_DF_EO", "df64_roundtrip", "build", "GatherScatter", "Poisson",
     "AX_PREC_F32", "AX_PREC_BF16", "Batch", "tune", "tune_set", "tune_get", "AX_BATCH_F64",
     "AX_BATCH_F32", "fourier_coefficient", "Mlp", "mlp_init_params", "training_pairs", "train_mlp", "axpby", "iterate_pairs",
-    "train_energy", "AX_MLP_TANH", "AX_MLP_SYM",
+    "train_energy", "AX_MLP_TANH", "AX_MLP_SYM", "Operator",
 ]
 
 
@@ -173,6 +173,41 @@ class _DeviceArray:
         self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
                                          "data": (int(ptr), False), "version": 3,
                                          "strides": None}
+
+
+class Operator:
+    """The element operator of one mesh for repeated applies (ax_op_*).
+    Keeps references to the borrowed device arrays; for lx in {6, 8, 10, 12}
+    the library holds the geometry in the even-odd kernel's prepared order."""
+
+    def __init__(self, lx: int, dx, dxt, h1, g11, g22, g33, g12, g13, g23):
+        import ctypes
+        self.lx, self.nelv = lx, h1.numel() // lx ** 3
+        self._keep = [dx, dxt, h1, g11, g22, g33, g12, g13, g23]
+        h = ctypes.c_void_p()
+        check("ax_op_create", lib().ax_op_create(
+            ctypes.addressof(h), lx, self.nelv, *[t.data_ptr() for t in self._keep],
+            _stream()))
+        self._h = h
+
+    def apply(self, w, u) -> None:
+        check("ax_op_apply", lib().ax_op_apply(self._h, w.data_ptr(), u.data_ptr(), _stream()))
+
+    def set_h1(self, h1) -> None:
+        check("ax_op_set_h1", lib().ax_op_set_h1(self._h, h1.data_ptr(), _stream()))
+        self._keep[2] = h1
+
+    def info(self):
+        import ctypes
+        p, b = ctypes.c_int(), ctypes.c_int64()
+        check("ax_op_info", lib().ax_op_info(self._h, ctypes.addressof(p), ctypes.addressof(b)))
+        return {"prepared": bool(p.value), "device_bytes": b.value}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib._lib is not None:
+            _lib._lib.ax_op_destroy(h)
+            self._h = None
 
 
 class GatherScatter:

@@ -21,7 +21,21 @@
 // back, broadcast across the threads sharing a line.  The same happens for
 // the geometry-weighted gradient before the transposed contractions.  No
 // fp64 instruction is issued.
+//
+// The geometry of the pointwise step comes either from the fp64 arrays
+// (split on the fly, one point at a time) or from a prepared copy in this
+// kernel's own order (eo_prepare_kernel), which the pointwise step consumes
+// two points at a time (a = 0, 1: i' and N-i') as the two lanes of packed
+// double-float arithmetic.  The prepared order is, per element, per
+// corner pair (c, b), per field (g11, g22, g33, g12, g13, g23, h1), per
+// thread, one 16-byte entry {hi(a=0), hi(a=1), lo(a=0), lo(a=1)}: the same
+// 8 bytes per value and the same split, but no conversion instructions and
+// coalesced 16-byte loads.  (The packed pointwise step rounds its tail sums
+// in another order than the scalar one, so the two paths agree to ~1e-16
+// relative, not bit for bit.)
 #pragma once
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "df64.cuh"
@@ -39,6 +53,25 @@ constexpr int dir_entries() {
   return LX * LX * line_stride<LX>();
 }
 
+// 16-byte entries of one element's prepared geometry
+template <int LX>
+constexpr int prep_entries() {
+  return 4 * 7 * (LX / 2) * (LX / 2) * (LX / 2);
+}
+
+// geometry in flight: 7 fields of one corner (fp64 arrays) or of one corner
+// pair (prepared)
+template <bool PREP>
+struct GeoStage;
+template <>
+struct GeoStage<false> {
+  double v[7];
+};
+template <>
+struct GeoStage<true> {
+  df::dd2 v[7];
+};
+
 }  // namespace eo
 
 template <int LX>
@@ -49,7 +82,7 @@ constexpr size_t df64eo_smem(int epb) {
   return 2 * H2 * (16 + 8) + (size_t)epb * 3 * eo::dir_entries<LX>() * 16;
 }
 
-template <int LX>
+template <int LX, bool PREP = false>
 __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double *__restrict__ u,
                                             const double *__restrict__ dx,
                                             const double *__restrict__ dxt,
@@ -59,7 +92,8 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
                                             const double *__restrict__ g33,
                                             const double *__restrict__ g12,
                                             const double *__restrict__ g13,
-                                            const double *__restrict__ g23, long long e0,
+                                            const double *__restrict__ g23,
+                                            const df::dd2 *__restrict__ gp, long long e0,
                                             int nel, int epb, unsigned char *smem_raw) {
   static_assert(LX % 2 == 0, "even-odd kernel needs an even lx");
   using namespace df;
@@ -100,10 +134,16 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
   const bool active = own && le < nel;
   const size_t eb = (size_t)(active ? e0 + le : 0) * N3;
   // the geometry of this element is read only in phase 3: start it towards L2 now
+  const size_t ep = (size_t)(active ? e0 + le : 0) * eo::prep_entries<LX>();
   if (active && t < 7) {
-    const double *f = t == 0 ? g11 : t == 1 ? g22 : t == 2 ? g33 : t == 3 ? g12 : t == 4 ? g13
-                    : t == 5 ? g23 : h1;
-    prefetch_l2(f + eb, (unsigned)(N3 * sizeof(double)));
+    if constexpr (PREP) {  // the element's prepared block, in 7 equal pieces
+      prefetch_l2(gp + ep + (size_t)t * (eo::prep_entries<LX>() / 7),
+                  (unsigned)(N3 * sizeof(double)));
+    } else {
+      const double *f = t == 0 ? g11 : t == 1 ? g22 : t == 2 ? g33 : t == 3 ? g12
+                      : t == 4 ? g13 : t == 5 ? g23 : h1;
+      prefetch_l2(f + eb, (unsigned)(N3 * sizeof(double)));
+    }
   }
   auto gidx = [&](int c, int b, int a) {
     const int k = c ? N - kp : kp, j = b ? N - jp : jp, i = a ? N - ip : ip;
@@ -158,18 +198,24 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
   }
   __syncthreads();
 
-  // geometry of corner q = (c, b, a) = bits of q; two corners in flight
-  auto load_geo = [&](int q, double (&g)[7]) {
-    const size_t x = gidx((q >> 2) & 1, (q >> 1) & 1, q & 1);
-    g[0] = __ldg(g11 + x);
-    g[1] = __ldg(g22 + x);
-    g[2] = __ldg(g33 + x);
-    g[3] = __ldg(g12 + x);
-    g[4] = __ldg(g13 + x);
-    g[5] = __ldg(g23 + x);
-    g[6] = __ldg(h1 + x);
+  // geometry of corner pair q = (c, b) (prepared) or of corner q = (c, b, a)
+  // (fp64 arrays); two in flight
+  auto load_geo = [&](int q, eo::GeoStage<PREP> &g) {
+    if constexpr (PREP) {
+      const dd2 *src = gp + ep + (size_t)q * 7 * H3 + t;
+#pragma unroll
+      for (int f = 0; f < 7; ++f) {
+        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(src + (size_t)f * H3));
+        g.v[f] = dd2{v.x, v.y};
+      }
+    } else {
+      const size_t x = gidx((q >> 2) & 1, (q >> 1) & 1, q & 1);
+      const double *fld[7] = {g11, g22, g33, g12, g13, g23, h1};
+#pragma unroll
+      for (int f = 0; f < 7; ++f) g.v[f] = __ldg(fld[f] + x);
+    }
   };
-  double geo[2][7];
+  eo::GeoStage<PREP> geo[2];
   if (active) load_geo(0, geo[0]);
 
   // ---- phase 2: reference gradient at the eight points
@@ -189,35 +235,79 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
       for (int a = 0; a < 2; ++a) contract(At + lt(b, a), cf, cn, kp, gt[0][b][a], gt[1][b][a]);
   }
 
-  // ---- phase 3: pointwise h1 G, the next corner's geometry loading meanwhile
-  if (own) {
+  // ---- phase 3: pointwise h1 G, the next geometry loading meanwhile
+  if constexpr (PREP) {  // point pairs a = 0, 1 as packed lanes
+    if (own) {
+      const u64 zero = pk(0.f, 0.f);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int c = (q >> 2) & 1, b = (q >> 1) & 1, a = q & 1;
-      if (active && q + 1 < 8) load_geo(q + 1, geo[(q + 1) & 1]);
-      df2 wr{0.f, 0.f}, ws{0.f, 0.f}, wt{0.f, 0.f};
-      if (active) {
-        const double(&g)[7] = geo[q & 1];
-        const df2 a11 = split(g[0]), a22 = split(g[1]), a33 = split(g[2]);
-        const df2 a12 = split(g[3]), a13 = split(g[4]), a23 = split(g[5]);
-        const df2 hh = split(g[6]);
-        const df2 ur = gr[c][b][a], us = gs_[c][b][a], ut = gt[c][b][a];
-        acc sum = prod(a11, ur);
-        mac(sum, a12, us);
-        mac(sum, a13, ut);
-        wr = mul2(hh, df2{sum.s, sum.c});
-        sum = prod(a12, ur);
-        mac(sum, a22, us);
-        mac(sum, a23, ut);
-        ws = mul2(hh, df2{sum.s, sum.c});
-        sum = prod(a13, ur);
-        mac(sum, a23, us);
-        mac(sum, a33, ut);
-        wt = mul2(hh, df2{sum.s, sum.c});
+      for (int cp = 0; cp < 4; ++cp) {
+        const int c = cp >> 1, b = cp & 1;
+        if (active && cp + 1 < 4) load_geo(cp + 1, geo[(cp + 1) & 1]);
+        dd2 WR{zero, zero}, WS{zero, zero}, WT{zero, zero};
+        if (active) {
+          const eo::GeoStage<PREP> &g = geo[cp & 1];
+          const dd2 UR{pk(gr[c][b][0].hi, gr[c][b][1].hi), pk(gr[c][b][0].lo, gr[c][b][1].lo)};
+          const dd2 US{pk(gs_[c][b][0].hi, gs_[c][b][1].hi),
+                       pk(gs_[c][b][0].lo, gs_[c][b][1].lo)};
+          const dd2 UT{pk(gt[c][b][0].hi, gt[c][b][1].hi), pk(gt[c][b][0].lo, gt[c][b][1].lo)};
+          const u64 nR = sub2(zero, UR.hi), nS = sub2(zero, US.hi), nT = sub2(zero, UT.hi);
+          const dd2 &G11 = g.v[0], &G22 = g.v[1], &G33 = g.v[2];
+          const dd2 &G12 = g.v[3], &G13 = g.v[4], &G23 = g.v[5], &HH = g.v[6];
+          const u64 nH = sub2(zero, HH.hi);
+          acc2 a = prod2(UR, nR, G11);
+          mac2(a, US, nS, G12);
+          mac2(a, UT, nT, G13);
+          acc2 m = prod2(HH, nH, dd2{a.s, a.c});
+          WR = dd2{m.s, m.c};
+          a = prod2(UR, nR, G12);
+          mac2(a, US, nS, G22);
+          mac2(a, UT, nT, G23);
+          m = prod2(HH, nH, dd2{a.s, a.c});
+          WS = dd2{m.s, m.c};
+          a = prod2(UR, nR, G13);
+          mac2(a, US, nS, G23);
+          mac2(a, UT, nT, G33);
+          m = prod2(HH, nH, dd2{a.s, a.c});
+          WT = dd2{m.s, m.c};
+        }
+        gr[c][b][0] = df2{lx_(WR.hi), lx_(WR.lo)};
+        gr[c][b][1] = df2{ly_(WR.hi), ly_(WR.lo)};
+        gs_[c][b][0] = df2{lx_(WS.hi), lx_(WS.lo)};
+        gs_[c][b][1] = df2{ly_(WS.hi), ly_(WS.lo)};
+        gt[c][b][0] = df2{lx_(WT.hi), lx_(WT.lo)};
+        gt[c][b][1] = df2{ly_(WT.hi), ly_(WT.lo)};
       }
-      gr[c][b][a] = wr;
-      gs_[c][b][a] = ws;
-      gt[c][b][a] = wt;
+    }
+  } else {  // one point at a time, geometry split on the fly
+    if (own) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int c = (q >> 2) & 1, b = (q >> 1) & 1, a = q & 1;
+        if (active && q + 1 < 8) load_geo(q + 1, geo[(q + 1) & 1]);
+        df2 wr{0.f, 0.f}, ws{0.f, 0.f}, wt{0.f, 0.f};
+        if (active) {
+          const double(&g)[7] = geo[q & 1].v;
+          const df2 a11 = split(g[0]), a22 = split(g[1]), a33 = split(g[2]);
+          const df2 a12 = split(g[3]), a13 = split(g[4]), a23 = split(g[5]);
+          const df2 hh = split(g[6]);
+          const df2 ur = gr[c][b][a], us = gs_[c][b][a], ut = gt[c][b][a];
+          acc sum = prod(a11, ur);
+          mac(sum, a12, us);
+          mac(sum, a13, ut);
+          wr = mul2(hh, df2{sum.s, sum.c});
+          sum = prod(a12, ur);
+          mac(sum, a22, us);
+          mac(sum, a23, ut);
+          ws = mul2(hh, df2{sum.s, sum.c});
+          sum = prod(a13, ur);
+          mac(sum, a23, us);
+          mac(sum, a33, ut);
+          wt = mul2(hh, df2{sum.s, sum.c});
+        }
+        gr[c][b][a] = wr;
+        gs_[c][b][a] = ws;
+        gt[c][b][a] = wt;
+      }
     }
   }
   __syncthreads();  // every thread has read the gradient lines
@@ -286,7 +376,54 @@ ax_df64eo_kernel(double *__restrict__ w, const double *__restrict__ u,
   const long long e0 = (long long)blockIdx.x * epb;
   const long long left = nelv - e0;
   const int nel = left < epb ? (int)left : epb;
-  df64eo_body<LX>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, e0, nel, epb, smem_raw);
+  df64eo_body<LX, false>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nullptr, e0, nel,
+                         epb, smem_raw);
+}
+
+// Same operator on geometry prepared by eo_prepare_kernel.
+template <int LX>
+__global__ void __launch_bounds__(256, 2)
+ax_df64eo_prep_kernel(double *__restrict__ w, const double *__restrict__ u,
+                      const double *__restrict__ dx, const double *__restrict__ dxt,
+                      const df::dd2 *__restrict__ gp, int nelv, int epb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long e0 = (long long)blockIdx.x * epb;
+  const long long left = nelv - e0;
+  const int nel = left < epb ? (int)left : epb;
+  df64eo_body<LX, true>(w, u, dx, dxt, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                        nullptr, gp, e0, nel, epb, smem_raw);
+}
+
+// Prepared geometry: entry ((e*4 + cp)*7 + f)*H3 + t holds field f at the
+// two points a = 0, 1 of corner pair cp = (c, b) of thread t, split into
+// double-float pairs exactly as the kernel above splits them.  fmask selects
+// the fields to (re)write (bit f; bit 6 = h1).
+template <int LX>
+__global__ void eo_prepare_kernel(df::dd2 *__restrict__ gp, const double *__restrict__ h1,
+                                  const double *__restrict__ g11,
+                                  const double *__restrict__ g22,
+                                  const double *__restrict__ g33,
+                                  const double *__restrict__ g12,
+                                  const double *__restrict__ g13,
+                                  const double *__restrict__ g23, int nelv, int fmask) {
+  using namespace df;
+  constexpr int H = LX / 2, N = LX - 1, H3 = H * H * H, N3 = LX * LX * LX;
+  const int64_t total = (int64_t)nelv * eo::prep_entries<LX>();
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(q % H3);
+    const int f = (int)((q / H3) % 7);
+    if (!((fmask >> f) & 1)) continue;
+    const int cp = (int)((q / (7 * H3)) % 4);
+    const int64_t e = q / eo::prep_entries<LX>();
+    const int ip = t % H, jp = (t / H) % H, kp = t / (H * H);
+    const int k = (cp >> 1) ? N - kp : kp, j = (cp & 1) ? N - jp : jp;
+    const double *fld = f == 0 ? g11 : f == 1 ? g22 : f == 2 ? g33 : f == 3 ? g12 : f == 4 ? g13
+                      : f == 5 ? g23 : h1;
+    const size_t row = (size_t)e * N3 + (size_t)(k * LX + j) * LX;
+    const df2 a0 = split(fld[row + ip]), a1 = split(fld[row + N - ip]);
+    gp[q] = dd2{pk(a0.hi, a1.hi), pk(a0.lo, a1.lo)};
+  }
 }
 
 template <int LX>
@@ -311,6 +448,41 @@ int launch_df64eo(double *w, const double *u, const double *dx, const double *dx
   const unsigned grid = (unsigned)((nelv + epb - 1) / epb);
   kern<<<grid, epb * H3, smem, stream>>>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nelv,
                                          epb);
+  return launch_status();
+}
+
+template <int LX>
+int launch_df64eo_prep(double *w, const double *u, const double *dx, const double *dxt,
+                       const df::dd2 *gp, int nelv, int epb, cudaStream_t stream) {
+  constexpr int H3 = (LX / 2) * (LX / 2) * (LX / 2);
+  // measured on GB300 (E = 32768 at lx = 8, 13824 at lx = 10): blocks of
+  // about 128 threads (4 per SM) beat 256-thread blocks by 8-9 %
+  if (epb <= 0) epb = 128 / H3 < 1 ? 1 : 128 / H3;
+  if (epb * H3 > 256) return AX_EINVAL;
+  const size_t smem = df64eo_smem<LX>(epb);
+  auto kern = ax_df64eo_prep_kernel<LX>;
+  static size_t granted = 48 * 1024;
+  if (smem > granted) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      (void)cudaGetLastError();
+      return AX_EINVAL;
+    }
+    granted = smem;
+  }
+  const unsigned grid = (unsigned)((nelv + epb - 1) / epb);
+  kern<<<grid, epb * H3, smem, stream>>>(w, u, dx, dxt, gp, nelv, epb);
+  return launch_status();
+}
+
+template <int LX>
+int launch_eo_prepare(df::dd2 *gp, const double *h1, const double *g11, const double *g22,
+                      const double *g33, const double *g12, const double *g13,
+                      const double *g23, int nelv, int fmask, cudaStream_t stream) {
+  const int64_t total = (int64_t)nelv * eo::prep_entries<LX>();
+  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
+  eo_prepare_kernel<LX><<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, stream>>>(
+      gp, h1, g11, g22, g33, g12, g13, g23, nelv, fmask);
   return launch_status();
 }
 

@@ -19,4 +19,33 @@ int dispatch_df64eo(int lx, double *w, const double *u, const double *dx, const 
   }
 }
 
+int dispatch_df64eo_prep(int lx, double *w, const double *u, const double *dx,
+                         const double *dxt, const df::dd2 *gp, int nelv, int epb,
+                         cudaStream_t st) {
+  switch (lx) {
+#define AX_CASE(L)                                                                             \
+  case L:                                                                                      \
+    return launch_df64eo_prep<L>(w, u, dx, dxt, gp, nelv, epb, st);
+    AX_CASE(4) AX_CASE(6) AX_CASE(8) AX_CASE(10) AX_CASE(12)
+#undef AX_CASE
+    default:
+      return AX_EINVAL;
+  }
+}
+
+int dispatch_eo_prepare(int lx, df::dd2 *gp, const double *h1, const double *g11,
+                        const double *g22, const double *g33, const double *g12,
+                        const double *g13, const double *g23, int nelv, int fmask,
+                        cudaStream_t st) {
+  switch (lx) {
+#define AX_CASE(L)                                                                             \
+  case L:                                                                                      \
+    return launch_eo_prepare<L>(gp, h1, g11, g22, g33, g12, g13, g23, nelv, fmask, st);
+    AX_CASE(4) AX_CASE(6) AX_CASE(8) AX_CASE(10) AX_CASE(12)
+#undef AX_CASE
+    default:
+      return AX_EINVAL;
+  }
+}
+
 }  // namespace ax

@@ -42,8 +42,8 @@ batch_lx_kernel(const BatchMeshDev *__restrict__ meshes, const BatchItem *__rest
       df64eo_body<LX>((double *)m.w, (const double *)m.u, (const double *)m.dx,
                       (const double *)m.dxt, (const double *)m.h1, (const double *)m.g[0],
                       (const double *)m.g[1], (const double *)m.g[2], (const double *)m.g[3],
-                      (const double *)m.g[4], (const double *)m.g[5], itm.e0, itm.nel, m.epb,
-                      smem_raw);
+                      (const double *)m.g[4], (const double *)m.g[5], nullptr, itm.e0,
+                      itm.nel, m.epb, smem_raw);
     } else if constexpr (F64) {
       df64_body<LX>((double *)m.w, (const double *)m.u, (const double *)m.dx,
                     (const double *)m.dxt, (const double *)m.h1, (const double *)m.g[0],

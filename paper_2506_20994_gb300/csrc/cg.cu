@@ -255,6 +255,7 @@ struct ax_poisson {
   int64_t n = 0;
   const double *dx = nullptr, *dxt = nullptr, *h1 = nullptr, *g[6] = {};
   const double *mask = nullptr;
+  ax_op *op = nullptr;  // the operator (prepared geometry where it applies)
   ax_gs *gs = nullptr;
   const double *c = nullptr;  // 1/multiplicity (owned by gs)
   // owned fp64 work
@@ -288,8 +289,7 @@ int alloc(T **p, size_t count) {
 }
 
 int apply_f64(ax_poisson *P, double *w, const double *u, cudaStream_t st) {
-  int rc = ax_helm(w, u, P->dx, P->dxt, P->h1, P->g[0], P->g[1], P->g[2], P->g[3], P->g[4],
-                   P->g[5], P->lx, P->nelv, st);
+  int rc = ax_op_apply(P->op, w, u, st);
   if (rc) return rc;
   return ax_gs_sum(P->gs, w, st);
 }
@@ -426,6 +426,7 @@ int ax_poisson_destroy(ax_poisson *P) {
   cudaFree(P->corr);
   cudaFree(P->r_old32);
   cudaFree(P->corr32);
+  if (P->op) ax_op_destroy(P->op);
   cudaFree(P->scal);
   if (P->scal_host) cudaFreeHost(P->scal_host);
   delete P;
@@ -455,6 +456,11 @@ int ax_poisson_create(ax_poisson **out, int lx, int nelv, const double *dx, cons
   P->gs = gs;
   P->c = ax_gs_inverse_multiplicity(gs);
   const int64_t n = P->n;
+  if (int rco = ax_op_create(&P->op, lx, nelv, dx, dxt, h1, g11, g22, g33, g12, g13, g23,
+                             stream)) {
+    ax_poisson_destroy(P);
+    return rco;
+  }
   int rc = alloc(&P->minv, n) | alloc(&P->cm, n) | alloc(&P->w, n) | alloc(&P->r, n) |
            alloc(&P->p, n) | alloc(&P->partials, 4 * (size_t)kRedBlocks) |
            alloc(&P->scal, 1);

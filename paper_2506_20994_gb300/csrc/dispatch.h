@@ -2,6 +2,8 @@
 // translation unit so that the kernel instantiations compile in parallel.
 #pragma once
 
+#include "df64.cuh"
+
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -42,6 +44,16 @@ int dispatch_df64eo(int lx, double *w, const double *u, const double *dx, const 
                     const double *g12, const double *g13, const double *g23, int nelv, int epb,
                     cudaStream_t st);
 inline bool df64eo_supported(int lx) { return lx >= 4 && lx <= 12 && lx % 2 == 0; }
+// The same kernel on geometry prepared by dispatch_eo_prepare (df::dd2
+// entries, 56 lx^3 bytes per element); fmask picks the fields to write
+// (bits 0-5 g11, g22, g33, g12, g13, g23; bit 6 h1).
+int dispatch_df64eo_prep(int lx, double *w, const double *u, const double *dx,
+                         const double *dxt, const df::dd2 *gp, int nelv, int epb,
+                         cudaStream_t st);
+int dispatch_eo_prepare(int lx, df::dd2 *gp, const double *h1, const double *g11,
+                        const double *g22, const double *g33, const double *g12,
+                        const double *g13, const double *g23, int nelv, int fmask,
+                        cudaStream_t st);
 
 // fp64-accurate double-float kernel, lx in 2..7 (a), 8..10 (b), 11..12 (c);
 // AX_EINVAL above AX_DF64_LX_MAX.
