@@ -94,7 +94,8 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
                                             const double *__restrict__ g13,
                                             const double *__restrict__ g23,
                                             const df::dd2 *__restrict__ gp, long long e0,
-                                            int nel, int epb, unsigned char *smem_raw) {
+                                            int nel, int epb, unsigned char *smem_raw,
+                                            double *__restrict__ dotp = nullptr) {
   static_assert(LX % 2 == 0, "even-odd kernel needs an even lx");
   using namespace df;
   constexpr int H = LX / 2, N = LX - 1;
@@ -329,6 +330,7 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
   }
   __syncthreads();
 
+  double dsum = 0.0;
   // ---- phase 5: transposed half-size contractions, summed, stored
   if (own) {
 #pragma unroll
@@ -357,9 +359,27 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
                           dd2{pk(s0.hi, s1.hi), pk(s0.lo, s1.lo)});
           acc = dsum2(acc, dd2{pk(t0.hi, t1.hi), pk(t0.lo, t1.lo)});
           const df2 w0 = norm(lx_(acc.hi), lx_(acc.lo)), w1 = norm(ly_(acc.hi), ly_(acc.lo));
-          w[gidx(c, b, 0)] = join(w0.hi, w0.lo);
-          w[gidx(c, b, 1)] = join(w1.hi, w1.lo);
+          const double wd0 = join(w0.hi, w0.lo), wd1 = join(w1.hi, w1.lo);
+          w[gidx(c, b, 0)] = wd0;
+          w[gidx(c, b, 1)] = wd1;
+          if (dotp) {  // u . Au of this element (u re-read from L2)
+            dsum = __fma_rn(__ldg(u + gidx(c, b, 0)), wd0, dsum);
+            dsum = __fma_rn(__ldg(u + gidx(c, b, 1)), wd1, dsum);
+          }
         }
+    }
+  }
+  if (dotp) {  // one partial per block, fixed order (block-uniform branch)
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = dsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int k = 0; k < (int)((blockDim.x + 31) / 32); ++k) s += red[k];
+      dotp[blockIdx.x] = s;
     }
   }
 }
@@ -380,18 +400,20 @@ ax_df64eo_kernel(double *__restrict__ w, const double *__restrict__ u,
                          epb, smem_raw);
 }
 
-// Same operator on geometry prepared by eo_prepare_kernel.
-template <int LX>
+// Same operator on geometry prepared by eo_prepare_kernel; DOT adds the
+// per-block partials of u . w.
+template <int LX, bool DOT>
 __global__ void __launch_bounds__(256, 2)
 ax_df64eo_prep_kernel(double *__restrict__ w, const double *__restrict__ u,
                       const double *__restrict__ dx, const double *__restrict__ dxt,
-                      const df::dd2 *__restrict__ gp, int nelv, int epb) {
+                      const df::dd2 *__restrict__ gp, int nelv, int epb,
+                      double *__restrict__ dotp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long e0 = (long long)blockIdx.x * epb;
   const long long left = nelv - e0;
   const int nel = left < epb ? (int)left : epb;
   df64eo_body<LX, true>(w, u, dx, dxt, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                        nullptr, gp, e0, nel, epb, smem_raw);
+                        nullptr, gp, e0, nel, epb, smem_raw, DOT ? dotp : nullptr);
 }
 
 // Prepared geometry: entry ((e*4 + cp)*7 + f)*H3 + t holds field f at the
@@ -451,27 +473,37 @@ int launch_df64eo(double *w, const double *u, const double *dx, const double *dx
   return launch_status();
 }
 
+// dotp (optional): one partial of sum u . w per block, gridDim = ceil(nelv /
+// epb) of them (prep_blocks).
+template <int LX>
+int prep_blocks(int nelv, int epb) {
+  constexpr int H3 = (LX / 2) * (LX / 2) * (LX / 2);
+  if (epb <= 0) epb = 128 / H3 < 1 ? 1 : 128 / H3;
+  return (nelv + epb - 1) / epb;
+}
+
 template <int LX>
 int launch_df64eo_prep(double *w, const double *u, const double *dx, const double *dxt,
-                       const df::dd2 *gp, int nelv, int epb, cudaStream_t stream) {
+                       const df::dd2 *gp, int nelv, int epb, cudaStream_t stream,
+                       double *dotp = nullptr) {
   constexpr int H3 = (LX / 2) * (LX / 2) * (LX / 2);
   // measured on GB300 (E = 32768 at lx = 8, 13824 at lx = 10): blocks of
   // about 128 threads (4 per SM) beat 256-thread blocks by 8-9 %
   if (epb <= 0) epb = 128 / H3 < 1 ? 1 : 128 / H3;
   if (epb * H3 > 256) return AX_EINVAL;
   const size_t smem = df64eo_smem<LX>(epb);
-  auto kern = ax_df64eo_prep_kernel<LX>;
-  static size_t granted = 48 * 1024;
-  if (smem > granted) {
+  auto kern = dotp ? ax_df64eo_prep_kernel<LX, true> : ax_df64eo_prep_kernel<LX, false>;
+  static size_t granted[2] = {48 * 1024, 48 * 1024};
+  if (smem > granted[dotp != nullptr]) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
       (void)cudaGetLastError();
       return AX_EINVAL;
     }
-    granted = smem;
+    granted[dotp != nullptr] = smem;
   }
   const unsigned grid = (unsigned)((nelv + epb - 1) / epb);
-  kern<<<grid, epb * H3, smem, stream>>>(w, u, dx, dxt, gp, nelv, epb);
+  kern<<<grid, epb * H3, smem, stream>>>(w, u, dx, dxt, gp, nelv, epb, dotp);
   return launch_status();
 }
 

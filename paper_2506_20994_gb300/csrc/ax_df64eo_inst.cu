@@ -21,15 +21,26 @@ int dispatch_df64eo(int lx, double *w, const double *u, const double *dx, const 
 
 int dispatch_df64eo_prep(int lx, double *w, const double *u, const double *dx,
                          const double *dxt, const df::dd2 *gp, int nelv, int epb,
-                         cudaStream_t st) {
+                         cudaStream_t st, double *dotp) {
   switch (lx) {
 #define AX_CASE(L)                                                                             \
   case L:                                                                                      \
-    return launch_df64eo_prep<L>(w, u, dx, dxt, gp, nelv, epb, st);
+    return launch_df64eo_prep<L>(w, u, dx, dxt, gp, nelv, epb, st, dotp);
     AX_CASE(4) AX_CASE(6) AX_CASE(8) AX_CASE(10) AX_CASE(12)
 #undef AX_CASE
     default:
       return AX_EINVAL;
+  }
+}
+
+int df64eo_prep_blocks(int lx, int nelv) {
+  switch (lx) {
+    case 4: return prep_blocks<4>(nelv, 0);
+    case 6: return prep_blocks<6>(nelv, 0);
+    case 8: return prep_blocks<8>(nelv, 0);
+    case 10: return prep_blocks<10>(nelv, 0);
+    case 12: return prep_blocks<12>(nelv, 0);
+    default: return 0;
   }
 }
 

@@ -16,10 +16,12 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
 #include "dispatch.h"
+#include "op.h"
 #include "mlp.cuh"
 #include "reduce.cuh"
 
@@ -142,7 +144,9 @@ __global__ void cg_alpha_kernel(const double *__restrict__ partials, int nblk,
 }
 
 // x += alpha p; r -= alpha w; partials rz' = sum cm r^2, rr' = sum c r^2
-template <typename T>
+// MASKW: w is not masked yet (fused apply); the Dirichlet rows, where
+// cm = c * minv is 0, keep r = 0.
+template <typename T, bool MASKW = false>
 __global__ void cg_update_kernel(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
                                  const T *__restrict__ w, const T *__restrict__ cm,
                                  const T *__restrict__ c, const CgScalars *__restrict__ s,
@@ -153,7 +157,7 @@ __global__ void cg_update_kernel(T *__restrict__ x, T *__restrict__ r, const T *
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
     x[q] += alpha * p[q];
-    const T rv = r[q] - alpha * w[q];
+    const T rv = (MASKW && cm[q] == T(0)) ? r[q] : r[q] - alpha * w[q];
     r[q] = rv;
     const T r2 = rv * rv;
     a_rz += cm[q] * r2;
@@ -256,6 +260,8 @@ struct ax_poisson {
   const double *dx = nullptr, *dxt = nullptr, *h1 = nullptr, *g[6] = {};
   const double *mask = nullptr;
   ax_op *op = nullptr;  // the operator (prepared geometry where it applies)
+  double *dotp = nullptr;  // per-block partials of p . Ap from the fused apply
+  int ndot = 0;
   ax_gs *gs = nullptr;
   const double *c = nullptr;  // 1/multiplicity (owned by gs)
   // owned fp64 work
@@ -337,13 +343,27 @@ int pcg_loop(ax_poisson *P, T *x, const T *b, T *r, T *p, T *w, const T *mask, c
     return AX_OK;
   }
   int status = AX_ENOTCONV;
+  // fp64 with prepared geometry: p . Ap comes out of the apply itself (for
+  // a continuous, masked p the assembled dot equals the element-local sum
+  // of p . A_e p), and the mask moves into the update
+  const bool fused = std::is_same<T, double>::value && P->dotp != nullptr;
   while (it < maxit) {
-    int rc = apply(w, p, st);
-    if (rc) return rc;
-    mask_dot_kernel<T><<<nb, kRedThreads, 0, st>>>(w, p, mask, c, P->partials, n);
-    cg_alpha_kernel<<<1, 32, 0, st>>>(P->partials, nb, P->scal);
-    cg_update_kernel<T><<<nb, kRedThreads, 0, st>>>(x, r, p, w, cm, c, P->scal, P->partials,
-                                                    n);
+    int rc;
+    if (fused) {
+      rc = ax::op_apply_dot(P->op, (double *)w, (const double *)p, P->dotp, st);
+      if (rc == AX_OK) rc = ax_gs_sum(P->gs, (double *)w, st);
+      if (rc) return rc;
+      cg_alpha_kernel<<<1, 32, 0, st>>>(P->dotp, P->ndot, P->scal);
+      cg_update_kernel<T, true><<<nb, kRedThreads, 0, st>>>(x, r, p, w, cm, c, P->scal,
+                                                            P->partials, n);
+    } else {
+      rc = apply(w, p, st);
+      if (rc) return rc;
+      mask_dot_kernel<T><<<nb, kRedThreads, 0, st>>>(w, p, mask, c, P->partials, n);
+      cg_alpha_kernel<<<1, 32, 0, st>>>(P->partials, nb, P->scal);
+      cg_update_kernel<T><<<nb, kRedThreads, 0, st>>>(x, r, p, w, cm, c, P->scal, P->partials,
+                                                      n);
+    }
     cg_beta_kernel<<<1, 64, 0, st>>>(P->partials, nb, P->scal, 0);
     ++it;
     if (it % P->check_every == 0 || it == maxit) {
@@ -427,6 +447,7 @@ int ax_poisson_destroy(ax_poisson *P) {
   cudaFree(P->r_old32);
   cudaFree(P->corr32);
   if (P->op) ax_op_destroy(P->op);
+  cudaFree(P->dotp);
   cudaFree(P->scal);
   if (P->scal_host) cudaFreeHost(P->scal_host);
   delete P;
@@ -460,6 +481,11 @@ int ax_poisson_create(ax_poisson **out, int lx, int nelv, const double *dx, cons
                              stream)) {
     ax_poisson_destroy(P);
     return rco;
+  }
+  P->ndot = ax::op_dot_blocks(P->op);
+  if (P->ndot > 0 && alloc(&P->dotp, (size_t)P->ndot)) {
+    ax_poisson_destroy(P);
+    return AX_ENOMEM;
   }
   int rc = alloc(&P->minv, n) | alloc(&P->cm, n) | alloc(&P->w, n) | alloc(&P->r, n) |
            alloc(&P->p, n) | alloc(&P->partials, 4 * (size_t)kRedBlocks) |

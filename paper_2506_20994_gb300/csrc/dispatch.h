@@ -47,9 +47,12 @@ inline bool df64eo_supported(int lx) { return lx >= 4 && lx <= 12 && lx % 2 == 0
 // The same kernel on geometry prepared by dispatch_eo_prepare (df::dd2
 // entries, 56 lx^3 bytes per element); fmask picks the fields to write
 // (bits 0-5 g11, g22, g33, g12, g13, g23; bit 6 h1).
+// dotp (optional): per-block partial sums of u . w, df64eo_prep_blocks(lx,
+// nelv) of them (default elements per block).
 int dispatch_df64eo_prep(int lx, double *w, const double *u, const double *dx,
                          const double *dxt, const df::dd2 *gp, int nelv, int epb,
-                         cudaStream_t st);
+                         cudaStream_t st, double *dotp = nullptr);
+int df64eo_prep_blocks(int lx, int nelv);
 int dispatch_eo_prepare(int lx, df::dd2 *gp, const double *h1, const double *g11,
                         const double *g22, const double *g33, const double *g12,
                         const double *g13, const double *g23, int nelv, int fmask,

@@ -9,6 +9,7 @@
 #include "../../include/axhelm.h"
 #include "common.cuh"
 #include "dispatch.h"
+#include "op.h"
 
 struct ax_op {
   int lx = 0, nelv = 0;
@@ -87,6 +88,19 @@ extern "C" int ax_op_apply(ax_op *op, double *w, const double *u, void *stream) 
   return ax_helm(w, u, op->dx, op->dxt, op->h1, g[0], g[1], g[2], g[3], g[4], g[5], op->lx,
                  op->nelv, stream);
 }
+
+namespace ax {
+
+int op_dot_blocks(const ax_op *op) {
+  return op && op->gp ? df64eo_prep_blocks(op->lx, op->nelv) : 0;
+}
+
+int op_apply_dot(ax_op *op, double *w, const double *u, double *partials, cudaStream_t st) {
+  if (!op || !op->gp || !partials) return AX_EINVAL;
+  return dispatch_df64eo_prep(op->lx, w, u, op->dx, op->dxt, op->gp, op->nelv, 0, st, partials);
+}
+
+}  // namespace ax
 
 extern "C" int ax_op_info(const ax_op *op, int *prepared, int64_t *device_bytes) {
   if (!op) return AX_EINVAL;

@@ -1,0 +1,17 @@
+// Library-internal entry points of the operator handle (op.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/axhelm.h"
+
+namespace ax {
+
+// Partials that op_apply_dot writes (0 when the handle has no prepared
+// geometry, where op_apply_dot returns AX_EINVAL).
+int op_dot_blocks(const ax_op *op);
+// w = Ax(u) as ax_op_apply, plus partials[b] = sum over block b's elements
+// of u . w (element-local, before any gather-scatter; fixed order).
+int op_apply_dot(ax_op *op, double *w, const double *u, double *partials, cudaStream_t st);
+
+}  // namespace ax

@@ -87,8 +87,10 @@ def test_assembled_apply(dims, lx):
     np.testing.assert_allclose(minv, ref.ravel(), rtol=1e-12)
 
 
-def test_cg_iterates_match_oracle():
-    lx = 6
+@pytest.mark.parametrize("lx", [5, 6, 8])
+def test_cg_iterates_match_oracle(lx):
+    """lx = 6, 8: fp64 PCG with p . Ap fused into the prepared-geometry
+    apply; lx = 5: the separate mask-and-dot pass."""
     _, P, O = _problem((3, 3, 3), lx, seed=4)
     b = P.rhs(oracle.poisson_rhs_f)
     np.testing.assert_allclose(b.cpu().numpy(), O.b, rtol=1e-12, atol=1e-14)
