@@ -81,6 +81,14 @@ __global__ void precond_kernel(double *__restrict__ minv, double *__restrict__ c
   cm[q] = c[q] * m;
 }
 
+// sqm = sqrt(minv) in fp32 (the scale of the symmetric learned form)
+__global__ void sqrt_minv_kernel(float *__restrict__ sqm, const double *__restrict__ minv,
+                                 int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    sqm[q] = sqrtf(ax::df::split(minv[q]).hi);
+}
+
 // r = b (masked), p = minv r; partials: rz = sum cm r^2, rr = sum c r^2
 template <typename T>
 __global__ void cg_init_kernel(T *__restrict__ x, T *__restrict__ r, T *__restrict__ p,
@@ -262,6 +270,7 @@ struct ax_poisson {
   ax_op *op = nullptr;  // the operator (prepared geometry where it applies)
   double *dotp = nullptr;  // per-block partials of p . Ap from the fused apply
   int ndot = 0;
+  float *sqm = nullptr;  // sqrt(minv) in fp32 for the symmetric learned form (lazily)
   ax_gs *gs = nullptr;
   const double *c = nullptr;  // 1/multiplicity (owned by gs)
   // owned fp64 work
@@ -448,6 +457,7 @@ int ax_poisson_destroy(ax_poisson *P) {
   cudaFree(P->corr32);
   if (P->op) ax_op_destroy(P->op);
   cudaFree(P->dotp);
+  cudaFree(P->sqm);
   cudaFree(P->scal);
   if (P->scal_host) cudaFreeHost(P->scal_host);
   delete P;
@@ -545,6 +555,7 @@ int ax_poisson_set_diag(ax_poisson *P, const double *diag, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = P->n;
   precond_kernel<<<blocks_for(n, 256), 256, 0, st>>>(P->minv, P->cm, diag, P->mask, P->c, n);
+  if (P->sqm) sqrt_minv_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(P->sqm, P->minv, n);
   if (P->minv32) {  // fp32 copies of the refinement solve, if converted already
     to_f32_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(P->minv32, P->minv, n);
     to_f32_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(P->cm32, P->cm, n);
@@ -874,7 +885,8 @@ int fcg_loop(ax_poisson *P, const ax_mlp *M, T *x, const T *b, T *r, T *r_old, T
   const int have = M != nullptr;
   auto precondition = [&](int first) -> int {
     if (have) {
-      int rc = ax::mlp_correction<T>(M, corr, r, minv, mask, c, P->nelv, st);
+      int rc = ax::mlp_correction<T>(M, corr, r, minv, mask, c, P->nelv, st,
+                                     M->arch == AX_MLP_SYM ? P->sqm : nullptr);
       if (rc) return rc;
       if ((rc = gs_sum_t<T>(P->gs, corr, st))) return rc;
     }
@@ -929,7 +941,15 @@ int fcg_loop(ax_poisson *P, const ax_mlp *M, T *x, const T *b, T *r, T *r_old, T
   return status;
 }
 
-int ensure_fcg64(ax_poisson *P) {
+int ensure_sqm(ax_poisson *P, cudaStream_t st) {
+  if (P->sqm) return AX_OK;
+  if (alloc(&P->sqm, P->n)) return AX_ENOMEM;
+  sqrt_minv_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(P->sqm, P->minv, P->n);
+  return ax::launch_status();
+}
+
+int ensure_fcg64(ax_poisson *P, cudaStream_t st) {
+  if (int rc = ensure_sqm(P, st)) return rc;
   if (P->r_old) return AX_OK;
   return alloc(&P->r_old, P->n) | alloc(&P->corr, P->n) ? AX_ENOMEM : AX_OK;
 }
@@ -941,9 +961,9 @@ extern "C" int ax_fcg_solve(ax_poisson *P, const ax_mlp *M, double *x, const dou
                             void *stream) {
   if (!P || !x || !b || maxit < 0 || !(tol >= 0)) return AX_EINVAL;
   if (M && M->n_in != P->lx * P->lx * P->lx) return AX_EINVAL;
-  int rc = ensure_fcg64(P);
-  if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
+  int rc = ensure_fcg64(P, st);
+  if (rc) return rc;
   auto A = [P](double *w, const double *u, cudaStream_t s) { return apply_f64(P, w, u, s); };
   return fcg_loop<double>(P, M, x, b, P->r, P->r_old, P->p, P->w, P->corr, P->mask, P->minv,
                           P->c, A, tol, maxit, iters, relres, fallbacks, st);
@@ -954,10 +974,11 @@ extern "C" int ax_precondition(ax_poisson *P, const ax_mlp *M, double *z, const 
   if (!P || !z || !r) return AX_EINVAL;
   if (M && M->n_in != P->lx * P->lx * P->lx) return AX_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  int rc = ensure_fcg64(P);
+  int rc = ensure_fcg64(P, st);
   if (rc) return rc;
   if (M) {
-    if ((rc = ax::mlp_correction<double>(M, P->corr, r, P->minv, P->mask, P->c, P->nelv, st)))
+    if ((rc = ax::mlp_correction<double>(M, P->corr, r, P->minv, P->mask, P->c, P->nelv, st,
+                                        M->arch == AX_MLP_SYM ? P->sqm : nullptr)))
       return rc;
     if ((rc = ax_gs_sum(P->gs, P->corr, st))) return rc;
   }
@@ -986,6 +1007,7 @@ extern "C" int ax_mpfcg_solve(ax_poisson *P, const ax_mlp *M, int mode, double *
   int rc = ensure_lowp(P, mode == AX_PREC_BF16 ? 2 : 1, st);
   if (rc) return rc;
   if (!P->r_old32 && (alloc(&P->r_old32, P->n) | alloc(&P->corr32, P->n))) return AX_ENOMEM;
+  if ((rc = ensure_sqm(P, st))) return rc;
   const int64_t n = P->n;
   const unsigned nb = kRedBlocks;
   double *sc = reinterpret_cast<double *>(P->scal);

@@ -7,8 +7,9 @@
 // * Apply (inference): both layers are small dense GEMMs over a tile of 64
 //   elements, run on the tensor cores with bf16 operands and fp32
 //   accumulation (mma.sync m16n8k16); x is staged in shared memory chunk by
-//   chunk, the hidden layer stays in shared memory, and the epilogue writes
-//   mask * (1/multiplicity) * s_e * y straight to the correction vector.
+//   chunk, the hidden layer stays in shared memory, and the output goes
+//   through shared memory in 128-column slabs so that every global access
+//   is a coalesced row segment.
 // * Training: fp32 SIMT kernels with one thread per output and a fixed
 //   summation order (deterministic, no atomics): forward, mean-squared loss,
 //   backpropagation, Adam (Kingma & Ba 2015).
@@ -68,29 +69,46 @@ AX_D void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t 
 // Inference over a tile of kTE elements.  Weights (bf16, padded with
 // zeros): W1T [HP][NP] (k contiguous per hidden unit), b1 [HP] (fp32),
 // W2T [NP][HP] (k contiguous per output), b2 [NP] (fp32).
-// Shared memory: xs [kTE][kKC+8] bf16, hs [kTE][HP+8] bf16, s[kTE] fp32.
+// Global memory is touched only by coalesced row-contiguous passes: the
+// input chunk is loaded one row segment per warp into xs, and each 128-wide
+// output slab goes through ys before it is scaled and stored.
+// Shared memory: xs [kTE][kKC+8] bf16, hs [kTE][HP+8] bf16,
+// ys [kTE][kYC+4] fp32, s [kTE] fp32, s_part [kTE][2] fp32.
+constexpr int kYC = 128;  // output columns per epilogue slab
+
+inline size_t apply_smem(int HP) {
+  return (size_t)kTE * (kKC + 8) * 2 + (size_t)kTE * (HP + 8) * 2 + (size_t)kTE * (kYC + 4) * 4 +
+         (size_t)kTE * 3 * 4;
+}
+
 template <typename T, bool SYM>
 __global__ void __launch_bounds__(kThreads)
 mlp_apply_kernel(T *__restrict__ corr, const T *__restrict__ r, const T *__restrict__ minv,
                  const T *__restrict__ mask, const T *__restrict__ cw,
-                 const __nv_bfloat16 *__restrict__ W1T, const float *__restrict__ b1,
-                 const __nv_bfloat16 *__restrict__ W2T, const float *__restrict__ b2, int N,
-                 int NP, int HP, int nelv) {
+                 const float *__restrict__ sc, const __nv_bfloat16 *__restrict__ W1T,
+                 const float *__restrict__ b1, const __nv_bfloat16 *__restrict__ W2T,
+                 const float *__restrict__ b2, int N, int NP, int HP, int nelv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int XS = kKC + 8, HS = HP + 8;  // row strides (bf16), padded against conflicts
+  const int XS = kKC + 8, HS = HP + 8, YS = kYC + 4;  // row strides, padded
   __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
   __nv_bfloat16 *hs = xs + kTE * XS;
-  float *s_sh = reinterpret_cast<float *>(hs + kTE * HS);
+  float *ys = reinterpret_cast<float *>(hs + kTE * HS);
+  float *s_sh = ys + kTE * YS;
+  float *s_part = s_sh + kTE;  // [kTE][2]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t4 = lane & 3;
   const long long e0 = (long long)blockIdx.x * kTE;
-  // input scale of the residual and activation of the hidden layer
-  auto in_scale = [](float mv) { return SYM ? sqrtf(mv) : mv; };
+  // input scale of the residual and activation of the hidden layer; the
+  // symmetric form is linear, so its per-element normalisation cancels and
+  // is skipped, and its scale sqrt(minv) comes precomputed in sc if given
+  auto in_scale = [&](size_t q) {
+    return SYM ? (sc ? sc[q] : sqrtf(to_f32(minv[q]))) : to_f32(minv[q]);
+  };
   auto act = [](float a) { return SYM ? a : tanhf(a); };
   const int nel = (int)min((long long)kTE, nelv - e0);
 
-  // ---- layer 1: acc = (minv r) W1 over k chunks; also ||minv r||^2 per row
+  // ---- layer 1: acc = x W1 over k chunks (and ||x||^2 per row, tanh form)
   const int mt = warp & 3;        // rows mt*16 .. +15
   const int nh = warp >> 2;       // n-tiles nh, nh+2, ...
   const int n_tiles1 = HP / 8;
@@ -99,28 +117,30 @@ mlp_apply_kernel(T *__restrict__ corr, const T *__restrict__ r, const T *__restr
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc1[a][b] = 0.f;
-  const int lrow = tid >> 2;          // loader: row
-  const int lcol = (tid & 3) * 16;    // loader: first of 16 columns
-  float ss = 0.f;
+  const int lcol = tid & 63;      // loader: column of the chunk
+  const int lrow0 = tid >> 6;     // loader: rows lrow0 + 4 i
+  float ss[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) ss[i] = 0.f;
   for (int kc = 0; kc < NP; kc += kKC) {
     __syncthreads();
-    {
-      const bool rok = lrow < nel;
-      const size_t base = (size_t)(e0 + (rok ? lrow : 0)) * N;
+    const int k = kc + lcol;
 #pragma unroll
-      for (int q = 0; q < 16; q += 2) {
-        const int k = kc + lcol + q;
-        float v0 = 0.f, v1 = 0.f;
-        if (rok && k < N) v0 = in_scale(to_f32(minv[base + k])) * to_f32(r[base + k]);
-        if (rok && k + 1 < N)
-          v1 = in_scale(to_f32(minv[base + k + 1])) * to_f32(r[base + k + 1]);
-        ss += v0 * v0 + v1 * v1;
-        *reinterpret_cast<uint32_t *>(&xs[lrow * XS + lcol + q]) = pack_bf16(v0, v1);
+    for (int i = 0; i < 16; ++i) {
+      const int row = lrow0 + 4 * i;
+      float v = 0.f;
+      if (row < nel && k < N) {
+        const size_t q = (size_t)(e0 + row) * N + k;
+        v = in_scale(q) * to_f32(r[q]);
       }
+      if (!SYM) ss[i] = fmaf(v, v, ss[i]);
+      xs[row * XS + lcol] = __float2bfloat16_rn(v);
     }
     __syncthreads();
     const int kmax = min(kKC, NP - kc);
-    for (int ks = 0; ks < kmax; ks += 16) {
+#pragma unroll
+    for (int ks = 0; ks < kKC; ks += 16) {
+      if (ks >= kmax) break;
       uint32_t a[4];
       const __nv_bfloat16 *x0 = xs + (mt * 16 + g) * XS + ks + 2 * t4;
       const __nv_bfloat16 *x1 = x0 + 8 * XS;
@@ -140,12 +160,20 @@ mlp_apply_kernel(T *__restrict__ corr, const T *__restrict__ r, const T *__restr
       }
     }
   }
-  // row norms: the four loader threads of a row are adjacent lanes
-  ss += __shfl_xor_sync(0xffffffffu, ss, 1);
-  ss += __shfl_xor_sync(0xffffffffu, ss, 2);
-  if ((tid & 3) == 0) s_sh[lrow] = sqrtf(ss);
+  // row norms: each warp holds 32 columns of its rows; fixed-order sums
+  if (!SYM) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      float v = ss[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) s_part[(lrow0 + 4 * i) * 2 + (warp & 1)] = v;
+    }
+  }
   __syncthreads();
-  // hidden layer: h = tanh(acc / s + b1) -> shared memory (bf16)
+  if (tid < kTE) s_sh[tid] = SYM ? 1.f : sqrtf(s_part[2 * tid] + s_part[2 * tid + 1]);
+  __syncthreads();
+  // hidden layer: h = act(acc / s + b1) -> shared memory (bf16)
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int nt = nh + 2 * j;
@@ -163,18 +191,21 @@ mlp_apply_kernel(T *__restrict__ corr, const T *__restrict__ r, const T *__restr
   }
   __syncthreads();
 
-  // ---- layer 2: y = h W2 + b2, epilogue corr = mask * c * s * y
+  // ---- layer 2: y = h W2 + b2 in slabs of kYC outputs, epilogue
+  // corr = mask * c * s * y (tanh form) or sqrt(minv) * y (symmetric form)
   const int half = warp >> 2;
   const int n_tiles2 = NP / 8;
   const int r0 = mt * 16 + g, r1 = r0 + 8;
-  const float s0 = s_sh[r0], s1 = s_sh[r1];
-  for (int nb = half * 8; nb < n_tiles2; nb += 16) {
+  const int ocol = tid & (kYC - 1), orow0 = tid / kYC;  // epilogue mapping
+  for (int nb0 = 0; nb0 < n_tiles2; nb0 += kYC / 8) {
     float acc2[8][4];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc2[a][b] = 0.f;
-    for (int ks = 0; ks < HP; ks += 16) {
+#pragma unroll
+    for (int ks = 0; ks < 64; ks += 16) {  // HP <= 64
+      if (ks >= HP) break;
       uint32_t a[4];
       const __nv_bfloat16 *h0 = hs + r0 * HS + ks + 2 * t4;
       const __nv_bfloat16 *h1 = hs + r1 * HS + ks + 2 * t4;
@@ -184,7 +215,7 @@ mlp_apply_kernel(T *__restrict__ corr, const T *__restrict__ r, const T *__restr
       a[3] = *reinterpret_cast<const uint32_t *>(h1 + 8);
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const int nt = nb + j;
+        const int nt = nb0 + half * 8 + j;
         if (nt < n_tiles2) {
           const __nv_bfloat16 *w = W2T + (size_t)(nt * 8 + g) * HP + ks + 2 * t4;
           const uint32_t b0 = __ldg(reinterpret_cast<const unsigned int *>(w));
@@ -195,26 +226,28 @@ mlp_apply_kernel(T *__restrict__ corr, const T *__restrict__ r, const T *__restr
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int nt = nb + j;
-      if (nt >= n_tiles2) continue;
-      const int col = nt * 8 + 2 * t4;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int row = h ? r1 : r0;
-        const float sc = h ? s1 : s0;
-        if (row >= nel) continue;
-        const size_t qb = (size_t)(e0 + row) * N;
-#pragma unroll
-        for (int c2 = 0; c2 < 2; ++c2) {
-          const int o = col + c2;
-          if (o >= N) continue;
-          const float y = acc2[j][2 * h + c2] + b2[o];
-          const size_t q = qb + o;
-          const float osc = SYM ? sqrtf(to_f32(minv[q])) : to_f32(cw[q]);
-          corr[q] = from_f32<T>(to_f32(mask[q]) * osc * sc * y);
+      const int col = (half * 8 + j) * 8 + 2 * t4;  // within the slab
+      *reinterpret_cast<float2 *>(&ys[r0 * YS + col]) = make_float2(acc2[j][0], acc2[j][1]);
+      *reinterpret_cast<float2 *>(&ys[r1 * YS + col]) = make_float2(acc2[j][2], acc2[j][3]);
+    }
+    __syncthreads();
+    const int o = nb0 * 8 + ocol;
+    if (o < N) {
+      const float bo = b2[o];
+      // fixed trip count, unrolled: the loads of several rows are in flight
+      // together instead of one latency per row
+#pragma unroll 8
+      for (int j = 0; j < kTE / (kThreads / kYC); ++j) {
+        const int row = orow0 + j * (kThreads / kYC);
+        if (row < nel) {
+          const size_t q = (size_t)(e0 + row) * N + o;
+          const float y = ys[row * YS + ocol] + bo;
+          const float osc = SYM ? in_scale(q) : to_f32(mask[q]) * to_f32(cw[q]);
+          corr[q] = from_f32<T>(osc * s_sh[row] * y);
         }
       }
     }
+    __syncthreads();
   }
 }
 
@@ -553,11 +586,11 @@ int mlp_tie_params(ax_mlp *M, cudaStream_t st) {
 
 template <typename T>
 int mlp_correction(const ax_mlp *M, T *corr, const T *r, const T *minv, const T *mask,
-                   const T *c, int nelv, cudaStream_t st) {
+                   const T *c, int nelv, cudaStream_t st, const float *sc) {
   if (nelv <= 0) return AX_OK;
   const Layout L = layout(M);
   const char *base = reinterpret_cast<const char *>(M->theta_bf);
-  const size_t smem = ((size_t)kTE * (kKC + 8) + (size_t)kTE * (L.HP + 8)) * 2 + kTE * 4;
+  const size_t smem = apply_smem(L.HP);
   auto kern = M->arch == AX_MLP_SYM ? mlp_apply_kernel<T, true> : mlp_apply_kernel<T, false>;
   if (smem > 48 * 1024 &&
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -567,7 +600,7 @@ int mlp_correction(const ax_mlp *M, T *corr, const T *r, const T *minv, const T 
   }
   const unsigned grid = (unsigned)((nelv + kTE - 1) / kTE);
   kern<<<grid, kThreads, smem, st>>>(
-      corr, r, minv, mask, c, reinterpret_cast<const __nv_bfloat16 *>(base + L.w1t),
+      corr, r, minv, mask, c, sc, reinterpret_cast<const __nv_bfloat16 *>(base + L.w1t),
       reinterpret_cast<const float *>(base + L.b1p),
       reinterpret_cast<const __nv_bfloat16 *>(base + L.w2t),
       reinterpret_cast<const float *>(base + L.b2p), M->n_in, L.NP, L.HP, nelv);
@@ -575,9 +608,11 @@ int mlp_correction(const ax_mlp *M, T *corr, const T *r, const T *minv, const T 
 }
 
 template int mlp_correction<double>(const ax_mlp *, double *, const double *, const double *,
-                                    const double *, const double *, int, cudaStream_t);
+                                    const double *, const double *, int, cudaStream_t,
+                                    const float *);
 template int mlp_correction<float>(const ax_mlp *, float *, const float *, const float *,
-                                   const float *, const float *, int, cudaStream_t);
+                                   const float *, const float *, int, cudaStream_t,
+                                   const float *);
 
 }  // namespace ax
 

@@ -44,9 +44,10 @@ int mlp_tie_params(ax_mlp *M, cudaStream_t st);
 // y_e = MLP(x_e), x_e = (minv .* r)_e / s_e, s_e = ||(minv .* r)_e||_2
 // (bf16 tensor-core apply, fp32 accumulation).  T is double or float.
 // For the symmetric form (arch AX_MLP_SYM) the scale sqrt(minv) replaces
-// minv on the input and c on the output, and the activation is the identity.
+// minv on the input and c on the output, and the activation is the identity;
+// sc, if not null, holds that scale precomputed in fp32 (mask and c unused).
 template <typename T>
 int mlp_correction(const ax_mlp *M, T *corr, const T *r, const T *minv, const T *mask,
-                   const T *c, int nelv, cudaStream_t st);
+                   const T *c, int nelv, cudaStream_t st, const float *sc = nullptr);
 
 }  // namespace ax
