@@ -134,13 +134,22 @@ __global__ void mask_dot_kernel(T *__restrict__ w, const T *__restrict__ p,
   if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
 }
 
+// alpha = rz / <p, Ap> from the partials (one warp for the fixed-grid
+// partials; a whole block for the per-element-block partials of the fused
+// apply)
 __global__ void cg_alpha_kernel(const double *__restrict__ partials, int nblk,
                                 CgScalars *__restrict__ s) {
-  __shared__ double t[1];
-  ax::warp_sum_partials<1>(partials, nblk, t);
-  __syncthreads();
+  __shared__ double t[32];
+  double pap_all;
+  if (blockDim.x == 32) {
+    ax::warp_sum_partials<1>(partials, nblk, t);
+    __syncthreads();
+    pap_all = t[0];
+  } else {
+    pap_all = ax::block_sum_partials(partials, nblk, t);
+  }
   if (threadIdx.x == 0) {
-    const double pap = t[0];
+    const double pap = pap_all;
     s->pap = pap;
     if (!(pap > 0.0) || !isfinite(pap) || !isfinite(s->rz)) {
       s->status = 1;
@@ -362,7 +371,7 @@ int pcg_loop(ax_poisson *P, T *x, const T *b, T *r, T *p, T *w, const T *mask, c
       rc = ax::op_apply_dot(P->op, (double *)w, (const double *)p, P->dotp, st);
       if (rc == AX_OK) rc = ax_gs_sum(P->gs, (double *)w, st);
       if (rc) return rc;
-      cg_alpha_kernel<<<1, 32, 0, st>>>(P->dotp, P->ndot, P->scal);
+      cg_alpha_kernel<<<1, 1024, 0, st>>>(P->dotp, P->ndot, P->scal);
       cg_update_kernel<T, true><<<nb, kRedThreads, 0, st>>>(x, r, p, w, cm, c, P->scal,
                                                             P->partials, n);
     } else {
@@ -739,11 +748,13 @@ extern "C" int ax_jacobi_noalloc(double *minv, const double *dx, const double *h
 // ---------------------------------------------------------------------------
 namespace {
 
-// x += alpha p; r_old = r; r -= alpha w; partial rr = sum c r^2
-template <typename T>
+// x += alpha p; r_old = r; r -= alpha w; partial rr = sum c r^2.  MASKW: w is
+// not masked yet (fused apply); rows where cm = c * minv is 0 keep r = 0.
+template <typename T, bool MASKW = false>
 __global__ void fcg_update_kernel(T *__restrict__ x, T *__restrict__ r, T *__restrict__ r_old,
                                   const T *__restrict__ p, const T *__restrict__ w,
-                                  const T *__restrict__ c, const CgScalars *__restrict__ s,
+                                  const T *__restrict__ c, const T *__restrict__ cm,
+                                  const CgScalars *__restrict__ s,
                                   double *__restrict__ partials, int64_t n) {
   __shared__ double sh[kRedThreads / 32];
   const T alpha = (T)s->alpha;
@@ -753,7 +764,7 @@ __global__ void fcg_update_kernel(T *__restrict__ x, T *__restrict__ r, T *__res
     x[q] += alpha * p[q];
     const T ro = r[q];
     r_old[q] = ro;
-    const T rv = ro - alpha * w[q];
+    const T rv = (MASKW && cm[q] == T(0)) ? ro : ro - alpha * w[q];
     r[q] = rv;
     a_rr += c[q] * rv * rv;
   }
@@ -762,23 +773,27 @@ __global__ void fcg_update_kernel(T *__restrict__ x, T *__restrict__ r, T *__res
   if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
 }
 
-// partials of <zj, r>, <corr, r>, <zj, r_old>, <corr, r_old> (zj = minv r)
+// partials of <zj, r>, <corr, r>, <zj, r_old>, <corr, r_old> (zj = minv r),
+// weighted by c; with cm = c * minv the Jacobi pair costs 3 multiply-adds and
+// the correction pair 3 more (the fp64 pipe, not memory, bounds this kernel)
 template <typename T>
 __global__ void fcg_dots_kernel(const T *__restrict__ r, const T *__restrict__ r_old,
-                                const T *__restrict__ corr, const T *__restrict__ minv,
+                                const T *__restrict__ corr, const T *__restrict__ cm,
                                 const T *__restrict__ c, int have_corr,
                                 double *__restrict__ partials, int64_t n) {
   __shared__ double sh[4 * kRedThreads / 32];
   T d0 = 0, d1 = 0, d2 = 0, d3 = 0;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
-    const T cq = c[q], rv = r[q], ro = r_old[q];
-    const T zj = minv[q] * rv;
-    const T co = have_corr ? corr[q] : T(0);
-    d0 += cq * zj * rv;
-    d1 += cq * co * rv;
-    d2 += cq * zj * ro;
-    d3 += cq * co * ro;
+    const T rv = r[q], ro = r_old[q];
+    const T a = cm[q] * rv;
+    d0 += a * rv;
+    d2 += a * ro;
+    if (have_corr) {
+      const T e = c[q] * corr[q];
+      d1 += e * rv;
+      d3 += e * ro;
+    }
   }
   double v[4] = {(double)d0, (double)d1, (double)d2, (double)d3};
   ax::block_sum<4>(v, sh);
@@ -878,8 +893,9 @@ int gs_sum_t<float>(ax_gs *g, float *v, cudaStream_t st) {
 // Flexible PCG loop (x0 = 0) with the learned correction when M != NULL.
 template <typename T, typename Apply>
 int fcg_loop(ax_poisson *P, const ax_mlp *M, T *x, const T *b, T *r, T *r_old, T *p, T *w,
-             T *corr, const T *mask, const T *minv, const T *c, Apply apply, double tol,
-             int maxit, int *iters, double *relres, int *fallbacks, cudaStream_t st) {
+             T *corr, const T *mask, const T *minv, const T *c, const T *cm, Apply apply,
+             double tol, int maxit, int *iters, double *relres, int *fallbacks,
+             cudaStream_t st) {
   const int64_t n = P->n;
   const unsigned nb = kRedBlocks;
   const int have = M != nullptr;
@@ -890,7 +906,7 @@ int fcg_loop(ax_poisson *P, const ax_mlp *M, T *x, const T *b, T *r, T *r_old, T
       if (rc) return rc;
       if ((rc = gs_sum_t<T>(P->gs, corr, st))) return rc;
     }
-    fcg_dots_kernel<T><<<nb, kRedThreads, 0, st>>>(r, r_old, corr, minv, c, have, P->partials,
+    fcg_dots_kernel<T><<<nb, kRedThreads, 0, st>>>(r, r_old, corr, cm, c, have, P->partials,
                                                    n);
     fcg_beta_kernel<<<1, 128, 0, st>>>(P->partials, nb, P->scal, first, have);
     fcg_p_kernel<T><<<nb, kRedThreads, 0, st>>>(p, r, minv, corr, P->scal, first, n);
@@ -912,12 +928,23 @@ int fcg_loop(ax_poisson *P, const ax_mlp *M, T *x, const T *b, T *r, T *r_old, T
   double rel = rr0 > 0 ? 1.0 : 0.0;
   int it = 0, status = AX_ENOTCONV;
   if (rr0 == 0.0 || tol >= 1.0) status = AX_OK;
+  // fp64 with prepared geometry: p . Ap from the apply itself (see pcg_loop)
+  const bool fused = std::is_same<T, double>::value && P->dotp != nullptr;
   while (status != AX_OK && it < maxit) {
-    if ((rc = apply(w, p, st))) return rc;
-    mask_dot_kernel<T><<<nb, kRedThreads, 0, st>>>(w, p, mask, c, P->partials, n);
-    cg_alpha_kernel<<<1, 32, 0, st>>>(P->partials, nb, P->scal);
-    fcg_update_kernel<T><<<nb, kRedThreads, 0, st>>>(x, r, r_old, p, w, c, P->scal, P->partials,
-                                                     n);
+    if (fused) {
+      rc = ax::op_apply_dot(P->op, (double *)w, (const double *)p, P->dotp, st);
+      if (rc == AX_OK) rc = ax_gs_sum(P->gs, (double *)w, st);
+      if (rc) return rc;
+      cg_alpha_kernel<<<1, 1024, 0, st>>>(P->dotp, P->ndot, P->scal);
+      fcg_update_kernel<T, true><<<nb, kRedThreads, 0, st>>>(x, r, r_old, p, w, c, cm, P->scal,
+                                                             P->partials, n);
+    } else {
+      if ((rc = apply(w, p, st))) return rc;
+      mask_dot_kernel<T><<<nb, kRedThreads, 0, st>>>(w, p, mask, c, P->partials, n);
+      cg_alpha_kernel<<<1, 32, 0, st>>>(P->partials, nb, P->scal);
+      fcg_update_kernel<T><<<nb, kRedThreads, 0, st>>>(x, r, r_old, p, w, c, cm, P->scal,
+                                                       P->partials, n);
+    }
     fcg_rr_kernel<<<1, 32, 0, st>>>(P->partials, nb, P->scal, 0);
     ++it;
     if (it % P->check_every == 0 || it == maxit) {
@@ -966,7 +993,7 @@ extern "C" int ax_fcg_solve(ax_poisson *P, const ax_mlp *M, double *x, const dou
   if (rc) return rc;
   auto A = [P](double *w, const double *u, cudaStream_t s) { return apply_f64(P, w, u, s); };
   return fcg_loop<double>(P, M, x, b, P->r, P->r_old, P->p, P->w, P->corr, P->mask, P->minv,
-                          P->c, A, tol, maxit, iters, relres, fallbacks, st);
+                          P->c, P->cm, A, tol, maxit, iters, relres, fallbacks, st);
 }
 
 extern "C" int ax_precondition(ax_poisson *P, const ax_mlp *M, double *z, const double *r,
@@ -1033,8 +1060,8 @@ extern "C" int ax_mpfcg_solve(ax_poisson *P, const ax_mlp *M, int mode, double *
     int its = 0, fb = 0;
     double irel = 0.0;
     rc = fcg_loop<float>(P, M, P->x32, P->r32, P->w32, P->r_old32, P->p32, P->q32, P->corr32,
-                         P->mask32, P->minv32, P->c32, A32, inner_tol, max_inner, &its, &irel,
-                         &fb, st);
+                         P->mask32, P->minv32, P->c32, P->cm32, A32, inner_tol, max_inner, &its,
+                         &irel, &fb, st);
     inner_total += its;
     fb_total += fb;
     if (rc != AX_OK && rc != AX_ENOTCONV) return rc;

@@ -49,4 +49,22 @@ AX_D void warp_sum_partials(const double *__restrict__ partials, int nblk, doubl
   if (lane == 0) out[q] = s;
 }
 
+// Sum of partials[0 .. nblk) by the whole block (blockDim.x a multiple of
+// 32, at most 1024): thread t adds t, t + blockDim.x, ... in order, then a
+// fixed shuffle tree and a fixed-order sum over the warps.  Valid in thread
+// 0.  For the many partials (one per element block) of a fused reduction.
+AX_D double block_sum_partials(const double *__restrict__ partials, int nblk, double *sh) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partials[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = s;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+  return t;
+}
+
 }  // namespace ax
