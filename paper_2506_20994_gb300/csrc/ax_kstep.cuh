@@ -36,7 +36,8 @@ __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restri
                                            const S *__restrict__ g22, const S *__restrict__ g33,
                                            const S *__restrict__ g12, const S *__restrict__ g13,
                                            const S *__restrict__ g23, long long e0, int nel,
-                                           int epb, unsigned char *smem_raw) {
+                                           int epb, unsigned char *smem_raw,
+                                           double *__restrict__ dotp = nullptr) {
   constexpr int N2 = LX * LX;
   constexpr int N3 = LX * N2;
   T *sdx = reinterpret_cast<T *>(smem_raw);
@@ -104,6 +105,7 @@ __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restri
   }
   __syncthreads();
 
+  T dsum = T(0);  // u . w of this thread's column (fused dot, if dotp)
   if (own) {
 #pragma unroll
     for (int k = 0; k < LX; ++k) {
@@ -114,23 +116,40 @@ __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restri
         acc = fma_t(sdxt[l * LX + j], sws[k * N2 + l * LX + i], acc);
       }
       if (active) w[base + (size_t)k * N2] = (W)acc;
+      if (dotp) dsum = fma_t(uk[k], acc, dsum);
+    }
+  }
+  if (dotp) {  // one partial per block, fixed order (block-uniform branch)
+    __shared__ double red[32];
+    double v = (double)dsum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int k = 0; k < (int)((blockDim.x + 31) / 32); ++k) t += red[k];
+      dotp[blockIdx.x] = t;
     }
   }
 }
 
-template <int LX, typename SU, typename S, typename T, typename W>
+// DOT: also one partial of sum u . w per block (the CG's <p, Ap> before the
+// gather-scatter, see the fused solver loops).
+template <int LX, typename SU, typename S, typename T, typename W, bool DOT = false>
 __global__ void __launch_bounds__(1024)
 ax_kstep_kernel(W *__restrict__ w, const SU *__restrict__ u, const T *__restrict__ dx,
                 const T *__restrict__ dxt, const S *__restrict__ h1,
                 const S *__restrict__ g11, const S *__restrict__ g22,
                 const S *__restrict__ g33, const S *__restrict__ g12,
-                const S *__restrict__ g13, const S *__restrict__ g23, int nelv, int epb) {
+                const S *__restrict__ g13, const S *__restrict__ g23, int nelv, int epb,
+                double *__restrict__ dotp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long e0 = (long long)blockIdx.x * epb;
   const long long left = nelv - e0;
   const int nel = left < epb ? (int)left : epb;
   kstep_body<LX, SU, S, T, W>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, e0, nel, epb,
-                              smem_raw);
+                              smem_raw, DOT ? dotp : nullptr);
 }
 
 // Shared-memory bytes of one block of the k-loop kernel.
@@ -145,26 +164,27 @@ inline int kstep_default_epb(int lx) {
   return e < 1 ? 1 : e;
 }
 
+// dotp (optional): ceil(nelv / epb) partials of sum u . w, one per block.
 template <int LX, typename SU, typename S, typename T, typename W>
 int launch_kstep(W *w, const SU *u, const T *dx, const T *dxt, const S *h1, const S *g11,
                  const S *g22, const S *g33, const S *g12, const S *g13, const S *g23,
-                 int nelv, int epb, cudaStream_t stream) {
+                 int nelv, int epb, cudaStream_t stream, double *dotp = nullptr) {
   if (epb <= 0) epb = kstep_default_epb(LX);
   if (epb * LX * LX > 1024) return AX_EINVAL;
   const size_t smem = kstep_smem<LX, T>(epb);
-  auto kern = ax_kstep_kernel<LX, SU, S, T, W>;
-  static size_t granted = 48 * 1024;  // per instantiation
-  if (smem > granted) {
+  auto kern = dotp ? ax_kstep_kernel<LX, SU, S, T, W, true> : ax_kstep_kernel<LX, SU, S, T, W>;
+  static size_t granted[2] = {48 * 1024, 48 * 1024};  // per instantiation
+  if (smem > granted[dotp != nullptr]) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
       (void)cudaGetLastError();
       return AX_EINVAL;
     }
-    granted = smem;
+    granted[dotp != nullptr] = smem;
   }
   const unsigned grid = (unsigned)((nelv + epb - 1) / epb);
   kern<<<grid, epb * LX * LX, smem, stream>>>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23,
-                                              nelv, epb);
+                                              nelv, epb, dotp);
   return launch_status();
 }
 

@@ -44,6 +44,11 @@ struct CgScalars {
 };
 
 // ---------------------------------------------------------------- kernels
+template <typename... P>
+__device__ __forceinline__ bool aligned16(const P *...p) {
+  return ((reinterpret_cast<uintptr_t>(p) | ...) & 15u) == 0;
+}
+
 __global__ void jacobi_diag_kernel(double *__restrict__ diag, const double *__restrict__ dx,
                                    const double *__restrict__ h1, const double *__restrict__ g11,
                                    const double *__restrict__ g22, const double *__restrict__ g33,
@@ -171,15 +176,37 @@ __global__ void cg_update_kernel(T *__restrict__ x, T *__restrict__ r, const T *
   __shared__ double sh[2 * kRedThreads / 32];
   const T alpha = (T)s->alpha;
   T a_rz = 0, a_rr = 0;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    x[q] += alpha * p[q];
-    const T rv = (MASKW && cm[q] == T(0)) ? r[q] : r[q] - alpha * w[q];
-    r[q] = rv;
+  auto point = [&](T &xq, T &rq, T pq, T wq, T cmq, T cq) {
+    xq += alpha * pq;
+    const T rv = (MASKW && cmq == T(0)) ? rq : rq - alpha * wq;
+    rq = rv;
     const T r2 = rv * rv;
-    a_rz += cm[q] * r2;
-    a_rr += c[q] * r2;
+    a_rz += cmq * r2;
+    a_rr += cq * r2;
+  };
+  int64_t q0 = 0;
+  if constexpr (sizeof(T) == 4) {
+    if (aligned16(x, r, p, w, cm, c)) {  // fp32: 16-byte accesses
+      using V = float4;
+      const int64_t n4 = n / 4;
+      for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n4;
+           v += (int64_t)gridDim.x * blockDim.x) {
+        V xv = reinterpret_cast<V *>(x)[v], rv = reinterpret_cast<V *>(r)[v];
+        const V pv = reinterpret_cast<const V *>(p)[v], wv = reinterpret_cast<const V *>(w)[v];
+        const V mv = reinterpret_cast<const V *>(cm)[v], cv = reinterpret_cast<const V *>(c)[v];
+        point(xv.x, rv.x, pv.x, wv.x, mv.x, cv.x);
+        point(xv.y, rv.y, pv.y, wv.y, mv.y, cv.y);
+        point(xv.z, rv.z, pv.z, wv.z, mv.z, cv.z);
+        point(xv.w, rv.w, pv.w, wv.w, mv.w, cv.w);
+        reinterpret_cast<V *>(x)[v] = xv;
+        reinterpret_cast<V *>(r)[v] = rv;
+      }
+      q0 = n4 * 4;
+    }
   }
+  for (int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    point(x[q], r[q], p[q], w[q], cm[q], c[q]);
   double v[2] = {(double)a_rz, (double)a_rr};
   ax::block_sum<2>(v, sh);
   if (threadIdx.x == 0) {
@@ -216,7 +243,25 @@ __global__ void cg_p_kernel(T *__restrict__ p, const T *__restrict__ r,
                             const T *__restrict__ minv, const CgScalars *__restrict__ s,
                             int64_t n) {
   const T beta = (T)s->beta;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+  int64_t q0 = 0;
+  if constexpr (sizeof(T) == 4) {
+    if (aligned16(p, r, minv)) {  // fp32: 16-byte accesses
+      using V = float4;
+      const int64_t n4 = n / 4;
+      for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n4;
+           v += (int64_t)gridDim.x * blockDim.x) {
+        V pv = reinterpret_cast<V *>(p)[v];
+        const V rv = reinterpret_cast<const V *>(r)[v], mv = reinterpret_cast<const V *>(minv)[v];
+        pv.x = mv.x * rv.x + beta * pv.x;
+        pv.y = mv.y * rv.y + beta * pv.y;
+        pv.z = mv.z * rv.z + beta * pv.z;
+        pv.w = mv.w * rv.w + beta * pv.w;
+        reinterpret_cast<V *>(p)[v] = pv;
+      }
+      q0 = n4 * 4;
+    }
+  }
+  for (int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x)
     p[q] = minv[q] * r[q] + beta * p[q];
 }
@@ -278,7 +323,8 @@ struct ax_poisson {
   const double *mask = nullptr;
   ax_op *op = nullptr;  // the operator (prepared geometry where it applies)
   double *dotp = nullptr;  // per-block partials of p . Ap from the fused apply
-  int ndot = 0;
+  int ndot = 0;            // partials of the fp64 (prepared-geometry) apply
+  int ndot32 = 0;          // partials of the fp32 / bf16-data k-loop apply
   float *sqm = nullptr;  // sqrt(minv) in fp32 for the symmetric learned form (lazily)
   ax_gs *gs = nullptr;
   const double *c = nullptr;  // 1/multiplicity (owned by gs)
@@ -318,22 +364,37 @@ int apply_f64(ax_poisson *P, double *w, const double *u, cudaStream_t st) {
   return ax_gs_sum(P->gs, w, st);
 }
 
-int apply_lowp(ax_poisson *P, float *w, const float *u, cudaStream_t st) {
+// dotp: also the per-block partials of u . Ax (kstep_blocks of them)
+int apply_lowp(ax_poisson *P, float *w, const float *u, cudaStream_t st,
+               double *dotp = nullptr) {
   int rc;
   if (P->lowp_mode == 2) {
     auto b = [](const void *x) { return reinterpret_cast<const __nv_bfloat16 *>(x); };
     // u is fp32: the bf16 mode keeps vectors in fp32 and only G, h1 in bf16
     rc = ax::dispatch_kstep_f32u_bf16(P->lx, w, u, P->dx32, P->dxt32, b(P->h1lp), b(P->glp[0]),
                                       b(P->glp[1]), b(P->glp[2]), b(P->glp[3]), b(P->glp[4]),
-                                      b(P->glp[5]), P->nelv, 0, st);
+                                      b(P->glp[5]), P->nelv, 0, st, dotp);
   } else {
     auto f = [](const void *x) { return reinterpret_cast<const float *>(x); };
     rc = ax::dispatch_kstep_f32(P->lx, w, u, P->dx32, P->dxt32, f(P->h1lp), f(P->glp[0]),
                                 f(P->glp[1]), f(P->glp[2]), f(P->glp[3]), f(P->glp[4]),
-                                f(P->glp[5]), P->nelv, 0, st);
+                                f(P->glp[5]), P->nelv, 0, st, dotp);
   }
   if (rc) return rc;
   return ax_gs_sum_f32(P->gs, w, st);
+}
+
+// The fused apply of a solver loop: w = gs(Ax(u)) (unmasked) and the
+// partials of u . Ax in P->dotp; returns the number of partials, or 0 when
+// this precision has no fused form (the caller masks and dots separately).
+int fused_parts(const ax_poisson *P, const double *) { return P->dotp ? P->ndot : 0; }
+int fused_parts(const ax_poisson *P, const float *) { return P->dotp ? P->ndot32 : 0; }
+int apply_fused(ax_poisson *P, double *w, const double *u, cudaStream_t st) {
+  int rc = ax::op_apply_dot(P->op, w, u, P->dotp, st);
+  return rc ? rc : ax_gs_sum(P->gs, w, st);
+}
+int apply_fused(ax_poisson *P, float *w, const float *u, cudaStream_t st) {
+  return apply_lowp(P, w, u, st, P->dotp);
 }
 
 // Generic PCG loop on vectors of type T (fp64 with the fp64 operator, or
@@ -364,14 +425,13 @@ int pcg_loop(ax_poisson *P, T *x, const T *b, T *r, T *p, T *w, const T *mask, c
   // fp64 with prepared geometry: p . Ap comes out of the apply itself (for
   // a continuous, masked p the assembled dot equals the element-local sum
   // of p . A_e p), and the mask moves into the update
-  const bool fused = std::is_same<T, double>::value && P->dotp != nullptr;
+  const int nparts = fused_parts(P, (const T *)nullptr);
+  const bool fused = nparts > 0;
   while (it < maxit) {
     int rc;
     if (fused) {
-      rc = ax::op_apply_dot(P->op, (double *)w, (const double *)p, P->dotp, st);
-      if (rc == AX_OK) rc = ax_gs_sum(P->gs, (double *)w, st);
-      if (rc) return rc;
-      cg_alpha_kernel<<<1, 1024, 0, st>>>(P->dotp, P->ndot, P->scal);
+      if ((rc = apply_fused(P, w, p, st))) return rc;
+      cg_alpha_kernel<<<1, 1024, 0, st>>>(P->dotp, nparts, P->scal);
       cg_update_kernel<T, true><<<nb, kRedThreads, 0, st>>>(x, r, p, w, cm, c, P->scal,
                                                             P->partials, n);
     } else {
@@ -502,7 +562,8 @@ int ax_poisson_create(ax_poisson **out, int lx, int nelv, const double *dx, cons
     return rco;
   }
   P->ndot = ax::op_dot_blocks(P->op);
-  if (P->ndot > 0 && alloc(&P->dotp, (size_t)P->ndot)) {
+  P->ndot32 = ax::kstep_blocks(lx, nelv);
+  if (alloc(&P->dotp, (size_t)std::max(P->ndot, P->ndot32))) {
     ax_poisson_destroy(P);
     return AX_ENOMEM;
   }
@@ -759,15 +820,37 @@ __global__ void fcg_update_kernel(T *__restrict__ x, T *__restrict__ r, T *__res
   __shared__ double sh[kRedThreads / 32];
   const T alpha = (T)s->alpha;
   T a_rr = 0;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    x[q] += alpha * p[q];
-    const T ro = r[q];
-    r_old[q] = ro;
-    const T rv = (MASKW && cm[q] == T(0)) ? ro : ro - alpha * w[q];
-    r[q] = rv;
-    a_rr += c[q] * rv * rv;
+  auto point = [&](T &xq, T &rq, T &roq, T pq, T wq, T cq, T cmq) {
+    xq += alpha * pq;
+    roq = rq;
+    rq = (MASKW && cmq == T(0)) ? rq : rq - alpha * wq;
+    a_rr += cq * rq * rq;
+  };
+  int64_t q0 = 0;
+  if constexpr (sizeof(T) == 4) {
+    if (aligned16(x, r, r_old, p, w, c, cm)) {  // fp32: 16-byte accesses
+      using V = float4;
+      const int64_t n4 = n / 4;
+      for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n4;
+           v += (int64_t)gridDim.x * blockDim.x) {
+        V xv = reinterpret_cast<V *>(x)[v], rv = reinterpret_cast<V *>(r)[v], ov;
+        const V pv = reinterpret_cast<const V *>(p)[v], wv = reinterpret_cast<const V *>(w)[v];
+        const V cv = reinterpret_cast<const V *>(c)[v];
+        const V mv = MASKW ? reinterpret_cast<const V *>(cm)[v] : V{1.f, 1.f, 1.f, 1.f};
+        point(xv.x, rv.x, ov.x, pv.x, wv.x, cv.x, mv.x);
+        point(xv.y, rv.y, ov.y, pv.y, wv.y, cv.y, mv.y);
+        point(xv.z, rv.z, ov.z, pv.z, wv.z, cv.z, mv.z);
+        point(xv.w, rv.w, ov.w, pv.w, wv.w, cv.w, mv.w);
+        reinterpret_cast<V *>(x)[v] = xv;
+        reinterpret_cast<V *>(r)[v] = rv;
+        reinterpret_cast<V *>(r_old)[v] = ov;
+      }
+      q0 = n4 * 4;
+    }
   }
+  for (int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    point(x[q], r[q], r_old[q], p[q], w[q], c[q], MASKW ? cm[q] : T(1));
   double v[1] = {(double)a_rr};
   ax::block_sum<1>(v, sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
@@ -834,11 +917,35 @@ __global__ void fcg_p_kernel(T *__restrict__ p, const T *__restrict__ r,
   const bool uc = s->use_corr != 0;
   // explicit roundings: the Jacobi-only step is the same bits whether or not
   // a (zero) correction is present
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+  auto point = [&](T &pq, T mq, T rq, T cq) {
+    T z = ax::mul_rn(mq, rq);
+    if (uc) z = ax::add_rn(z, cq);
+    pq = first ? z : ax::fma_rn(beta, pq, z);
+  };
+  int64_t q0 = 0;
+  if constexpr (sizeof(T) == 4) {
+    if (aligned16(p, r, minv, corr)) {  // fp32: 16-byte accesses
+      using V = float4;
+      const int64_t n4 = n / 4;
+      for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n4;
+           v += (int64_t)gridDim.x * blockDim.x) {
+        V pv = first ? V{} : reinterpret_cast<V *>(p)[v];
+        const V rv = reinterpret_cast<const V *>(r)[v], mv = reinterpret_cast<const V *>(minv)[v];
+        const V cv = uc ? reinterpret_cast<const V *>(corr)[v] : V{};
+        point(pv.x, mv.x, rv.x, cv.x);
+        point(pv.y, mv.y, rv.y, cv.y);
+        point(pv.z, mv.z, rv.z, cv.z);
+        point(pv.w, mv.w, rv.w, cv.w);
+        reinterpret_cast<V *>(p)[v] = pv;
+      }
+      q0 = n4 * 4;
+    }
+  }
+  for (int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
-    T z = ax::mul_rn(minv[q], r[q]);
-    if (uc) z = ax::add_rn(z, corr[q]);
-    p[q] = first ? z : ax::fma_rn(beta, p[q], z);
+    T pq = first ? T(0) : p[q];
+    point(pq, minv[q], r[q], uc ? corr[q] : T(0));
+    p[q] = pq;
   }
 }
 
@@ -929,13 +1036,12 @@ int fcg_loop(ax_poisson *P, const ax_mlp *M, T *x, const T *b, T *r, T *r_old, T
   int it = 0, status = AX_ENOTCONV;
   if (rr0 == 0.0 || tol >= 1.0) status = AX_OK;
   // fp64 with prepared geometry: p . Ap from the apply itself (see pcg_loop)
-  const bool fused = std::is_same<T, double>::value && P->dotp != nullptr;
+  const int nparts = fused_parts(P, (const T *)nullptr);
+  const bool fused = nparts > 0;
   while (status != AX_OK && it < maxit) {
     if (fused) {
-      rc = ax::op_apply_dot(P->op, (double *)w, (const double *)p, P->dotp, st);
-      if (rc == AX_OK) rc = ax_gs_sum(P->gs, (double *)w, st);
-      if (rc) return rc;
-      cg_alpha_kernel<<<1, 1024, 0, st>>>(P->dotp, P->ndot, P->scal);
+      if ((rc = apply_fused(P, w, p, st))) return rc;
+      cg_alpha_kernel<<<1, 1024, 0, st>>>(P->dotp, nparts, P->scal);
       fcg_update_kernel<T, true><<<nb, kRedThreads, 0, st>>>(x, r, r_old, p, w, c, cm, P->scal,
                                                              P->partials, n);
     } else {

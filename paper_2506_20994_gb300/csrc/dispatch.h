@@ -24,7 +24,7 @@ int dispatch_kstep_f64(int lx, double *w, const double *u, const double *dx, con
 int dispatch_kstep_f32(int lx, float *w, const float *u, const float *dx, const float *dxt,
                        const float *h1, const float *g11, const float *g22, const float *g33,
                        const float *g12, const float *g13, const float *g23, int nelv, int epb,
-                       cudaStream_t st);
+                       cudaStream_t st, double *dotp = nullptr);
 // k-loop kernel: bf16 storage of u, h1, G; fp32 D, arithmetic and w.
 int dispatch_kstep_bf16(int lx, float *w, const __nv_bfloat16 *u, const float *dx,
                         const float *dxt, const __nv_bfloat16 *h1, const __nv_bfloat16 *g11,
@@ -37,7 +37,15 @@ int dispatch_kstep_f32u_bf16(int lx, float *w, const float *u, const float *dx, 
                              const __nv_bfloat16 *h1, const __nv_bfloat16 *g11,
                              const __nv_bfloat16 *g22, const __nv_bfloat16 *g33,
                              const __nv_bfloat16 *g12, const __nv_bfloat16 *g13,
-                             const __nv_bfloat16 *g23, int nelv, int epb, cudaStream_t st);
+                             const __nv_bfloat16 *g23, int nelv, int epb, cudaStream_t st,
+                             double *dotp = nullptr);
+// Blocks (and dot partials) of a k-loop launch with the default elements per
+// block.
+inline int kstep_blocks(int lx, int nelv) {
+  int e = 256 / (lx * lx);
+  e = e < 1 ? 1 : e;
+  return (nelv + e - 1) / e;
+}
 // Even-odd double-float kernel (lx in {4, 6, 8, 10, 12}; AX_EINVAL otherwise).
 int dispatch_df64eo(int lx, double *w, const double *u, const double *dx, const double *dxt,
                     const double *h1, const double *g11, const double *g22, const double *g33,
