@@ -82,7 +82,10 @@ constexpr size_t df64eo_smem(int epb) {
   return 2 * H2 * (16 + 8) + (size_t)epb * 3 * eo::dir_entries<LX>() * 16;
 }
 
-template <int LX, bool PREP = false>
+// PUPD (prepared geometry only): u is not an input; instead the kernel first
+// forms the solver's next search direction in place, pw = minv .* r +
+// (*beta) pw (fp64), and applies the operator to it.
+template <int LX, bool PREP = false, bool PUPD = false>
 __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double *__restrict__ u,
                                             const double *__restrict__ dx,
                                             const double *__restrict__ dxt,
@@ -95,7 +98,11 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
                                             const double *__restrict__ g23,
                                             const df::dd2 *__restrict__ gp, long long e0,
                                             int nel, int epb, unsigned char *smem_raw,
-                                            double *__restrict__ dotp = nullptr) {
+                                            double *__restrict__ dotp = nullptr,
+                                            double *__restrict__ pw = nullptr,
+                                            const double *__restrict__ r_in = nullptr,
+                                            const double *__restrict__ minv_in = nullptr,
+                                            const double *__restrict__ beta_p = nullptr) {
   static_assert(LX % 2 == 0, "even-odd kernel needs an even lx");
   using namespace df;
   constexpr int H = LX / 2, N = LX - 1;
@@ -188,13 +195,31 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
   df2 gr[2][2][2], gs_[2][2][2], gt[2][2][2];
   // ---- phase 1: own values of u, (e, o) along each direction
   if (own) {
+    if constexpr (PUPD) {
+      const double beta = *beta_p;
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+      for (int c = 0; c < 2; ++c)
 #pragma unroll
-      for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < 2; ++b)
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
-          gr[c][b][a] = active ? split(__ldg(u + gidx(c, b, a))) : df2{0.f, 0.f};
+          for (int a = 0; a < 2; ++a) {
+            gr[c][b][a] = df2{0.f, 0.f};
+            if (active) {
+              const size_t q = gidx(c, b, a);
+              const double pn = __fma_rn(beta, pw[q], __dmul_rn(__ldg(minv_in + q), __ldg(r_in + q)));
+              pw[q] = pn;
+              gr[c][b][a] = split(pn);
+            }
+          }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int a = 0; a < 2; ++a)
+            gr[c][b][a] = active ? split(__ldg(u + gidx(c, b, a))) : df2{0.f, 0.f};
+    }
     publish(gr);
   }
   __syncthreads();
@@ -363,8 +388,13 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
           w[gidx(c, b, 0)] = wd0;
           w[gidx(c, b, 1)] = wd1;
           if (dotp) {  // u . Au of this element (u re-read from L2)
-            dsum = __fma_rn(__ldg(u + gidx(c, b, 0)), wd0, dsum);
-            dsum = __fma_rn(__ldg(u + gidx(c, b, 1)), wd1, dsum);
+            if constexpr (PUPD) {  // written above by this thread: coherent loads
+              dsum = __fma_rn(__ldcg(pw + gidx(c, b, 0)), wd0, dsum);
+              dsum = __fma_rn(__ldcg(pw + gidx(c, b, 1)), wd1, dsum);
+            } else {
+              dsum = __fma_rn(__ldg(u + gidx(c, b, 0)), wd0, dsum);
+              dsum = __fma_rn(__ldg(u + gidx(c, b, 1)), wd1, dsum);
+            }
           }
         }
     }
@@ -401,19 +431,23 @@ ax_df64eo_kernel(double *__restrict__ w, const double *__restrict__ u,
 }
 
 // Same operator on geometry prepared by eo_prepare_kernel; DOT adds the
-// per-block partials of u . w.
-template <int LX, bool DOT>
+// per-block partials of u . w; PUPD forms u = pw = minv .* r + beta pw first
+// (see df64eo_body).
+template <int LX, bool DOT, bool PUPD = false>
 __global__ void __launch_bounds__(256, 2)
 ax_df64eo_prep_kernel(double *__restrict__ w, const double *__restrict__ u,
                       const double *__restrict__ dx, const double *__restrict__ dxt,
                       const df::dd2 *__restrict__ gp, int nelv, int epb,
-                      double *__restrict__ dotp) {
+                      double *__restrict__ dotp, double *__restrict__ pw,
+                      const double *__restrict__ r_in, const double *__restrict__ minv_in,
+                      const double *__restrict__ beta_p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long e0 = (long long)blockIdx.x * epb;
   const long long left = nelv - e0;
   const int nel = left < epb ? (int)left : epb;
-  df64eo_body<LX, true>(w, u, dx, dxt, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                        nullptr, gp, e0, nel, epb, smem_raw, DOT ? dotp : nullptr);
+  df64eo_body<LX, true, PUPD>(w, u, dx, dxt, nullptr, nullptr, nullptr, nullptr, nullptr,
+                              nullptr, nullptr, gp, e0, nel, epb, smem_raw,
+                              DOT ? dotp : nullptr, pw, r_in, minv_in, beta_p);
 }
 
 // Prepared geometry: entry ((e*4 + cp)*7 + f)*H3 + t holds field f at the
@@ -482,28 +516,36 @@ int prep_blocks(int nelv, int epb) {
   return (nelv + epb - 1) / epb;
 }
 
+// pw (with dotp, r_in, minv_in, beta_p): the fused direction update.
 template <int LX>
 int launch_df64eo_prep(double *w, const double *u, const double *dx, const double *dxt,
                        const df::dd2 *gp, int nelv, int epb, cudaStream_t stream,
-                       double *dotp = nullptr) {
+                       double *dotp = nullptr, double *pw = nullptr,
+                       const double *r_in = nullptr, const double *minv_in = nullptr,
+                       const double *beta_p = nullptr) {
+  if (pw && !(dotp && r_in && minv_in && beta_p)) return AX_EINVAL;
   constexpr int H3 = (LX / 2) * (LX / 2) * (LX / 2);
   // measured on GB300 (E = 32768 at lx = 8, 13824 at lx = 10): blocks of
   // about 128 threads (4 per SM) beat 256-thread blocks by 8-9 %
   if (epb <= 0) epb = 128 / H3 < 1 ? 1 : 128 / H3;
   if (epb * H3 > 256) return AX_EINVAL;
   const size_t smem = df64eo_smem<LX>(epb);
-  auto kern = dotp ? ax_df64eo_prep_kernel<LX, true> : ax_df64eo_prep_kernel<LX, false>;
-  static size_t granted[2] = {48 * 1024, 48 * 1024};
-  if (smem > granted[dotp != nullptr]) {
+  const int kind = pw ? 2 : dotp ? 1 : 0;
+  auto kern = kind == 2   ? ax_df64eo_prep_kernel<LX, true, true>
+              : kind == 1 ? ax_df64eo_prep_kernel<LX, true>
+                          : ax_df64eo_prep_kernel<LX, false>;
+  static size_t granted[3] = {48 * 1024, 48 * 1024, 48 * 1024};
+  if (smem > granted[kind]) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
       (void)cudaGetLastError();
       return AX_EINVAL;
     }
-    granted[dotp != nullptr] = smem;
+    granted[kind] = smem;
   }
   const unsigned grid = (unsigned)((nelv + epb - 1) / epb);
-  kern<<<grid, epb * H3, smem, stream>>>(w, u, dx, dxt, gp, nelv, epb, dotp);
+  kern<<<grid, epb * H3, smem, stream>>>(w, u, dx, dxt, gp, nelv, epb, dotp, pw, r_in, minv_in,
+                                         beta_p);
   return launch_status();
 }
 

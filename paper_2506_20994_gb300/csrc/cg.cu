@@ -14,6 +14,7 @@
 // weighted by 1/multiplicity.  The scalars of the iteration live on the
 // device; the host reads the residual norm every `check_every` iterations.
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <type_traits>
@@ -396,6 +397,19 @@ int apply_fused(ax_poisson *P, double *w, const double *u, cudaStream_t st) {
 int apply_fused(ax_poisson *P, float *w, const float *u, cudaStream_t st) {
   return apply_lowp(P, w, u, st, P->dotp);
 }
+// The direction update p = minv r + beta p folded into the apply that reads
+// p next (fp64 with prepared geometry); false where no such kernel exists.
+bool fuses_update(const ax_poisson *P, const double *) { return P->dotp && P->ndot > 0; }
+bool fuses_update(const ax_poisson *, const float *) { return false; }
+int apply_fused_update(ax_poisson *P, double *w, double *p, const double *r,
+                       const double *minv, const double *beta, cudaStream_t st) {
+  int rc = ax::op_update_apply_dot(P->op, w, p, r, minv, beta, P->dotp, st);
+  return rc ? rc : ax_gs_sum(P->gs, w, st);
+}
+int apply_fused_update(ax_poisson *, float *, float *, const float *, const float *,
+                       const double *, cudaStream_t) {
+  return AX_EINVAL;
+}
 
 // Generic PCG loop on vectors of type T (fp64 with the fp64 operator, or
 // fp32 with the low-precision operator).  x0 = 0.  Returns AX_OK when
@@ -427,10 +441,17 @@ int pcg_loop(ax_poisson *P, T *x, const T *b, T *r, T *p, T *w, const T *mask, c
   // of p . A_e p), and the mask moves into the update
   const int nparts = fused_parts(P, (const T *)nullptr);
   const bool fused = nparts > 0;
+  // after the first iteration the next direction is formed inside the apply
+  const bool fused_p = fused && fuses_update(P, (const T *)nullptr);
   while (it < maxit) {
     int rc;
     if (fused) {
-      if ((rc = apply_fused(P, w, p, st))) return rc;
+      // device address of the beta field (P->scal lives on the device)
+      const double *beta_dev = reinterpret_cast<const double *>(
+          reinterpret_cast<const char *>(P->scal) + offsetof(CgScalars, beta));
+      rc = (fused_p && it > 0) ? apply_fused_update(P, w, p, r, minv, beta_dev, st)
+                               : apply_fused(P, w, p, st);
+      if (rc) return rc;
       cg_alpha_kernel<<<1, 1024, 0, st>>>(P->dotp, nparts, P->scal);
       cg_update_kernel<T, true><<<nb, kRedThreads, 0, st>>>(x, r, p, w, cm, c, P->scal,
                                                             P->partials, n);
@@ -459,7 +480,7 @@ int pcg_loop(ax_poisson *P, T *x, const T *b, T *r, T *p, T *w, const T *mask, c
         break;
       }
     }
-    cg_p_kernel<T><<<nb, kRedThreads, 0, st>>>(p, r, minv, P->scal, n);
+    if (!fused_p) cg_p_kernel<T><<<nb, kRedThreads, 0, st>>>(p, r, minv, P->scal, n);
   }
   if (ax::launch_status()) return AX_ELAUNCH;
   if (iters) *iters = it;

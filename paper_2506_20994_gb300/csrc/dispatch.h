@@ -57,9 +57,13 @@ inline bool df64eo_supported(int lx) { return lx >= 4 && lx <= 12 && lx % 2 == 0
 // (bits 0-5 g11, g22, g33, g12, g13, g23; bit 6 h1).
 // dotp (optional): per-block partial sums of u . w, df64eo_prep_blocks(lx,
 // nelv) of them (default elements per block).
+// pw, r_in, minv_in, beta_p (optional, with dotp): u is replaced by the
+// search direction formed in place, pw = minv_in .* r_in + (*beta_p) pw.
 int dispatch_df64eo_prep(int lx, double *w, const double *u, const double *dx,
                          const double *dxt, const df::dd2 *gp, int nelv, int epb,
-                         cudaStream_t st, double *dotp = nullptr);
+                         cudaStream_t st, double *dotp = nullptr, double *pw = nullptr,
+                         const double *r_in = nullptr, const double *minv_in = nullptr,
+                         const double *beta_p = nullptr);
 int df64eo_prep_blocks(int lx, int nelv);
 int dispatch_eo_prepare(int lx, df::dd2 *gp, const double *h1, const double *g11,
                         const double *g22, const double *g33, const double *g12,

@@ -100,6 +100,13 @@ int op_apply_dot(ax_op *op, double *w, const double *u, double *partials, cudaSt
   return dispatch_df64eo_prep(op->lx, w, u, op->dx, op->dxt, op->gp, op->nelv, 0, st, partials);
 }
 
+int op_update_apply_dot(ax_op *op, double *w, double *p, const double *r, const double *minv,
+                        const double *beta, double *partials, cudaStream_t st) {
+  if (!op || !op->gp || !partials || !p || !r || !minv || !beta) return AX_EINVAL;
+  return dispatch_df64eo_prep(op->lx, w, nullptr, op->dx, op->dxt, op->gp, op->nelv, 0, st,
+                              partials, p, r, minv, beta);
+}
+
 }  // namespace ax
 
 extern "C" int ax_op_info(const ax_op *op, int *prepared, int64_t *device_bytes) {

@@ -13,5 +13,10 @@ int op_dot_blocks(const ax_op *op);
 // w = Ax(u) as ax_op_apply, plus partials[b] = sum over block b's elements
 // of u . w (element-local, before any gather-scatter; fixed order).
 int op_apply_dot(ax_op *op, double *w, const double *u, double *partials, cudaStream_t st);
+// The solver's direction update fused in front of the same apply:
+// p = minv .* r + (*beta) p in place (fp64), then w = Ax(p) and the partials
+// of p . w.  beta is a device scalar.
+int op_update_apply_dot(ax_op *op, double *w, double *p, const double *r, const double *minv,
+                        const double *beta, double *partials, cudaStream_t st);
 
 }  // namespace ax
