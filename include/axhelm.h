@@ -310,7 +310,11 @@ typedef struct {
 /* Builds the plan (host array meshes[nmesh], copied; the device arrays are
  * borrowed and must outlive the plan).  blocks_per_sm <= 0 picks the
  * default residency.  Allocates the device work list; synchronises stream.
- * Uses the tuned elements-per-block of each lx (ax_tune_*), else a default. */
+ * Uses the tuned elements-per-block of each lx (ax_tune_*), else a default.
+ * For AX_BATCH_F64 meshes with lx in {8, 10, 12} the plan also keeps a copy
+ * of h1 and G prepared for the even-odd kernel (56 lx^3 bytes per element,
+ * as ax_op_create; results equal ax_op_apply's bit for bit); a change of
+ * those meshes' h1 or G needs a new plan. */
 int ax_batch_create(ax_batch **B, int dtype, int nmesh, const ax_batch_mesh *meshes,
                     int blocks_per_sm, void *stream);
 /* All meshes of the plan in one persistent kernel launch (asynchronous). */

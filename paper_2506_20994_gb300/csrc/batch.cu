@@ -12,7 +12,8 @@
 // walk their own contiguous item list; there are no atomics and no
 // inter-block waits.  Each item runs the same device body as the
 // single-mesh kernel (ax_df64.cuh / ax_df64_eo.cuh / ax_kstep.cuh), so the
-// results are bit-identical to ax_helm / ax_helm_f32.  One kernel per lx
+// results are bit-identical to ax_helm / ax_helm_f32, or, for fp64 meshes
+// with lx in {8, 10, 12}, to the operator handle (geometry prepared here).  One kernel per lx
 // (rather than one kernel switching over lx) keeps each kernel's register
 // footprint, and so its occupancy, that of its single-mesh counterpart.
 #include <algorithm>
@@ -83,6 +84,7 @@ struct ax_batch {
   size_t smem = 0;
   std::vector<Group> groups;
   BatchMeshDev *d_mesh = nullptr;
+  std::vector<void *> prepared;  // owned prepared geometry of even-odd fp64 meshes
   BatchItem *d_items = nullptr;
   int *d_start = nullptr;
   cudaGraph_t graph = nullptr;
@@ -113,6 +115,7 @@ int ax_batch_destroy(ax_batch *B) {
   cudaFree(B->d_mesh);
   cudaFree(B->d_items);
   cudaFree(B->d_start);
+  for (void *q : B->prepared) cudaFree(q);
   delete B;
   return AX_OK;
 }
@@ -146,7 +149,7 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
       epb = std::min(epb, kBatchThreads / (s.lx * s.lx));
     }
     mh[m] = BatchMeshDev{s.lx, epb, s.w, s.u, s.dx, s.dxt, s.h1,
-                         {s.g11, s.g22, s.g33, s.g12, s.g13, s.g23}};
+                         {s.g11, s.g22, s.g33, s.g12, s.g13, s.g23}, nullptr};
     smem[s.lx] = std::max(smem[s.lx], body_smem(f64, s.lx, epb));
     const double l = s.lx, l3 = l * l * l;
     for (long long e = 0; e < s.nelv; e += epb) {
@@ -205,6 +208,28 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
   }
   ax_batch *B = new (std::nothrow) ax_batch();
   if (!B) return AX_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  // fp64 meshes of the even-odd orders: prepare their geometry once
+  for (int m = 0; f64 && m < nmesh; ++m) {
+    const ax_batch_mesh &s = meshes[m];
+    if (!ax::batch_uses_eo(s.lx) || s.nelv == 0) continue;
+    void *gp = nullptr;
+    if (cudaMalloc(&gp, (size_t)s.nelv * 56 * s.lx * s.lx * s.lx) != cudaSuccess) {
+      (void)cudaGetLastError();
+      ax_batch_destroy(B);
+      return AX_ENOMEM;
+    }
+    B->prepared.push_back(gp);
+    auto d = [](const void *q) { return static_cast<const double *>(q); };
+    int rc = ax::dispatch_eo_prepare(s.lx, static_cast<ax::df::dd2 *>(gp), d(s.h1), d(s.g11),
+                                     d(s.g22), d(s.g33), d(s.g12), d(s.g13), d(s.g23), s.nelv,
+                                     0x7F, st);
+    if (rc) {
+      ax_batch_destroy(B);
+      return rc;
+    }
+    mh[m].gp = static_cast<const ax::df::dd2 *>(gp);
+  }
   B->dtype = dtype;
   B->nmesh = nmesh;
   B->nitems = (int)flat.size();
@@ -213,7 +238,6 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
   B->smem = smem_max;
   B->flops = flops;
   B->bytes = bytes;
-  cudaStream_t st = (cudaStream_t)stream;
   bool ok = cudaMalloc(&B->d_mesh, std::max<size_t>(1, mh.size()) * sizeof(BatchMeshDev)) ==
                 cudaSuccess &&
             cudaMalloc(&B->d_items, std::max<size_t>(1, flat.size()) * sizeof(BatchItem)) ==

@@ -2,7 +2,8 @@
 // kernel per (dtype, lx), each block walking its own statically assigned
 // list of work items and running the single-mesh device body on each, so
 // that every kernel keeps the register footprint and occupancy of its
-// single-mesh counterpart.
+// single-mesh counterpart.  fp64 meshes of the even-odd orders run on
+// geometry the plan prepared once (as the operator handle does).
 #pragma once
 
 #include "ax_df64.cuh"
@@ -15,6 +16,7 @@ struct BatchMeshDev {
   int lx, epb;
   void *w;
   const void *u, *dx, *dxt, *h1, *g[6];
+  const df::dd2 *gp;  // geometry prepared for the even-odd kernel, or null
 };
 
 struct BatchItem {
@@ -39,11 +41,10 @@ batch_lx_kernel(const BatchMeshDev *__restrict__ meshes, const BatchItem *__rest
     const BatchItem itm = items[it];
     const BatchMeshDev m = meshes[itm.mesh];
     if constexpr (F64 && batch_uses_eo(LX)) {
-      df64eo_body<LX>((double *)m.w, (const double *)m.u, (const double *)m.dx,
-                      (const double *)m.dxt, (const double *)m.h1, (const double *)m.g[0],
-                      (const double *)m.g[1], (const double *)m.g[2], (const double *)m.g[3],
-                      (const double *)m.g[4], (const double *)m.g[5], nullptr, itm.e0,
-                      itm.nel, m.epb, smem_raw);
+      // every mesh of these orders has prepared geometry (the plan made it)
+      df64eo_body<LX, true>((double *)m.w, (const double *)m.u, (const double *)m.dx,
+                            (const double *)m.dxt, nullptr, nullptr, nullptr, nullptr, nullptr,
+                            nullptr, nullptr, m.gp, itm.e0, itm.nel, m.epb, smem_raw);
     } else if constexpr (F64) {
       df64_body<LX>((double *)m.w, (const double *)m.u, (const double *)m.dx,
                     (const double *)m.dxt, (const double *)m.h1, (const double *)m.g[0],
