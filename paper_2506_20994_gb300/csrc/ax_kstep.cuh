@@ -29,7 +29,9 @@ constexpr bool kPrefetchGeometry = true;
 AX_D double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
 AX_D float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
-template <int LX, typename SU, typename S, typename T, typename W>
+// AHEAD: geometry loads one k-plane ahead (measured faster for the
+// single-mesh fp32-storage kernel only).
+template <int LX, typename SU, typename S, typename T, typename W, bool AHEAD = false>
 __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restrict__ u,
                                            const T *__restrict__ dx, const T *__restrict__ dxt,
                                            const S *__restrict__ h1, const S *__restrict__ g11,
@@ -74,12 +76,33 @@ __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restri
   }
   __syncthreads();
 
+  // geometry of one k-plane; with AHEAD loaded one plane ahead of its use so
+  // that the loads are in flight during the previous plane's contractions
+  constexpr bool kAhead = AHEAD;
+  auto load_plane = [&](int k, T (&g)[7]) {
+    const size_t q = base + (size_t)k * N2;
+    g[0] = ld_cvt<T>(g11 + q);
+    g[1] = ld_cvt<T>(g22 + q);
+    g[2] = ld_cvt<T>(g33 + q);
+    g[3] = ld_cvt<T>(g12 + q);
+    g[4] = ld_cvt<T>(g13 + q);
+    g[5] = ld_cvt<T>(g23 + q);
+    g[6] = ld_cvt<T>(h1 + q);
+  };
+  T gcur[7], gnext[7];
+  if (kAhead && active) load_plane(0, gnext);
+
   T wacc[LX];
   if (own) {
 #pragma unroll
     for (int k = 0; k < LX; ++k) wacc[k] = T(0);
 #pragma unroll
     for (int k = 0; k < LX; ++k) {
+      if constexpr (kAhead) {
+#pragma unroll
+        for (int f = 0; f < 7; ++f) gcur[f] = gnext[f];
+        if (active && k + 1 < LX) load_plane(k + 1, gnext);
+      }
       T ur = T(0), us = T(0), ut = T(0);
 #pragma unroll
       for (int l = 0; l < LX; ++l) {
@@ -89,10 +112,9 @@ __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restri
       }
       T wr = T(0), ws = T(0), wt = T(0);
       if (active) {
-        const size_t q = base + (size_t)k * N2;
-        const T a11 = ld_cvt<T>(g11 + q), a22 = ld_cvt<T>(g22 + q), a33 = ld_cvt<T>(g33 + q);
-        const T a12 = ld_cvt<T>(g12 + q), a13 = ld_cvt<T>(g13 + q), a23 = ld_cvt<T>(g23 + q);
-        const T hh = ld_cvt<T>(h1 + q);
+        if constexpr (!kAhead) load_plane(k, gcur);
+        const T a11 = gcur[0], a22 = gcur[1], a33 = gcur[2];
+        const T a12 = gcur[3], a13 = gcur[4], a23 = gcur[5], hh = gcur[6];
         wr = hh * (a11 * ur + a12 * us + a13 * ut);
         ws = hh * (a12 * ur + a22 * us + a23 * ut);
         wt = hh * (a13 * ur + a23 * us + a33 * ut);
@@ -148,8 +170,9 @@ ax_kstep_kernel(W *__restrict__ w, const SU *__restrict__ u, const T *__restrict
   const long long e0 = (long long)blockIdx.x * epb;
   const long long left = nelv - e0;
   const int nel = left < epb ? (int)left : epb;
-  kstep_body<LX, SU, S, T, W>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, e0, nel, epb,
-                              smem_raw, DOT ? dotp : nullptr);
+  constexpr bool ahead = sizeof(S) == 4 && sizeof(T) == 4;
+  kstep_body<LX, SU, S, T, W, ahead>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, e0, nel,
+                                     epb, smem_raw, DOT ? dotp : nullptr);
 }
 
 // Shared-memory bytes of one block of the k-loop kernel.
