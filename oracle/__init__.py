@@ -260,6 +260,16 @@ def ax_helm(u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx,
     return w
 
 
+def ax_helm_h2(u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx, h2, B) -> np.ndarray:
+    """Helmholtz form w = A u + h2 B u: the stiffness apply of Listing 2 plus
+    the mass term with coefficient h2 (B the diagonal mass, jac * W).  The
+    paper's listing is h1-only; the h2 term is the other half of Neko's
+    Helmholtz operator, added pointwise."""
+    w = ax_helm(u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx)
+    flat = lambda a: np.asarray(a, dtype=np.float64).reshape(-1)
+    return w + (flat(h2) * flat(B) * flat(u)).reshape(w.shape)
+
+
 def gs_sum(v: np.ndarray, glob: np.ndarray) -> np.ndarray:
     """Direct-stiffness summation: every copy of a global node gets the sum
     over all its local copies (C loop, dense scatter-add then gather)."""
@@ -302,9 +312,11 @@ def jacobi_diagonal(dx, h1, g11, g22, g33, g12, g13, g23, lx) -> np.ndarray:
 
 class Problem:
     """A Poisson problem on a perturbed box: operator data, numbering, mask,
-    multiplicity, right-hand side.  ``apply(p)`` is mask(gs(Ax(p)))."""
+    multiplicity, right-hand side.  ``apply(p)`` is mask(gs(Ax(p))); with h2
+    the Helmholtz problem -div(h1 grad u) + h2 u = f, ``apply(p)`` then
+    mask(gs(Ax(p) + h2 B p))."""
 
-    def __init__(self, vertices: np.ndarray, lx: int, h1=None, f=None):
+    def __init__(self, vertices: np.ndarray, lx: int, h1=None, f=None, h2=None):
         nz, ny, nx = (s - 1 for s in vertices.shape[:3])
         self.nx, self.ny, self.nz, self.lx = nx, ny, nz, lx
         self.geo = box_geometry(vertices, lx)
@@ -316,7 +328,12 @@ class Problem:
         self.mult = multiplicity(self.glob)
         g = self.geo
         self.G = (g["g11"], g["g22"], g["g33"], g["g12"], g["g13"], g["g23"])
-        self.diag = gs_sum(jacobi_diagonal(self.dx, self.h1, *self.G, lx), self.glob)
+        self.h2 = None if h2 is None else np.broadcast_to(
+            np.asarray(h2, dtype=np.float64), shp).copy()
+        dloc = jacobi_diagonal(self.dx, self.h1, *self.G, lx)
+        if self.h2 is not None:
+            dloc = dloc + self.h2 * g["B"]
+        self.diag = gs_sum(dloc, self.glob)
         if f is not None:
             x = g["xyz"]
             fv = f(x[..., 0], x[..., 1], x[..., 2])
@@ -325,6 +342,9 @@ class Problem:
             self.b = None
 
     def ax_local(self, p):
+        if self.h2 is not None:
+            return ax_helm_h2(p, self.dx, self.dxt, self.h1, *self.G, self.lx, self.h2,
+                              self.geo["B"]).reshape(p.shape)
         return ax_helm(p, self.dx, self.dxt, self.h1, *self.G, self.lx).reshape(p.shape)
 
     def apply(self, p):
