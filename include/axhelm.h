@@ -98,6 +98,21 @@ int ax_helm_bf16(float *w, const ax_bf16 *u, const float *dx, const float *dxt,
                  const ax_bf16 *g33, const ax_bf16 *g12, const ax_bf16 *g13,
                  const ax_bf16 *g23, int lx, int nelv, void *stream);
 
+/* Helmholtz form: w = Ax(u) + h2 .* B .* u, the stiffness apply above plus
+ * the mass term with a coefficient h2 (B the diagonal mass matrix, jac *
+ * w_i w_j w_k, in the element-major layout).  The paper's listing is
+ * h1-only; the h2 term is the other half of Neko's Helmholtz operator.
+ * fp64-accurate stiffness part, fp64 mass part (one extra pass).  Same
+ * errors as ax_helm (h2 and B must not be NULL when nelv > 0). */
+int ax_helm_h2(double *w, const double *u, const double *dx, const double *dxt,
+               const double *h1, const double *g11, const double *g22, const double *g33,
+               const double *g12, const double *g13, const double *g23, const double *h2,
+               const double *B, int lx, int nelv, void *stream);
+/* w += hb .* u over n points (device fp64 / fp32): the mass term with its
+ * coefficient folded in (hb = h2 .* B). */
+int ax_mass_add(double *w, const double *hb, const double *u, int64_t n, void *stream);
+int ax_mass_add_f32(float *w, const float *hb, const float *u, int64_t n, void *stream);
+
 /* ------------------------------------------------------------------------
  * Operator handle for repeated applies on one mesh (the paper's interface
  * passes an opaque handle first, Listing 1; here it owns per-mesh state).
@@ -121,6 +136,10 @@ int ax_op_create(ax_op **op, int lx, int nelv, const double *dx, const double *d
 int ax_op_apply(ax_op *op, double *w, const double *u, void *stream);
 /* New coefficient h1 (borrowed; the prepared copy is refreshed on stream). */
 int ax_op_set_h1(ax_op *op, const double *h1, void *stream);
+/* Adds the Helmholtz mass term: apply becomes w = Ax(u) + h2 .* B .* u.  The
+ * handle keeps hb = h2 .* B (device, owned; computed on stream); h2 = NULL
+ * removes the term.  Returns AX_ENOMEM if hb cannot be allocated. */
+int ax_op_set_h2(ax_op *op, const double *h2, const double *B, void *stream);
 /* Whether the geometry is prepared and how many device bytes that holds. */
 int ax_op_info(const ax_op *op, int *prepared, int64_t *device_bytes);
 int ax_op_destroy(ax_op *op);
@@ -173,6 +192,14 @@ int ax_poisson_destroy(ax_poisson *P);
 int ax_poisson_apply(ax_poisson *P, double *w, const double *u, void *stream);
 /* Device array of the masked inverse Jacobi diagonal, owned by P. */
 int ax_poisson_jacobi(const ax_poisson *P, const double **minv);
+/* Makes the problem Helmholtz, -div(h1 grad u) + h2 u = f: the operator
+ * gains h2 .* B .* u (B the diagonal mass, device fp64 arrays of n points,
+ * read here; the handle keeps h2 .* B) and the Jacobi diagonal h2 .* B.
+ * Every solver then solves the Helmholtz system; the fused p.Ap of the fp64
+ * solvers stays on (the mass part's u . hb . u is added by the mass pass).
+ * Call before the first mixed-precision solve or again after it (the fp32
+ * copies are refreshed).  Synchronises stream. */
+int ax_poisson_set_h2(ax_poisson *P, const double *h2, const double *B, void *stream);
 /* The assembled Jacobi diagonal before masking and inversion:
  * diag = gs(diag_e(A)) over this handle's gather-scatter (exact element
  * diagonal, reading of the Jacobi preconditioner in the oracle).  diag is a

@@ -25,7 +25,7 @@ __all__ = [
     "AX_VARIANT_F64_NATIVE", "AX_VARIANT_F64_DF_EO", "df64_roundtrip", "build", "GatherScatter", "Poisson",
     "AX_PREC_F32", "AX_PREC_BF16", "Batch", "tune", "tune_set", "tune_get", "AX_BATCH_F64",
     "AX_BATCH_F32", "fourier_coefficient", "Mlp", "mlp_init_params", "training_pairs", "train_mlp", "axpby", "iterate_pairs",
-    "train_energy", "AX_MLP_TANH", "AX_MLP_SYM", "Operator",
+    "train_energy", "AX_MLP_TANH", "AX_MLP_SYM", "Operator", "ax_helm_h2",
 ]
 
 
@@ -138,6 +138,13 @@ def ax_helm(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx: int,
     check("ax_helm", rc)
 
 
+def ax_helm_h2(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, h2, B, lx: int) -> None:
+    """Helmholtz form w = Ax(u) + h2 .* B .* u (fp64 CUDA tensors)."""
+    ts = [w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, h2, B]
+    nelv = u.numel() // lx ** 3
+    check("ax_helm_h2", lib().ax_helm_h2(*[t.data_ptr() for t in ts], lx, nelv, _stream()))
+
+
 def ax_helm_f32(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx: int) -> None:
     """fp32 storage and arithmetic (ax_helm_f32)."""
     import torch
@@ -196,6 +203,12 @@ class Operator:
     def set_h1(self, h1) -> None:
         check("ax_op_set_h1", lib().ax_op_set_h1(self._h, h1.data_ptr(), _stream()))
         self._keep[2] = h1
+
+    def set_h2(self, h2, B) -> None:
+        """Adds the Helmholtz mass term h2 .* B .* u (h2 None removes it)."""
+        check("ax_op_set_h2", lib().ax_op_set_h2(
+            self._h, None if h2 is None else h2.data_ptr(),
+            None if B is None else B.data_ptr(), _stream()))
 
     def info(self):
         import ctypes
@@ -276,10 +289,11 @@ class Poisson:
     GKEYS = ("g11", "g22", "g33", "g12", "g13", "g23")
 
     def __init__(self, vertices: np.ndarray, lx: int, h1=None, device=None,
-                 dirichlet=(True, True, True, True, True, True)):
+                 dirichlet=(True, True, True, True, True, True), h2=None):
         """dirichlet: which faces (x0, x1, y0, y1, z0, z1) carry the
         homogeneous Dirichlet condition; a face left open is an interface to
-        another partition (see ``dist``)."""
+        another partition (see ``dist``).  h2 (callable, array or scalar)
+        makes it the Helmholtz problem -div(h1 grad u) + h2 u = f."""
         import ctypes
         import torch
         self.device = torch.device("cuda") if device is None else torch.device(device)
@@ -322,6 +336,15 @@ class Poisson:
             check("ax_poisson_create", rc)
         self._h = h
         self.shape = mask.shape
+        if h2 is not None:
+            if callable(h2):
+                h2 = h2(self.xyz[..., 0], self.xyz[..., 1], self.xyz[..., 2])
+            h2v = np.broadcast_to(np.asarray(h2, dtype=np.float64).reshape(
+                mask.shape) if np.size(h2) == mask.size else np.asarray(h2, dtype=np.float64),
+                mask.shape).copy()
+            self.d["h2"] = t(h2v)
+            check("ax_poisson_set_h2", lib().ax_poisson_set_h2(
+                self._h, self.d["h2"].data_ptr(), self.mass.data_ptr(), _stream()))
 
     def rhs(self, f) -> "torch.Tensor":
         """b = mask .* gs(B f) for a callable f(x, y, z) (evaluated on host)."""

@@ -55,6 +55,11 @@ PROTOTYPES = {
     "ax_jacobi_noalloc": (c_int, [P] * 10 + [c_void_p, c_int, c_int, c_void_p]),
     "ax_mlp_create": (c_int, [P, c_int, c_int]),
     "ax_mlp_create_ex": (c_int, [P, c_int, c_int, c_int]),
+    "ax_helm_h2": (c_int, [P] * 13 + [c_int, c_int, P]),
+    "ax_mass_add": (c_int, [P, P, P, c_int64, P]),
+    "ax_mass_add_f32": (c_int, [P, P, P, c_int64, P]),
+    "ax_op_set_h2": (c_int, [P, P, P, P]),
+    "ax_poisson_set_h2": (c_int, [P, P, P, P]),
     "ax_op_create": (c_int, [P, c_int, c_int] + [P] * 9 + [P]),
     "ax_op_apply": (c_int, [P, P, P, P]),
     "ax_op_set_h1": (c_int, [P, P, P]),

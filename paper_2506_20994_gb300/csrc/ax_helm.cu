@@ -2,6 +2,7 @@
 // and dispatch over lx and storage type to the templated kernels.
 #include "common.cuh"
 #include "dispatch.h"
+#include "op.h"
 
 namespace {
 
@@ -62,6 +63,16 @@ int ax_helm_variant(int variant, double *w, const double *u, const double *dx,
     default:
       return AX_EINVAL;
   }
+}
+
+int ax_helm_h2(double *w, const double *u, const double *dx, const double *dxt,
+               const double *h1, const double *g11, const double *g22, const double *g33,
+               const double *g12, const double *g13, const double *g23, const double *h2,
+               const double *B, int lx, int nelv, void *stream) {
+  if (nelv > 0 && !ax::all_nonnull(h2, B)) return AX_EINVAL;
+  int rc = ax_helm(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx, nelv, stream);
+  if (rc || nelv == 0) return rc;
+  return ax::mass_add2(w, h2, B, u, (int64_t)nelv * lx * lx * lx, (cudaStream_t)stream);
 }
 
 int ax_helm(double *w, const double *u, const double *dx, const double *dxt, const double *h1,

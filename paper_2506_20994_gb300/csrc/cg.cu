@@ -267,6 +267,19 @@ __global__ void cg_p_kernel(T *__restrict__ p, const T *__restrict__ r,
     p[q] = minv[q] * r[q] + beta * p[q];
 }
 
+// out = a .* b; out += a
+__global__ void mul_kernel(double *__restrict__ out, const double *__restrict__ a,
+                           const double *__restrict__ b, int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    out[q] = a[q] * b[q];
+}
+__global__ void add_kernel(double *__restrict__ out, const double *__restrict__ a, int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    out[q] += a[q];
+}
+
 // fp64 -> fp32 / bf16 conversions and the fp64 refinement updates
 __global__ void to_f32_kernel(float *__restrict__ out, const double *__restrict__ in, int64_t n) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
@@ -327,6 +340,8 @@ struct ax_poisson {
   int ndot = 0;            // partials of the fp64 (prepared-geometry) apply
   int ndot32 = 0;          // partials of the fp32 / bf16-data k-loop apply
   float *sqm = nullptr;  // sqrt(minv) in fp32 for the symmetric learned form (lazily)
+  double *hb = nullptr;  // h2 .* B of the Helmholtz problem, or null (Poisson)
+  float *hb32 = nullptr;  // its fp32 copy for the mixed-precision solves
   ax_gs *gs = nullptr;
   const double *c = nullptr;  // 1/multiplicity (owned by gs)
   // owned fp64 work
@@ -361,6 +376,7 @@ int alloc(T **p, size_t count) {
 
 int apply_f64(ax_poisson *P, double *w, const double *u, cudaStream_t st) {
   int rc = ax_op_apply(P->op, w, u, st);
+  if (rc == AX_OK && P->hb) rc = ax::mass_add<double>(w, P->hb, u, P->n, nullptr, st);
   if (rc) return rc;
   return ax_gs_sum(P->gs, w, st);
 }
@@ -381,6 +397,8 @@ int apply_lowp(ax_poisson *P, float *w, const float *u, cudaStream_t st,
                                 f(P->glp[1]), f(P->glp[2]), f(P->glp[3]), f(P->glp[4]),
                                 f(P->glp[5]), P->nelv, 0, st, dotp);
   }
+  if (rc == AX_OK && P->hb32)  // the mass term's partials follow the kernel's
+    rc = ax::mass_add<float>(w, P->hb32, u, P->n, dotp ? dotp + P->ndot32 : nullptr, st);
   if (rc) return rc;
   return ax_gs_sum_f32(P->gs, w, st);
 }
@@ -388,10 +406,19 @@ int apply_lowp(ax_poisson *P, float *w, const float *u, cudaStream_t st,
 // The fused apply of a solver loop: w = gs(Ax(u)) (unmasked) and the
 // partials of u . Ax in P->dotp; returns the number of partials, or 0 when
 // this precision has no fused form (the caller masks and dots separately).
-int fused_parts(const ax_poisson *P, const double *) { return P->dotp ? P->ndot : 0; }
-int fused_parts(const ax_poisson *P, const float *) { return P->dotp ? P->ndot32 : 0; }
+// (With a mass term its kRedBlocks partials follow the operator's.)
+int fused_parts(const ax_poisson *P, const double *) {
+  return P->dotp && P->ndot ? P->ndot + (P->hb ? kRedBlocks : 0) : 0;
+}
+int fused_parts(const ax_poisson *P, const float *) {
+  return P->dotp ? P->ndot32 + (P->hb32 ? kRedBlocks : 0) : 0;
+}
+int mass_fused(ax_poisson *P, double *w, const double *u, cudaStream_t st) {
+  return P->hb ? ax::mass_add<double>(w, P->hb, u, P->n, P->dotp + P->ndot, st) : AX_OK;
+}
 int apply_fused(ax_poisson *P, double *w, const double *u, cudaStream_t st) {
   int rc = ax::op_apply_dot(P->op, w, u, P->dotp, st);
+  if (rc == AX_OK) rc = mass_fused(P, w, u, st);
   return rc ? rc : ax_gs_sum(P->gs, w, st);
 }
 int apply_fused(ax_poisson *P, float *w, const float *u, cudaStream_t st) {
@@ -404,6 +431,7 @@ bool fuses_update(const ax_poisson *, const float *) { return false; }
 int apply_fused_update(ax_poisson *P, double *w, double *p, const double *r,
                        const double *minv, const double *beta, cudaStream_t st) {
   int rc = ax::op_update_apply_dot(P->op, w, p, r, minv, beta, P->dotp, st);
+  if (rc == AX_OK) rc = mass_fused(P, w, p, st);
   return rc ? rc : ax_gs_sum(P->gs, w, st);
 }
 int apply_fused_update(ax_poisson *, float *, float *, const float *, const float *,
@@ -523,6 +551,10 @@ int ensure_lowp(ax_poisson *P, int mode, cudaStream_t st) {
   to_f32_kernel<<<nb, kRedThreads, 0, st>>>(P->cm32, P->cm, n);
   to_f32_kernel<<<1, 256, 0, st>>>(P->dx32, P->dx, (int64_t)lx2);
   to_f32_kernel<<<1, 256, 0, st>>>(P->dxt32, P->dxt, (int64_t)lx2);
+  if (P->hb) {  // the Helmholtz mass term of the inner operator
+    if (!P->hb32 && alloc(&P->hb32, n)) return AX_ENOMEM;
+    to_f32_kernel<<<nb, kRedThreads, 0, st>>>(P->hb32, P->hb, n);
+  }
   if (ax::launch_status()) return AX_ELAUNCH;
   P->lowp_mode = mode;
   return AX_OK;
@@ -548,6 +580,8 @@ int ax_poisson_destroy(ax_poisson *P) {
   if (P->op) ax_op_destroy(P->op);
   cudaFree(P->dotp);
   cudaFree(P->sqm);
+  cudaFree(P->hb);
+  cudaFree(P->hb32);
   cudaFree(P->scal);
   if (P->scal_host) cudaFreeHost(P->scal_host);
   delete P;
@@ -584,7 +618,7 @@ int ax_poisson_create(ax_poisson **out, int lx, int nelv, const double *dx, cons
   }
   P->ndot = ax::op_dot_blocks(P->op);
   P->ndot32 = ax::kstep_blocks(lx, nelv);
-  if (alloc(&P->dotp, (size_t)std::max(P->ndot, P->ndot32))) {
+  if (alloc(&P->dotp, (size_t)std::max(P->ndot, P->ndot32) + kRedBlocks)) {
     ax_poisson_destroy(P);
     return AX_ENOMEM;
   }
@@ -652,6 +686,28 @@ int ax_poisson_set_diag(ax_poisson *P, const double *diag, void *stream) {
     to_f32_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(P->cm32, P->cm, n);
   }
   return ax::launch_status();
+}
+
+int ax_poisson_set_h2(ax_poisson *P, const double *h2, const double *B, void *stream) {
+  if (!P || !h2 || !B) return AX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = P->n;
+  if (!P->hb && alloc(&P->hb, n)) return AX_ENOMEM;
+  mul_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(P->hb, h2, B, n);
+  // Jacobi diagonal: the stiffness diagonal plus h2 .* B, assembled
+  jacobi_diag_kernel<<<blocks_for(n, 256), 256, 0, st>>>(P->w, P->dx, P->h1, P->g[0], P->g[1],
+                                                         P->g[2], P->g[3], P->g[4], P->g[5],
+                                                         P->lx, n);
+  add_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(P->w, P->hb, n);
+  int rc = ax_gs_sum(P->gs, P->w, st);
+  if (rc == AX_OK) rc = ax_poisson_set_diag(P, P->w, stream);
+  if (rc == AX_OK && P->lowp_mode) {
+    if (!P->hb32 && alloc(&P->hb32, n)) return AX_ENOMEM;
+    to_f32_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(P->hb32, P->hb, n);
+  }
+  if (rc == AX_OK) rc = ax::launch_status();
+  if (rc == AX_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = AX_ELAUNCH;
+  return rc;
 }
 
 int ax_poisson_jacobi(const ax_poisson *P, const double **minv) {

@@ -4,6 +4,7 @@
 // prepared order (converted once here), so each apply reads the same bytes
 // per point as from the fp64 arrays but spends no instruction on converting
 // them.
+#include <algorithm>
 #include <new>
 
 #include "../../include/axhelm.h"
@@ -15,7 +16,17 @@ struct ax_op {
   int lx = 0, nelv = 0;
   const double *dx = nullptr, *dxt = nullptr, *h1 = nullptr, *g[6] = {};
   ax::df::dd2 *gp = nullptr;  // prepared geometry (owned), or null
+  double *hb = nullptr;       // h2 .* B of the Helmholtz form (owned), or null
 };
+
+namespace {
+__global__ void hb_kernel(double *__restrict__ hb, const double *__restrict__ h2,
+                          const double *__restrict__ B, int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    hb[q] = h2[q] * B[q];
+}
+}  // namespace
 
 namespace {
 
@@ -28,6 +39,7 @@ bool op_prepares(int lx) { return lx == 6 || lx == 8 || lx == 10 || lx == 12; }
 extern "C" int ax_op_destroy(ax_op *op) {
   if (!op) return AX_EINVAL;
   if (op->gp) cudaFree(op->gp);
+  if (op->hb) cudaFree(op->hb);
   delete op;
   return AX_OK;
 }
@@ -78,15 +90,40 @@ extern "C" int ax_op_set_h1(ax_op *op, const double *h1, void *stream) {
                                  op->nelv, 0x40, (cudaStream_t)stream);
 }
 
+extern "C" int ax_op_set_h2(ax_op *op, const double *h2, const double *B, void *stream) {
+  if (!op) return AX_EINVAL;
+  if (!h2) {
+    if (op->hb) cudaFree(op->hb);
+    op->hb = nullptr;
+    return AX_OK;
+  }
+  if (!B) return AX_EINVAL;
+  const int64_t n = (int64_t)op->nelv * op->lx * op->lx * op->lx;
+  if (!op->hb && cudaMalloc((void **)&op->hb, std::max<int64_t>(n, 1) * sizeof(double)) !=
+                     cudaSuccess) {
+    (void)cudaGetLastError();
+    op->hb = nullptr;
+    return AX_ENOMEM;
+  }
+  hb_kernel<<<608, 256, 0, (cudaStream_t)stream>>>(op->hb, h2, B, n);
+  return ax::launch_status();
+}
+
 extern "C" int ax_op_apply(ax_op *op, double *w, const double *u, void *stream) {
   if (!op || (op->nelv > 0 && (!w || !u))) return AX_EINVAL;
   if (op->nelv == 0) return AX_OK;
-  if (op->gp)
-    return ax::dispatch_df64eo_prep(op->lx, w, u, op->dx, op->dxt, op->gp, op->nelv, 0,
-                                    (cudaStream_t)stream);
-  const double *const *g = op->g;
-  return ax_helm(w, u, op->dx, op->dxt, op->h1, g[0], g[1], g[2], g[3], g[4], g[5], op->lx,
+  int rc;
+  if (op->gp) {
+    rc = ax::dispatch_df64eo_prep(op->lx, w, u, op->dx, op->dxt, op->gp, op->nelv, 0,
+                                  (cudaStream_t)stream);
+  } else {
+    const double *const *g = op->g;
+    rc = ax_helm(w, u, op->dx, op->dxt, op->h1, g[0], g[1], g[2], g[3], g[4], g[5], op->lx,
                  op->nelv, stream);
+  }
+  if (rc || !op->hb) return rc;
+  const int64_t n = (int64_t)op->nelv * op->lx * op->lx * op->lx;
+  return ax::mass_add<double>(w, op->hb, u, n, nullptr, (cudaStream_t)stream);
 }
 
 namespace ax {

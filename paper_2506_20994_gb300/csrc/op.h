@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include "../../include/axhelm.h"
 
@@ -18,5 +19,13 @@ int op_apply_dot(ax_op *op, double *w, const double *u, double *partials, cudaSt
 // of p . w.  beta is a device scalar.
 int op_update_apply_dot(ax_op *op, double *w, double *p, const double *r, const double *minv,
                         const double *beta, double *partials, cudaStream_t st);
+
+// w += hb .* u over n points; partials (optional): kRedBlocks partial sums
+// of u . hb . u (the mass term's share of a fused p . Ap).
+template <typename T>
+int mass_add(T *w, const T *hb, const T *u, int64_t n, double *partials, cudaStream_t st);
+// w += (h2 .* B) .* u over n points (coefficient and mass given apart).
+int mass_add2(double *w, const double *h2, const double *B, const double *u, int64_t n,
+              cudaStream_t st);
 
 }  // namespace ax

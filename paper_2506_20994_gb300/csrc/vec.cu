@@ -2,6 +2,7 @@
 // pack / unpack of the values at nodes shared with another partition.
 #include <algorithm>
 
+#include "op.h"
 #include "reduce.cuh"
 
 namespace {
@@ -39,6 +40,35 @@ __global__ void scatter_add_kernel(double *__restrict__ v, const double *__restr
     v[idx[q]] += vals[pos[q]];
 }
 
+// w += hb .* u; partials (optional, kRedBlocks of them): sum u . hb . u
+template <typename T>
+__global__ void mass_add_kernel(T *__restrict__ w, const T *__restrict__ hb,
+                                const T *__restrict__ u, int64_t n,
+                                double *__restrict__ partials) {
+  __shared__ double sh[ax::kRedThreads / 32];
+  T acc = T(0);
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const T m = hb[q] * u[q];
+    w[q] += m;
+    acc += m * u[q];
+  }
+  if (partials) {  // kernel-uniform
+    double v[1] = {(double)acc};
+    ax::block_sum<1>(v, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+  }
+}
+
+// w += (h2 .* B) .* u
+__global__ void mass_add2_kernel(double *__restrict__ w, const double *__restrict__ h2,
+                                 const double *__restrict__ B, const double *__restrict__ u,
+                                 int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    w[q] += (h2[q] * B[q]) * u[q];
+}
+
 unsigned grid_for(int64_t n) {
   const int64_t b = (n + 255) / 256;
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, ax::kRedBlocks));
@@ -71,4 +101,38 @@ extern "C" int ax_scatter_add(double *v, const double *vals, const int64_t *idx,
   if (!ax::all_nonnull(v, vals, idx, pos)) return AX_EINVAL;
   scatter_add_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(v, vals, idx, pos, n);
   return ax::launch_status();
+}
+
+namespace ax {
+
+template <typename T>
+int mass_add(T *w, const T *hb, const T *u, int64_t n, double *partials, cudaStream_t st) {
+  if (n < 0) return AX_EINVAL;
+  if (n > 0 && !all_nonnull(w, hb, u)) return AX_EINVAL;
+  mass_add_kernel<T><<<kRedBlocks, kRedThreads, 0, st>>>(w, hb, u, n, partials);
+  return launch_status();
+}
+template int mass_add<double>(double *, const double *, const double *, int64_t, double *,
+                              cudaStream_t);
+template int mass_add<float>(float *, const float *, const float *, int64_t, double *,
+                             cudaStream_t);
+
+int mass_add2(double *w, const double *h2, const double *B, const double *u, int64_t n,
+              cudaStream_t st) {
+  if (n < 0) return AX_EINVAL;
+  if (n > 0 && !all_nonnull(w, h2, B, u)) return AX_EINVAL;
+  mass_add2_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(w, h2, B, u, n);
+  return launch_status();
+}
+
+}  // namespace ax
+
+extern "C" int ax_mass_add(double *w, const double *hb, const double *u, int64_t n,
+                           void *stream) {
+  return ax::mass_add<double>(w, hb, u, n, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int ax_mass_add_f32(float *w, const float *hb, const float *u, int64_t n,
+                               void *stream) {
+  return ax::mass_add<float>(w, hb, u, n, nullptr, (cudaStream_t)stream);
 }
