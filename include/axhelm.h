@@ -366,6 +366,22 @@ int ax_tune_run(int dtype, int lx, int nelv, void *w, const void *u, const void 
 int ax_tune_set(int dtype, int lx, int elems_per_block);
 int ax_tune_get(int dtype, int lx, int *elems_per_block);
 
+/* Variant selection for AX_VARIANT_AUTO, process-wide (Neko times its
+ * kernel variants at run time and keeps the fastest, Sec. "Methodology").
+ * ax_tune_variant_run times AX_VARIANT_F64_NATIVE, AX_VARIANT_F64_DF (lx <=
+ * 12) and AX_VARIANT_F64_DF_EO (even lx in 4..12) with default elements per
+ * block on the caller's fp64 buffers (w is overwritten; reps timed launches
+ * each, after one warm-up), records the fastest for lx and returns it.
+ * ax_tune_variant_set / _get write and read the table (0 = the built-in
+ * choice, which ax_helm uses until a variant is recorded). */
+int ax_tune_variant_run(int lx, int nelv, double *w, const double *u, const double *dx,
+                        const double *dxt, const double *h1, const double *g11,
+                        const double *g22, const double *g33, const double *g12,
+                        const double *g13, const double *g23, int reps, int *best_variant,
+                        float *best_ms, void *stream);
+int ax_tune_variant_set(int lx, int variant);
+int ax_tune_variant_get(int lx, int *variant);
+
 /* y = a x + b y on device fp64 vectors of n values (asynchronous). */
 int ax_axpby(double *y, double a, const double *x, double b, int64_t n, void *stream);
 

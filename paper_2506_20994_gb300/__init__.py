@@ -25,7 +25,8 @@ __all__ = [
     "AX_VARIANT_F64_NATIVE", "AX_VARIANT_F64_DF_EO", "df64_roundtrip", "build", "GatherScatter", "Poisson",
     "AX_PREC_F32", "AX_PREC_BF16", "Batch", "tune", "tune_set", "tune_get", "AX_BATCH_F64",
     "AX_BATCH_F32", "fourier_coefficient", "Mlp", "mlp_init_params", "training_pairs", "train_mlp", "axpby", "iterate_pairs",
-    "train_energy", "AX_MLP_TANH", "AX_MLP_SYM", "Operator", "ax_helm_h2",
+    "train_energy", "AX_MLP_TANH", "AX_MLP_SYM", "Operator", "ax_helm_h2", "tune_variant",
+    "tune_variant_set", "tune_variant_get",
 ]
 
 
@@ -491,6 +492,30 @@ def tune_get(dtype: int, lx: int) -> int:
     e = ctypes.c_int()
     check("ax_tune_get", lib().ax_tune_get(dtype, lx, ctypes.addressof(e)))
     return e.value
+
+
+def tune_variant(lx: int, fields: dict, reps: int = 5):
+    """Times the fp64 variants for lx on the given fp64 tensors (keys as in
+    Batch; w is overwritten), records the fastest for AX_VARIANT_AUTO and
+    returns (variant, ms)."""
+    import ctypes
+    nel = fields["u"].numel() // lx ** 3
+    v, ms = ctypes.c_int(), ctypes.c_float()
+    check("ax_tune_variant_run", lib().ax_tune_variant_run(
+        lx, nel, *[fields[k].data_ptr() for k in _FIELDS], reps, ctypes.addressof(v),
+        ctypes.addressof(ms), _stream()))
+    return v.value, ms.value
+
+
+def tune_variant_set(lx: int, variant: int) -> None:
+    check("ax_tune_variant_set", lib().ax_tune_variant_set(lx, variant))
+
+
+def tune_variant_get(lx: int) -> int:
+    import ctypes
+    v = ctypes.c_int()
+    check("ax_tune_variant_get", lib().ax_tune_variant_get(lx, ctypes.addressof(v)))
+    return v.value
 
 
 # ---------------------------------------------------------------------------

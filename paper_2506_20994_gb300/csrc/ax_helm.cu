@@ -17,6 +17,9 @@ int check_args(W *w, const S *u, const T *dx, const T *dxt, const S *h1, const S
   return AX_OK;
 }
 
+// variant chosen for AX_VARIANT_AUTO per lx by the tuner; 0 = built-in
+int g_variant[AX_LX_MAX + 1];
+
 }  // namespace
 
 extern "C" {
@@ -45,6 +48,7 @@ int ax_helm_variant(int variant, double *w, const double *u, const double *dx,
   // measured on GB300 at E = 32768 / 13824 / 8000: the even-odd kernel wins
   // for lx 8, 10, 12; the k-loop double-float kernel below that; fp64 units
   // above the double-float instantiations
+  if (variant == AX_VARIANT_AUTO && g_variant[lx] != 0) variant = g_variant[lx];
   if (variant == AX_VARIANT_AUTO)
     variant = (lx == 8 || lx == 10 || lx == 12) ? AX_VARIANT_F64_DF_EO
               : lx <= ax::AX_DF64_LX_MAX        ? AX_VARIANT_F64_DF
@@ -105,3 +109,62 @@ int ax_helm_bf16(float *w, const ax_bf16 *u, const float *dx, const float *dxt,
 }
 
 }  // extern "C"
+
+extern "C" int ax_tune_variant_run(int lx, int nelv, double *w, const double *u,
+                                   const double *dx, const double *dxt, const double *h1,
+                                   const double *g11, const double *g22, const double *g33,
+                                   const double *g12, const double *g13, const double *g23,
+                                   int reps, int *best_variant, float *best_ms, void *stream) {
+  if (!ax::lx_ok(lx) || nelv <= 0 || reps < 1 ||
+      !ax::all_nonnull(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23))
+    return AX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return AX_ELAUNCH;
+  const int cands[3] = {AX_VARIANT_F64_NATIVE, AX_VARIANT_F64_DF, AX_VARIANT_F64_DF_EO};
+  int best = 0;
+  float best_t = 1e30f;
+  for (int v : cands) {
+    auto run = [&]() {
+      return ax_helm_variant(v, w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx, nelv, 0,
+                             stream);
+    };
+    if (run() != AX_OK) {  // inadmissible for this lx
+      (void)cudaGetLastError();
+      continue;
+    }
+    cudaEventRecord(e0, st);
+    int rc = AX_OK;
+    for (int r = 0; r < reps && rc == AX_OK; ++r) rc = run();
+    cudaEventRecord(e1, st);
+    if (rc != AX_OK || cudaEventSynchronize(e1) != cudaSuccess) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (ms < best_t) {
+      best_t = ms;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best == 0) return AX_ELAUNCH;
+  g_variant[lx] = best;
+  if (best_variant) *best_variant = best;
+  if (best_ms) *best_ms = best_t;
+  return AX_OK;
+}
+
+extern "C" int ax_tune_variant_set(int lx, int variant) {
+  if (!ax::lx_ok(lx) || variant < AX_VARIANT_AUTO || variant > AX_VARIANT_F64_DF_EO)
+    return AX_EINVAL;
+  g_variant[lx] = variant;
+  return AX_OK;
+}
+
+extern "C" int ax_tune_variant_get(int lx, int *variant) {
+  if (!ax::lx_ok(lx) || !variant) return AX_EINVAL;
+  *variant = g_variant[lx];
+  return AX_OK;
+}

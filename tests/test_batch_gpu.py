@@ -117,3 +117,33 @@ def test_tuner_records_choice_and_parity_holds(dtype):
             assert rel_l2(mm["w"].double().cpu().numpy(), mm["ref"]) <= tol
     finally:
         ax.tune_set(dtype, lx, 0)
+
+
+@pytest.mark.parametrize("lx", [5, 8])
+def test_variant_tuner_drives_auto(lx):
+    """The variant tuner times the admissible fp64 variants, records the
+    fastest, and ax_helm's automatic choice then runs exactly that variant
+    (same bits); parity holds; the table resets to the built-in choice."""
+    from _cases import operator_case
+    case = operator_case((6, 5, 4), lx, seed=70 + lx)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    f = {k: t(case[k]) for k in ("u", "dx", "dxt", "h1") + GKEYS}
+    f["w"] = torch.empty_like(f["u"])
+    try:
+        v, ms = ax.tune_variant(lx, f, reps=2)
+        assert v in (ax.AX_VARIANT_F64_NATIVE, ax.AX_VARIANT_F64_DF, ax.AX_VARIANT_F64_DF_EO)
+        assert ms > 0 and ax.tune_variant_get(lx) == v
+        if lx % 2:
+            assert v != ax.AX_VARIANT_F64_DF_EO
+        args = [f[k] for k in ("u", "dx", "dxt", "h1") + GKEYS]
+        w_auto, w_v = torch.empty_like(f["u"]), torch.empty_like(f["u"])
+        ax.ax_helm(w_auto, *args, lx)
+        ax.ax_helm(w_v, *args, lx, variant=v)
+        torch.cuda.synchronize()
+        assert torch.equal(w_auto, w_v)
+        assert rel_l2(w_auto.cpu().numpy(), case["w"]) <= 1e-12
+        with pytest.raises(ax.AxError):
+            ax.tune_variant_set(lx, 7)
+    finally:
+        ax.tune_variant_set(lx, 0)
+    assert ax.tune_variant_get(lx) == 0
