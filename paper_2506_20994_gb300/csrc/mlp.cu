@@ -251,6 +251,119 @@ mlp_apply_kernel(T *__restrict__ corr, const T *__restrict__ r, const T *__restr
   }
 }
 
+// Symmetric form with its scale precomputed (sc = sqrt(minv), fp32) and an
+// even number of points per element: one warp streams 16 elements through
+// both layers with no shared memory and no block barrier.  Layer 1 loads the
+// mma A-fragments straight from r and sc (rows g, g+8, columns k+2t4 and
+// k+2t4+8: 16-byte and 8-byte pairs, full sectors), one k-step ahead;
+// its accumulators are re-packed in registers as the A-fragments of
+// layer 2 (n-tiles 2q, 2q+1 of layer 1 are k-step q of layer 2); the
+// epilogue stores corr = sc * y as pairs.  Weights come through L1/L2.
+constexpr int kSymWarps = 4;  // warps per block
+
+template <typename T>
+struct Pair;  // two consecutive values of T
+template <>
+struct Pair<double> {
+  using V = double2;
+};
+template <>
+struct Pair<float> {
+  using V = float2;
+};
+
+template <typename T, int NT1>  // NT1 = HP / 8 hidden n-tiles
+__global__ void __launch_bounds__(kSymWarps * 32)
+mlp_sym_apply_kernel(T *__restrict__ corr, const T *__restrict__ r,
+                     const float *__restrict__ sc, const __nv_bfloat16 *__restrict__ W1T,
+                     const __nv_bfloat16 *__restrict__ W2T, int N, int NP, int nelv) {
+  using V = typename Pair<T>::V;
+  constexpr int HP = NT1 * 8;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
+  const long long ew = ((long long)blockIdx.x * kSymWarps + (threadIdx.x >> 5)) * 16;
+  if (ew >= nelv) return;  // warp-uniform
+  const bool ok0 = ew + g < nelv, ok1 = ew + g + 8 < nelv;
+  const size_t row0 = (size_t)(ok0 ? ew + g : 0) * N, row1 = (size_t)(ok1 ? ew + g + 8 : 0) * N;
+
+  // A-fragment inputs of one k-step: x at (row, k + 2 t4 + {0, 1, 8, 9})
+  struct In {
+    V r[4];
+    float2 s[4];
+  };
+  auto load = [&](int ks, In &in) {
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int k = ks + 2 * t4 + ((h & 2) ? 8 : 0);
+      const bool okr = (h & 1) ? ok1 : ok0;
+      const size_t q = ((h & 1) ? row1 : row0) + k;
+      if (okr && k < N) {  // N even: the pair (k, k + 1) is inside the element
+        in.r[h] = *reinterpret_cast<const V *>(r + q);
+        in.s[h] = *reinterpret_cast<const float2 *>(sc + q);
+      } else {
+        in.r[h] = V{};
+        in.s[h] = make_float2(0.f, 0.f);
+      }
+    }
+  };
+  float acc1[NT1][4];
+#pragma unroll
+  for (int j = 0; j < NT1; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc1[j][q] = 0.f;
+  In cur, nxt;
+  load(0, nxt);
+  for (int ks = 0; ks < NP; ks += 16) {
+    cur = nxt;
+    if (ks + 16 < NP) load(ks + 16, nxt);
+    uint32_t a[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h)  // fragment order: (g, k), (g+8, k), (g, k+8), (g+8, k+8)
+      a[h] = pack_bf16(cur.s[h].x * to_f32(cur.r[h].x), cur.s[h].y * to_f32(cur.r[h].y));
+#pragma unroll
+    for (int j = 0; j < NT1; ++j) {
+      const __nv_bfloat16 *w = W1T + (size_t)(j * 8 + g) * NP + ks + 2 * t4;
+      mma_bf16(acc1[j], a, __ldg(reinterpret_cast<const unsigned int *>(w)),
+               __ldg(reinterpret_cast<const unsigned int *>(w + 8)));
+    }
+  }
+  // layer-1 accumulators (rows g, g+8; hidden 8j + 2t4 + {0, 1}) as layer-2
+  // A-fragments: k-step q takes n-tiles 2q (k) and 2q + 1 (k + 8)
+  uint32_t a2[NT1 / 2][4];
+#pragma unroll
+  for (int q = 0; q < NT1 / 2; ++q) {
+    a2[q][0] = pack_bf16(acc1[2 * q][0], acc1[2 * q][1]);
+    a2[q][1] = pack_bf16(acc1[2 * q][2], acc1[2 * q][3]);
+    a2[q][2] = pack_bf16(acc1[2 * q + 1][0], acc1[2 * q + 1][1]);
+    a2[q][3] = pack_bf16(acc1[2 * q + 1][2], acc1[2 * q + 1][3]);
+  }
+  for (int nt = 0; nt < NP / 8; ++nt) {
+    float acc2[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < NT1 / 2; ++q) {
+      const __nv_bfloat16 *w = W2T + (size_t)(nt * 8 + g) * HP + 16 * q + 2 * t4;
+      mma_bf16(acc2, a2[q], __ldg(reinterpret_cast<const unsigned int *>(w)),
+               __ldg(reinterpret_cast<const unsigned int *>(w + 8)));
+    }
+    const int col = nt * 8 + 2 * t4;
+    if (col < N) {
+      if (ok0) {
+        const float2 sv = *reinterpret_cast<const float2 *>(sc + row0 + col);
+        V o;
+        o.x = from_f32<T>(sv.x * acc2[0]);
+        o.y = from_f32<T>(sv.y * acc2[1]);
+        *reinterpret_cast<V *>(corr + row0 + col) = o;
+      }
+      if (ok1) {
+        const float2 sv = *reinterpret_cast<const float2 *>(sc + row1 + col);
+        V o;
+        o.x = from_f32<T>(sv.x * acc2[2]);
+        o.y = from_f32<T>(sv.y * acc2[3]);
+        *reinterpret_cast<V *>(corr + row1 + col) = o;
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- training
 // X[b][k] = (minv r)_e / s, T[b][k] = (err - minv r)_e / s for e = idx[b]
 __global__ void gather_pairs_kernel(float *__restrict__ X, float *__restrict__ Tt,
@@ -590,6 +703,20 @@ int mlp_correction(const ax_mlp *M, T *corr, const T *r, const T *minv, const T 
   if (nelv <= 0) return AX_OK;
   const Layout L = layout(M);
   const char *base = reinterpret_cast<const char *>(M->theta_bf);
+  if (M->arch == AX_MLP_SYM && sc && M->n_in % 2 == 0 && (L.HP == 16 || L.HP == 32 ||
+                                                          L.HP == 48 || L.HP == 64)) {
+    auto w1 = reinterpret_cast<const __nv_bfloat16 *>(base + L.w1t);
+    auto w2 = reinterpret_cast<const __nv_bfloat16 *>(base + L.w2t);
+    const unsigned grid = (unsigned)((nelv + 16 * kSymWarps - 1) / (16 * kSymWarps));
+    const int th = kSymWarps * 32;
+    switch (L.HP) {
+      case 16: mlp_sym_apply_kernel<T, 2><<<grid, th, 0, st>>>(corr, r, sc, w1, w2, M->n_in, L.NP, nelv); break;
+      case 32: mlp_sym_apply_kernel<T, 4><<<grid, th, 0, st>>>(corr, r, sc, w1, w2, M->n_in, L.NP, nelv); break;
+      case 48: mlp_sym_apply_kernel<T, 6><<<grid, th, 0, st>>>(corr, r, sc, w1, w2, M->n_in, L.NP, nelv); break;
+      default: mlp_sym_apply_kernel<T, 8><<<grid, th, 0, st>>>(corr, r, sc, w1, w2, M->n_in, L.NP, nelv); break;
+    }
+    return launch_status();
+  }
   const size_t smem = apply_smem(L.HP);
   auto kern = M->arch == AX_MLP_SYM ? mlp_apply_kernel<T, true> : mlp_apply_kernel<T, false>;
   if (smem > 48 * 1024 &&
