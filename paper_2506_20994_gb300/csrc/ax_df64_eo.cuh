@@ -83,8 +83,9 @@ constexpr size_t df64eo_smem(int epb) {
 }
 
 // PUPD (prepared geometry only): u is not an input; instead the kernel first
-// forms the solver's next search direction in place, pw = minv .* r +
-// (*beta) pw (fp64), and applies the operator to it.
+// forms the solver's next search direction in place, pw = z + (*beta) pw
+// with z = minv .* r (+ corr when *use_corr, the flexible CG's learned
+// step), in fp64 with explicit roundings, and applies the operator to it.
 template <int LX, bool PREP = false, bool PUPD = false>
 __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double *__restrict__ u,
                                             const double *__restrict__ dx,
@@ -102,7 +103,9 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
                                             double *__restrict__ pw = nullptr,
                                             const double *__restrict__ r_in = nullptr,
                                             const double *__restrict__ minv_in = nullptr,
-                                            const double *__restrict__ beta_p = nullptr) {
+                                            const double *__restrict__ beta_p = nullptr,
+                                            const double *__restrict__ corr_in = nullptr,
+                                            const int *__restrict__ use_corr_p = nullptr) {
   static_assert(LX % 2 == 0, "even-odd kernel needs an even lx");
   using namespace df;
   constexpr int H = LX / 2, N = LX - 1;
@@ -197,6 +200,8 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
   if (own) {
     if constexpr (PUPD) {
       const double beta = *beta_p;
+      // flexible CG: z = minv r + corr when its step took the correction
+      const bool uc = corr_in != nullptr && *use_corr_p != 0;
 #pragma unroll
       for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -206,7 +211,9 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
             gr[c][b][a] = df2{0.f, 0.f};
             if (active) {
               const size_t q = gidx(c, b, a);
-              const double pn = __fma_rn(beta, pw[q], __dmul_rn(__ldg(minv_in + q), __ldg(r_in + q)));
+              double z = __dmul_rn(__ldg(minv_in + q), __ldg(r_in + q));
+              if (uc) z = __dadd_rn(z, __ldg(corr_in + q));
+              const double pn = __fma_rn(beta, pw[q], z);
               pw[q] = pn;
               gr[c][b][a] = split(pn);
             }
@@ -440,14 +447,16 @@ ax_df64eo_prep_kernel(double *__restrict__ w, const double *__restrict__ u,
                       const df::dd2 *__restrict__ gp, int nelv, int epb,
                       double *__restrict__ dotp, double *__restrict__ pw,
                       const double *__restrict__ r_in, const double *__restrict__ minv_in,
-                      const double *__restrict__ beta_p) {
+                      const double *__restrict__ beta_p, const double *__restrict__ corr_in,
+                      const int *__restrict__ use_corr_p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long e0 = (long long)blockIdx.x * epb;
   const long long left = nelv - e0;
   const int nel = left < epb ? (int)left : epb;
   df64eo_body<LX, true, PUPD>(w, u, dx, dxt, nullptr, nullptr, nullptr, nullptr, nullptr,
                               nullptr, nullptr, gp, e0, nel, epb, smem_raw,
-                              DOT ? dotp : nullptr, pw, r_in, minv_in, beta_p);
+                              DOT ? dotp : nullptr, pw, r_in, minv_in, beta_p, corr_in,
+                              use_corr_p);
 }
 
 // Prepared geometry: entry ((e*4 + cp)*7 + f)*H3 + t holds field f at the
@@ -522,8 +531,10 @@ int launch_df64eo_prep(double *w, const double *u, const double *dx, const doubl
                        const df::dd2 *gp, int nelv, int epb, cudaStream_t stream,
                        double *dotp = nullptr, double *pw = nullptr,
                        const double *r_in = nullptr, const double *minv_in = nullptr,
-                       const double *beta_p = nullptr) {
+                       const double *beta_p = nullptr, const double *corr_in = nullptr,
+                       const int *use_corr_p = nullptr) {
   if (pw && !(dotp && r_in && minv_in && beta_p)) return AX_EINVAL;
+  if (corr_in && !use_corr_p) return AX_EINVAL;
   constexpr int H3 = (LX / 2) * (LX / 2) * (LX / 2);
   // measured on GB300 (E = 32768 at lx = 8, 13824 at lx = 10): blocks of
   // about 128 threads (4 per SM) beat 256-thread blocks by 8-9 %
@@ -545,7 +556,7 @@ int launch_df64eo_prep(double *w, const double *u, const double *dx, const doubl
   }
   const unsigned grid = (unsigned)((nelv + epb - 1) / epb);
   kern<<<grid, epb * H3, smem, stream>>>(w, u, dx, dxt, gp, nelv, epb, dotp, pw, r_in, minv_in,
-                                         beta_p);
+                                         beta_p, corr_in, use_corr_p);
   return launch_status();
 }
 

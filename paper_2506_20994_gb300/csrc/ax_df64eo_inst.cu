@@ -22,12 +22,13 @@ int dispatch_df64eo(int lx, double *w, const double *u, const double *dx, const 
 int dispatch_df64eo_prep(int lx, double *w, const double *u, const double *dx,
                          const double *dxt, const df::dd2 *gp, int nelv, int epb,
                          cudaStream_t st, double *dotp, double *pw, const double *r_in,
-                         const double *minv_in, const double *beta_p) {
+                         const double *minv_in, const double *beta_p, const double *corr_in,
+                         const int *use_corr_p) {
   switch (lx) {
 #define AX_CASE(L)                                                                             \
   case L:                                                                                      \
     return launch_df64eo_prep<L>(w, u, dx, dxt, gp, nelv, epb, st, dotp, pw, r_in, minv_in,   \
-                                 beta_p);
+                                 beta_p, corr_in, use_corr_p);
     AX_CASE(4) AX_CASE(6) AX_CASE(8) AX_CASE(10) AX_CASE(12)
 #undef AX_CASE
     default:

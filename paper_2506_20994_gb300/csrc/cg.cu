@@ -429,13 +429,15 @@ int apply_fused(ax_poisson *P, float *w, const float *u, cudaStream_t st) {
 bool fuses_update(const ax_poisson *P, const double *) { return P->dotp && P->ndot > 0; }
 bool fuses_update(const ax_poisson *, const float *) { return false; }
 int apply_fused_update(ax_poisson *P, double *w, double *p, const double *r,
-                       const double *minv, const double *beta, cudaStream_t st) {
-  int rc = ax::op_update_apply_dot(P->op, w, p, r, minv, beta, P->dotp, st);
+                       const double *minv, const double *beta, cudaStream_t st,
+                       const double *corr = nullptr, const int *use_corr = nullptr) {
+  int rc = ax::op_update_apply_dot(P->op, w, p, r, minv, beta, P->dotp, st, corr, use_corr);
   if (rc == AX_OK) rc = mass_fused(P, w, p, st);
   return rc ? rc : ax_gs_sum(P->gs, w, st);
 }
 int apply_fused_update(ax_poisson *, float *, float *, const float *, const float *,
-                       const double *, cudaStream_t) {
+                       const double *, cudaStream_t, const float * = nullptr,
+                       const int * = nullptr) {
   return AX_EINVAL;
 }
 
@@ -1083,6 +1085,10 @@ int fcg_loop(ax_poisson *P, const ax_mlp *M, T *x, const T *b, T *r, T *r_old, T
   const int64_t n = P->n;
   const unsigned nb = kRedBlocks;
   const int have = M != nullptr;
+  // fp64 with prepared geometry: after the first step the direction update
+  // p = z + beta p runs inside the next apply (see pcg_loop)
+  const bool fused_p = fused_parts(P, (const T *)nullptr) > 0 &&
+                       fuses_update(P, (const T *)nullptr);
   auto precondition = [&](int first) -> int {
     if (have) {
       int rc = ax::mlp_correction<T>(M, corr, r, minv, mask, c, P->nelv, st,
@@ -1093,9 +1099,14 @@ int fcg_loop(ax_poisson *P, const ax_mlp *M, T *x, const T *b, T *r, T *r_old, T
     fcg_dots_kernel<T><<<nb, kRedThreads, 0, st>>>(r, r_old, corr, cm, c, have, P->partials,
                                                    n);
     fcg_beta_kernel<<<1, 128, 0, st>>>(P->partials, nb, P->scal, first, have);
-    fcg_p_kernel<T><<<nb, kRedThreads, 0, st>>>(p, r, minv, corr, P->scal, first, n);
+    if (first || !fused_p)
+      fcg_p_kernel<T><<<nb, kRedThreads, 0, st>>>(p, r, minv, corr, P->scal, first, n);
     return ax::launch_status();
   };
+  const char *scal_bytes = reinterpret_cast<const char *>(P->scal);
+  const double *beta_dev =
+      reinterpret_cast<const double *>(scal_bytes + offsetof(CgScalars, beta));
+  const int *use_corr_dev = reinterpret_cast<const int *>(scal_bytes + offsetof(CgScalars, use_corr));
   auto read_scalars = [&]() -> int {
     if (cudaMemcpyAsync(P->scal_host, P->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
@@ -1115,9 +1126,14 @@ int fcg_loop(ax_poisson *P, const ax_mlp *M, T *x, const T *b, T *r, T *r_old, T
   // fp64 with prepared geometry: p . Ap from the apply itself (see pcg_loop)
   const int nparts = fused_parts(P, (const T *)nullptr);
   const bool fused = nparts > 0;
+  int applied = 0;  // applies so far: the first uses the p formed above
   while (status != AX_OK && it < maxit) {
     if (fused) {
-      if ((rc = apply_fused(P, w, p, st))) return rc;
+      rc = (fused_p && applied > 0)
+               ? apply_fused_update(P, w, p, r, minv, beta_dev, st, corr, use_corr_dev)
+               : apply_fused(P, w, p, st);
+      ++applied;
+      if (rc) return rc;
       cg_alpha_kernel<<<1, 1024, 0, st>>>(P->dotp, nparts, P->scal);
       fcg_update_kernel<T, true><<<nb, kRedThreads, 0, st>>>(x, r, r_old, p, w, c, cm, P->scal,
                                                              P->partials, n);

@@ -63,7 +63,8 @@ int dispatch_df64eo_prep(int lx, double *w, const double *u, const double *dx,
                          const double *dxt, const df::dd2 *gp, int nelv, int epb,
                          cudaStream_t st, double *dotp = nullptr, double *pw = nullptr,
                          const double *r_in = nullptr, const double *minv_in = nullptr,
-                         const double *beta_p = nullptr);
+                         const double *beta_p = nullptr, const double *corr_in = nullptr,
+                         const int *use_corr_p = nullptr);
 int df64eo_prep_blocks(int lx, int nelv);
 int dispatch_eo_prepare(int lx, df::dd2 *gp, const double *h1, const double *g11,
                         const double *g22, const double *g33, const double *g12,

@@ -138,10 +138,11 @@ int op_apply_dot(ax_op *op, double *w, const double *u, double *partials, cudaSt
 }
 
 int op_update_apply_dot(ax_op *op, double *w, double *p, const double *r, const double *minv,
-                        const double *beta, double *partials, cudaStream_t st) {
+                        const double *beta, double *partials, cudaStream_t st,
+                        const double *corr, const int *use_corr) {
   if (!op || !op->gp || !partials || !p || !r || !minv || !beta) return AX_EINVAL;
   return dispatch_df64eo_prep(op->lx, w, nullptr, op->dx, op->dxt, op->gp, op->nelv, 0, st,
-                              partials, p, r, minv, beta);
+                              partials, p, r, minv, beta, corr, use_corr);
 }
 
 }  // namespace ax

@@ -15,10 +15,11 @@ int op_dot_blocks(const ax_op *op);
 // of u . w (element-local, before any gather-scatter; fixed order).
 int op_apply_dot(ax_op *op, double *w, const double *u, double *partials, cudaStream_t st);
 // The solver's direction update fused in front of the same apply:
-// p = minv .* r + (*beta) p in place (fp64), then w = Ax(p) and the partials
-// of p . w.  beta is a device scalar.
+// p = z + (*beta) p in place (fp64), z = minv .* r (+ corr when *use_corr),
+// then w = Ax(p) and the partials of p . w.  beta, use_corr: device scalars.
 int op_update_apply_dot(ax_op *op, double *w, double *p, const double *r, const double *minv,
-                        const double *beta, double *partials, cudaStream_t st);
+                        const double *beta, double *partials, cudaStream_t st,
+                        const double *corr = nullptr, const int *use_corr = nullptr);
 
 // w += hb .* u over n points; partials (optional): kRedBlocks partial sums
 // of u . hb . u (the mass term's share of a fused p . Ap).
