@@ -98,6 +98,22 @@ int ax_helm_bf16(float *w, const ax_bf16 *u, const float *dx, const float *dxt,
                  const ax_bf16 *g33, const ax_bf16 *g12, const ax_bf16 *g13,
                  const ax_bf16 *g23, int lx, int nelv, void *stream);
 
+/* The operator on host buffers (the paper's interface passes device
+ * arrays; this serves callers whose fields live in host memory): w, u, h1
+ * and G are host arrays of nelv * lx^3 doubles, dx and dxt host arrays of
+ * lx^2; they should be page-locked (pinned) for the copies to run
+ * asynchronously.  The elements stream through the device in chunks of
+ * `chunk` elements (0 picks about 4 M points per field), the copies in,
+ * the apply (as ax_helm) and the copies out of different chunks overlapping
+ * on three streams; the device staging buffers are kept per device for the
+ * next call.  Work starts after the work queued on `stream`; the call
+ * returns when w is written (synchronises).  Calls are serialised per
+ * process.  Errors as ax_helm; AX_ENOMEM if staging cannot be allocated. */
+int ax_helm_host(double *w, const double *u, const double *dx, const double *dxt,
+                 const double *h1, const double *g11, const double *g22, const double *g33,
+                 const double *g12, const double *g13, const double *g23, int lx, int nelv,
+                 int chunk, void *stream);
+
 /* Helmholtz form: w = Ax(u) + h2 .* B .* u, the stiffness apply above plus
  * the mass term with a coefficient h2 (B the diagonal mass matrix, jac *
  * w_i w_j w_k, in the element-major layout).  The paper's listing is

@@ -203,3 +203,24 @@ def test_f64_even_odd_adversarial():
     nz = per_ref > 0
     assert np.all(per_el[nz] <= 1e-12 * per_ref[nz])
     assert np.all(w[::4] == 0.0)
+
+
+@pytest.mark.parametrize("chunk", [0, 100, 567])
+def test_host_buffers_streamed_in_chunks(chunk):
+    """ax_helm_host on host tensors (pinned and pageable), chunks with a
+    ragged tail, against the oracle and bit for bit against ax_helm on the
+    device (the same kernel runs on every chunk)."""
+    lx = 8
+    case = operator_case((9, 9, 7), lx, seed=90)
+    keys = ("u", "dx", "dxt", "h1") + GKEYS
+    pinned = {k: torch.as_tensor(np.ascontiguousarray(case[k])).pin_memory() for k in keys}
+    w = torch.full(case["u"].shape, float("nan"), dtype=torch.float64).pin_memory()
+    ax.ax_helm_host(w, *[pinned[k] for k in keys], lx, chunk=chunk)
+    assert rel_l2(w.numpy(), case["w"]) <= TOL["f64"]
+    wd = torch.empty(case["u"].shape, dtype=torch.float64, device="cuda")
+    ax.ax_helm(wd, *[pinned[k].cuda() for k in keys], lx)
+    assert torch.equal(wd.cpu(), w)
+    pageable = {k: torch.as_tensor(np.ascontiguousarray(case[k])) for k in keys}
+    w2 = torch.empty(case["u"].shape, dtype=torch.float64)
+    ax.ax_helm_host(w2, *[pageable[k] for k in keys], lx, chunk=chunk)
+    assert torch.equal(w2, w)
