@@ -9,11 +9,12 @@ CUDA events (kernels) or wall time around a synchronising solve (solvers):
   cg       Poisson solve to a 1e-8 relative residual at E = 32768, lx = 8:
            fp64 Jacobi-CG against fp64 iterative refinement around fp32 and
            bf16-data inner CG
+  cg_sweep fp64 Jacobi-CG to 1e-8 at E in {4096, 32768} x lx in {6, 8, 10, 12}
   learned  the same target on the variable-coefficient problem: Jacobi
            flexible CG against the learned element preconditioner in its
            symmetric linear form (trained here by the library's kernels on
-           residual/error pairs of plain CG on an 8^3 mesh), in fp64 and
-           inside mixed refinement
+           residual/error pairs of 20 plain-CG iterates on an 8^3 mesh: 10,240
+           element pairs), in fp64 and inside mixed refinement
   batch    64 meshes, E log-uniform in [64, 8192], lx in {5, 6, 8, 10}: one
            persistent launch (and its CUDA-graph replay) against one launch
            per mesh, fp64 and fp32
@@ -141,6 +142,24 @@ def cg(ax, synth, oracle_f, dev):
     return out
 
 
+def cg_sweep(ax, synth, oracle_f, dev):
+    """Jacobi-PCG to 1e-8 on the sweep meshes (E in {4096, 32768} x lx in
+    {6, 8, 10, 12}), fp64."""
+    out = {}
+    for n in (16, 32):
+        for lx in (6, 8, 10, 12):
+            P = ax.Poisson(synth.box_vertices(n, seed=0), lx, device=dev)
+            P.set_check_every(8)
+            b = P.rhs(oracle_f)
+            P.cg(b, tol=1e-8, maxit=3)  # warm-up
+            t, (x, its, rel, rc) = _wall(lambda: P.cg(b, tol=1e-8))
+            out[f"E{n ** 3}_lx{lx}"] = {"s": round(t, 4), "iters": its, "relres": rel,
+                                        "status": rc,
+                                        "ms_per_iter": round(t / max(its, 1) * 1e3, 4)}
+            del P, b, x
+    return out
+
+
 def learned(ax, synth, oracle_f, dev):
     lx = 8
     coef = ax.fourier_coefficient(1)
@@ -148,16 +167,19 @@ def learned(ax, synth, oracle_f, dev):
                        "tol 1e-8"}
     # train on residual/error pairs of plain CG on an 8^3 mesh (element-local
     # network: it transfers to the larger mesh)
+    # 8^3 elements x 20 CG iterates = 10,240 element residual/error pairs
     Ps = ax.Poisson(synth.box_vertices(8, seed=0), lx, h1=coef, device=dev)
     bs = Ps.rhs(oracle_f)
+    iterates = (1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 112, 128)
     n_hid = 48
     M = ax.Mlp(lx ** 3, n_hid, arch=ax.AX_MLP_SYM,
                params=ax.mlp_init_params(lx ** 3, n_hid, seed=1, arch=ax.AX_MLP_SYM))
-    t_pairs, (R, E) = _wall(lambda: ax.iterate_pairs(Ps, bs, iterates=(2, 4, 8, 16, 32, 64)))
-    t_train, loss = _wall(lambda: ax.train_energy(Ps, M, R, E, epochs=100, lr=5e-3))
-    out["training"] = {"arch": "symmetric linear, n_hid 48", "pairs": int(R.shape[0]),
-                       "elements_per_pair": Ps.nelv, "pair_s": round(t_pairs, 3),
-                       "train_s": round(t_train, 3), "final_rel_energy_err": loss}
+    t_pairs, (R, E) = _wall(lambda: ax.iterate_pairs(Ps, bs, iterates=iterates))
+    t_train, loss = _wall(lambda: ax.train_energy(Ps, M, R, E, epochs=100, lr=2e-3))
+    out["training"] = {"arch": "symmetric linear, n_hid 48", "iterates": int(R.shape[0]),
+                       "element_pairs": int(R.shape[0]) * Ps.nelv, "params": M.nparams,
+                       "pair_s": round(t_pairs, 3), "train_s": round(t_train, 3),
+                       "final_rel_energy_err": loss}
     del Ps, R, E
     P = ax.Poisson(synth.box_vertices(32, seed=0), lx, h1=coef, device=dev)
     P.set_check_every(8)
@@ -226,6 +248,7 @@ def run_extras(ax, host, d, lx, nel, stream, hbm_peak, which):
         "modes": lambda: modes(ax, d, lx, nel, hbm_peak),
         "sweep": lambda: sweep(ax, synth, dev, hbm_peak),
         "cg": lambda: cg(ax, synth, synth.poisson_source, dev),
+        "cg_sweep": lambda: cg_sweep(ax, synth, synth.poisson_source, dev),
         "learned": lambda: learned(ax, synth, synth.poisson_source, dev),
         "batch": lambda: batch(ax, synth, dev, hbm_peak),
     }

@@ -26,19 +26,19 @@
 #include "dispatch.h"
 
 namespace ax {
-int batch_lx_launch_f64(int, int, size_t, const BatchMeshDev *, const BatchItem *, const int *,
-                        cudaStream_t);
+int batch_lx_launch_f64(int, int, int, size_t, const BatchMeshDev *, const BatchItem *,
+                        const int *, cudaStream_t);
 int batch_lx_launch_f32(int, int, size_t, const BatchMeshDev *, const BatchItem *, const int *,
                         cudaStream_t);
-int batch_lx_setup_f64(int, size_t, int *);
+int batch_lx_setup_f64(int, int, size_t, int *);
 int batch_lx_setup_f32(int, size_t, int *);
-int batch_lx_launch(bool f64, int lx, int nblocks, size_t smem, const BatchMeshDev *m,
+int batch_lx_launch(bool f64, int lx, int body, int nblocks, size_t smem, const BatchMeshDev *m,
                     const BatchItem *it, const int *bs, cudaStream_t st) {
-  return f64 ? batch_lx_launch_f64(lx, nblocks, smem, m, it, bs, st)
+  return f64 ? batch_lx_launch_f64(lx, body, nblocks, smem, m, it, bs, st)
              : batch_lx_launch_f32(lx, nblocks, smem, m, it, bs, st);
 }
-int batch_lx_setup(bool f64, int lx, size_t smem, int *bps) {
-  return f64 ? batch_lx_setup_f64(lx, smem, bps) : batch_lx_setup_f32(lx, smem, bps);
+int batch_lx_setup(bool f64, int lx, int body, size_t smem, int *bps) {
+  return f64 ? batch_lx_setup_f64(lx, body, smem, bps) : batch_lx_setup_f32(lx, smem, bps);
 }
 }  // namespace ax
 
@@ -49,9 +49,9 @@ using ax::BatchMeshDev;
 using ax::kBatchThreads;
 constexpr int kBatchLxMin = 2, kBatchLxMax = 12;
 
-size_t body_smem(bool f64, int lx, int epb) {
+size_t body_smem(bool f64, int lx, int body, int epb) {
   const size_t n2 = (size_t)lx * lx, n3 = n2 * lx;
-  if (f64 && ax::batch_uses_eo(lx)) {
+  if (f64 && body == ax::kBodyEvenOdd) {
     const size_t h = lx / 2;
     return 2 * h * h * 24 + (size_t)epb * 3 * n2 * (h + 1) * 16;
   }
@@ -60,8 +60,19 @@ size_t body_smem(bool f64, int lx, int epb) {
 
 int default_epb(int lx) { return std::max(1, kBatchThreads / (lx * lx)); }
 
+// Thread layout of the fp64 kernel for lx: the variant the tuner recorded
+// (ax_tune_variant_run; either k-loop variant runs the double-float k-loop
+// body here), else ax_helm's built-in choice.
+int choose_body(int lx) {
+  int v = 0;
+  if (ax_tune_variant_get(lx, &v) != AX_OK) v = 0;
+  if (v == AX_VARIANT_F64_DF_EO && ax::batch_eo_ok(lx)) return ax::kBodyEvenOdd;
+  if (v == AX_VARIANT_F64_DF || v == AX_VARIANT_F64_NATIVE) return ax::kBodyKLoop;
+  return ax::batch_uses_eo(lx) ? ax::kBodyEvenOdd : ax::kBodyKLoop;
+}
+
 struct Group {
-  int lx = 0, nblocks = 0;
+  int lx = 0, body = 0, nblocks = 0;
   size_t smem = 0;
   int item_off = 0, start_off = 0;  // into d_items / d_start
 };
@@ -97,7 +108,7 @@ namespace {
 int batch_launch_raw(ax_batch *B, cudaStream_t st) {
   const bool f64 = B->dtype == AX_BATCH_F64;
   for (const Group &g : B->groups) {
-    int rc = ax::batch_lx_launch(f64, g.lx, g.nblocks, g.smem, B->d_mesh,
+    int rc = ax::batch_lx_launch(f64, g.lx, g.body, g.nblocks, g.smem, B->d_mesh,
                                  B->d_items + g.item_off, B->d_start + g.start_off, st);
     if (rc) return rc;
   }
@@ -128,9 +139,12 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
   *out = nullptr;
   const bool f64 = dtype == AX_BATCH_F64;
   std::vector<BatchMeshDev> mh(nmesh);
-  std::vector<std::vector<BatchItem>> items(kBatchLxMax + 1);
-  std::vector<std::vector<double>> cost(kBatchLxMax + 1);
-  std::vector<size_t> smem(kBatchLxMax + 1, 0);
+  std::vector<int> mbody(nmesh, ax::kBodyKLoop);
+  // per (lx, layout): key = 2 lx + layout
+  const int nkey = 2 * (kBatchLxMax + 1);
+  std::vector<std::vector<BatchItem>> items(nkey);
+  std::vector<std::vector<double>> cost(nkey);
+  std::vector<size_t> smem(nkey, 0);
   double flops = 0, bytes = 0;
   for (int m = 0; m < nmesh; ++m) {
     const ax_batch_mesh &s = meshes[m];
@@ -139,8 +153,11 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
                                        s.g13, s.g23))
       return AX_EINVAL;
     int epb;
-    if (f64 && ax::batch_uses_eo(s.lx)) {
-      // even-odd body: (lx/2)^3 threads per element, same choice as ax_helm
+    const int body = f64 ? choose_body(s.lx) : ax::kBodyKLoop;
+    mbody[m] = body;
+    const int key = 2 * s.lx + body;
+    if (body == ax::kBodyEvenOdd) {
+      // even-odd body: (lx/2)^3 threads per element
       const int h = s.lx / 2;
       epb = std::max(1, kBatchThreads / (h * h * h));
     } else {
@@ -150,12 +167,12 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
     }
     mh[m] = BatchMeshDev{s.lx, epb, s.w, s.u, s.dx, s.dxt, s.h1,
                          {s.g11, s.g22, s.g33, s.g12, s.g13, s.g23}, nullptr};
-    smem[s.lx] = std::max(smem[s.lx], body_smem(f64, s.lx, epb));
+    smem[key] = std::max(smem[key], body_smem(f64, s.lx, body, epb));
     const double l = s.lx, l3 = l * l * l;
     for (long long e = 0; e < s.nelv; e += epb) {
       const int nel = (int)std::min<long long>(epb, s.nelv - e);
-      items[s.lx].push_back(BatchItem{m, nel, e});
-      cost[s.lx].push_back(nel * (l3 * l + 2.0 * l3));
+      items[key].push_back(BatchItem{m, nel, e});
+      cost[key].push_back(nel * (l3 * l + 2.0 * l3));
     }
     flops += (double)s.nelv * (12.0 * l3 * l + 18.0 * l3);
     bytes += (double)s.nelv * 9.0 * l3 * (f64 ? 8 : 4);
@@ -167,19 +184,20 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
   std::vector<BatchItem> flat;
   std::vector<int> start;
   size_t smem_max = 0;
-  for (int lx = kBatchLxMin; lx <= kBatchLxMax; ++lx) {
-    if (items[lx].empty()) continue;
+  for (int key = 2 * kBatchLxMin; key < nkey; ++key) {
+    if (items[key].empty()) continue;
+    const int lx = key / 2, body = key % 2;
     int bps = 0;
-    int rc = ax::batch_lx_setup(f64, lx, smem[lx], &bps);
+    int rc = ax::batch_lx_setup(f64, lx, body, smem[key], &bps);
     if (rc) return rc;
     if (bps < 1) return AX_EINVAL;
     if (blocks_per_sm > 0) bps = std::min(bps, blocks_per_sm);
-    const int nb = std::max(1, std::min<int>(nsm * bps, (int)items[lx].size()));
+    const int nb = std::max(1, std::min<int>(nsm * bps, (int)items[key].size()));
     // longest processing time first onto the least-loaded block
-    std::vector<int> order(items[lx].size());
+    std::vector<int> order(items[key].size());
     for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
     std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return cost[lx][a] > cost[lx][b]; });
+                     [&](int a, int b) { return cost[key][a] > cost[key][b]; });
     using Load = std::pair<double, int>;
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
     for (int b = 0; b < nb; ++b) heap.push({0.0, b});
@@ -188,19 +206,20 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
       Load ld = heap.top();
       heap.pop();
       per[ld.second].push_back(q);
-      heap.push({ld.first + cost[lx][q], ld.second});
+      heap.push({ld.first + cost[key][q], ld.second});
     }
     Group g;
     g.lx = lx;
+    g.body = body;
     g.nblocks = nb;
-    g.smem = smem[lx];
+    g.smem = smem[key];
     g.item_off = (int)flat.size();
     g.start_off = (int)start.size();
     int cnt = 0;
     for (int b = 0; b < nb; ++b) {
       std::sort(per[b].begin(), per[b].end());  // memory order inside a block
       start.push_back(cnt);
-      for (int q : per[b]) flat.push_back(items[lx][q]), ++cnt;
+      for (int q : per[b]) flat.push_back(items[key][q]), ++cnt;
     }
     start.push_back(cnt);
     groups.push_back(g);
@@ -212,7 +231,7 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
   // fp64 meshes of the even-odd orders: prepare their geometry once
   for (int m = 0; f64 && m < nmesh; ++m) {
     const ax_batch_mesh &s = meshes[m];
-    if (!ax::batch_uses_eo(s.lx) || s.nelv == 0) continue;
+    if (mbody[m] != ax::kBodyEvenOdd || s.nelv == 0) continue;
     void *gp = nullptr;
     if (cudaMalloc(&gp, (size_t)s.nelv * 56 * s.lx * s.lx * s.lx) != cudaSuccess) {
       (void)cudaGetLastError();

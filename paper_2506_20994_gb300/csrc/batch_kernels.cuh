@@ -26,12 +26,18 @@ struct BatchItem {
 
 constexpr int kBatchThreads = 256;
 
-// The fp64 body matches ax_helm's choice for each lx.
+// Thread layout of a group's kernel: the k-loop body (lx^2 threads per
+// element walking k) or the even-odd body on prepared geometry ((lx/2)^3
+// threads per element, fp64 and even lx only).
+enum BatchBody : int { kBodyKLoop = 0, kBodyEvenOdd = 1 };
+
+// The default fp64 layout (ax_helm's built-in choice) for lx.
 __host__ __device__ constexpr bool batch_uses_eo(int lx) {
   return lx == 8 || lx == 10 || lx == 12;
 }
+__host__ __device__ constexpr bool batch_eo_ok(int lx) { return lx >= 4 && lx <= 12 && lx % 2 == 0; }
 
-template <bool F64, int LX>
+template <bool F64, int LX, int BODY = kBodyKLoop>
 __global__ void __launch_bounds__(kBatchThreads, 2)
 batch_lx_kernel(const BatchMeshDev *__restrict__ meshes, const BatchItem *__restrict__ items,
                 const int *__restrict__ block_start) {
@@ -40,8 +46,8 @@ batch_lx_kernel(const BatchMeshDev *__restrict__ meshes, const BatchItem *__rest
   for (int it = b0; it < b1; ++it) {
     const BatchItem itm = items[it];
     const BatchMeshDev m = meshes[itm.mesh];
-    if constexpr (F64 && batch_uses_eo(LX)) {
-      // every mesh of these orders has prepared geometry (the plan made it)
+    if constexpr (F64 && BODY == kBodyEvenOdd) {
+      // every mesh of this group has prepared geometry (the plan made it)
       df64eo_body<LX, true>((double *)m.w, (const double *)m.u, (const double *)m.dx,
                             (const double *)m.dxt, nullptr, nullptr, nullptr, nullptr, nullptr,
                             nullptr, nullptr, m.gp, itm.e0, itm.nel, m.epb, smem_raw);

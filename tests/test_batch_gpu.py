@@ -147,3 +147,31 @@ def test_variant_tuner_drives_auto(lx):
     finally:
         ax.tune_variant_set(lx, 0)
     assert ax.tune_variant_get(lx) == 0
+
+
+def test_batch_follows_the_tuned_thread_layout():
+    """With the variant table set, the plan switches thread layout per lx:
+    lx = 8 on the k-loop body (bitwise equal to ax_helm's double-float
+    k-loop variant) and lx = 6 on the even-odd body on prepared geometry
+    (bitwise equal to the operator handle)."""
+    meshes = [m for m in _meshes(ax.AX_BATCH_F64, count=8, seed=5) if m["lx"] in (6, 8)]
+    assert {m["lx"] for m in meshes} == {6, 8}
+    try:
+        ax.tune_variant_set(8, ax.AX_VARIANT_F64_DF)
+        ax.tune_variant_set(6, ax.AX_VARIANT_F64_DF_EO)
+        B = ax.Batch(meshes, dtype=ax.AX_BATCH_F64)
+        B.launch()
+        torch.cuda.synchronize()
+        for m in meshes:
+            assert rel_l2(m["w"].cpu().numpy(), m["ref"]) <= 1e-12
+            w1 = torch.empty_like(m["u"])
+            args = [m["u"], m["dx"], m["dxt"], m["h1"]] + [m[k] for k in GKEYS]
+            if m["lx"] == 8:
+                ax.ax_helm(w1, *args, 8, variant=ax.AX_VARIANT_F64_DF)
+            else:
+                ax.Operator(6, m["dx"], m["dxt"], m["h1"], *[m[k] for k in GKEYS]).apply(w1, m["u"])
+            torch.cuda.synchronize()
+            assert torch.equal(w1, m["w"]), m["lx"]
+    finally:
+        ax.tune_variant_set(8, 0)
+        ax.tune_variant_set(6, 0)

@@ -137,3 +137,16 @@ def test_poisson_cg_unchanged_by_the_handle():
     O = oracle.Problem(v, lx, f=oracle.poisson_rhs_f)
     r = O.b - O.apply(x.cpu().numpy().reshape(O.b.shape))
     assert np.sqrt(O.dot(r, r) / O.dot(O.b, O.b)) <= 1.5e-8
+
+
+def test_small_config_through_the_handle():
+    """E = 512 (8^3 perturbed hexahedra), lx = 8, h1 = 1, u uniform in
+    [-1, 1]: the small workload, the whole output against the oracle."""
+    lx = 8
+    case = operator_case((8, 8, 8), lx, seed=0, h1_const=1.0)
+    op, t = _op(case)
+    w = torch.full_like(t["u"], float("nan"))
+    op.apply(w, t["u"])
+    got = w.cpu().numpy()
+    assert rel_l2(got, case["w"]) <= 1e-12
+    assert np.abs(got - case["w"]).max() <= 1e-11 * np.abs(case["w"]).max()
