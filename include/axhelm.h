@@ -125,7 +125,8 @@ int ax_helm_h2(double *w, const double *u, const double *dx, const double *dxt,
                const double *g12, const double *g13, const double *g23, const double *h2,
                const double *B, int lx, int nelv, void *stream);
 /* w += hb .* u over n points (device fp64 / fp32): the mass term with its
- * coefficient folded in (hb = h2 .* B). */
+ * coefficient folded in (hb = h2 .* B).  Asynchronous; n == 0 is a no-op;
+ * AX_EINVAL for n < 0 or a NULL pointer with n > 0. */
 int ax_mass_add(double *w, const double *hb, const double *u, int64_t n, void *stream);
 int ax_mass_add_f32(float *w, const float *hb, const float *u, int64_t n, void *stream);
 
