@@ -86,7 +86,7 @@ constexpr size_t df64eo_smem(int epb) {
 // forms the solver's next search direction in place, pw = z + (*beta) pw
 // with z = minv .* r (+ corr when *use_corr, the flexible CG's learned
 // step), in fp64 with explicit roundings, and applies the operator to it.
-template <int LX, bool PREP = false, bool PUPD = false>
+template <int LX, bool PREP = false, bool PUPD = false, bool NBAR = true>
 __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double *__restrict__ u,
                                             const double *__restrict__ dx,
                                             const double *__restrict__ dxt,
@@ -141,6 +141,21 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
       (tr ? tn : cn)[q] = pk(-0.5f * P.hi, -0.5f * M.hi);
     }
   }
+
+  // Phase barriers: with whole warps per element, every thread of the block
+  // owning an element and at least four elements, each element synchronises
+  // on its own named barrier, so the elements of a block do not wait for one
+  // another (measured: faster with four elements per block, slower with two,
+  // where the extra block barrier for the coefficients costs more).
+  const bool elem_bar =
+      NBAR && (H3 % 32 == 0) && (int)blockDim.x == epb * H3 && epb >= 4 && epb <= 8;
+  auto phase_sync = [&]() {
+    if (elem_bar)
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + le), "r"(H3) : "memory");
+    else
+      __syncthreads();
+  };
+  if (elem_bar) __syncthreads();  // the coefficients above are shared by all elements
 
   const bool active = own && le < nel;
   const size_t eb = (size_t)(active ? e0 + le : 0) * N3;
@@ -229,7 +244,7 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
     }
     publish(gr);
   }
-  __syncthreads();
+  phase_sync();
 
   // geometry of corner pair q = (c, b) (prepared) or of corner q = (c, b, a)
   // (fp64 arrays); two in flight
@@ -343,7 +358,7 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
       }
     }
   }
-  __syncthreads();  // every thread has read the gradient lines
+  phase_sync();  // every thread of the element has read its gradient lines
 
   // ---- phase 4: (e, o) of the weighted gradient, one direction each
   if (own) {
@@ -360,7 +375,7 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
 #pragma unroll
       for (int a = 0; a < 2; ++a) At[lt(b, a) + kp] = eo_pair(gt[0][b][a], gt[1][b][a]);
   }
-  __syncthreads();
+  phase_sync();
 
   double dsum = 0.0;
   // ---- phase 5: transposed half-size contractions, summed, stored
@@ -453,7 +468,7 @@ ax_df64eo_prep_kernel(double *__restrict__ w, const double *__restrict__ u,
   const long long e0 = (long long)blockIdx.x * epb;
   const long long left = nelv - e0;
   const int nel = left < epb ? (int)left : epb;
-  df64eo_body<LX, true, PUPD>(w, u, dx, dxt, nullptr, nullptr, nullptr, nullptr, nullptr,
+  df64eo_body<LX, true, PUPD, false>(w, u, dx, dxt, nullptr, nullptr, nullptr, nullptr, nullptr,
                               nullptr, nullptr, gp, e0, nel, epb, smem_raw,
                               DOT ? dotp : nullptr, pw, r_in, minv_in, beta_p, corr_in,
                               use_corr_p);
