@@ -82,6 +82,56 @@ def test_deformed_elements_vs_kronecker(lx):
         assert ev[1] > 1e-8 * ev[-1]
 
 
+def _kron_xyz(lx, mats, h1, gs):
+    """Listing 2 with one matrix per direction as a dense matrix: buffer
+    m[l*lx + i] is the (i, l) entry of the 1-D factor, so the forward
+    gradient is (I(x)I(x)X, I(x)Y(x)I, Z(x)I(x)I) u and the transposed one
+    sums (I(x)I(x)Xt) wr + (I(x)Yt(x)I) ws + (Zt(x)I(x)I) wt."""
+    I = np.eye(lx)
+    X, Y, Z, Xt, Yt, Zt = (np.asarray(m).reshape(lx, lx).T for m in mats)
+    F = [np.kron(I, np.kron(I, X)), np.kron(I, np.kron(Y, I)), np.kron(Z, np.kron(I, I))]
+    T = [np.kron(I, np.kron(I, Xt)), np.kron(I, np.kron(Yt, I)), np.kron(Zt, np.kron(I, I))]
+    g11, g22, g33, g12, g13, g23 = (np.asarray(g).ravel() for g in gs)
+    G = [[g11, g12, g13], [g12, g22, g23], [g13, g23, g33]]
+    h = np.asarray(h1).ravel()
+    A = np.zeros((lx ** 3, lx ** 3))
+    for a in range(3):
+        for b in range(3):
+            A += T[a] @ np.diag(h * G[a][b]) @ F[b]
+    return A
+
+
+@pytest.mark.parametrize("lx", [2, 3, 5])
+def test_separate_direction_matrices_vs_kronecker(lx):
+    """The full signature of Listings 1-2 (dx, dy, dz, dxt, dyt, dzt): six
+    unrelated random matrices on deformed elements against the dense
+    Kronecker form; each matrix reaches its own direction (a swapped pair
+    fails)."""
+    v = synth.box_vertices(2, seed=5)
+    geo = oracle.box_geometry(v, lx)
+    h1 = synth.uniform(geo["jac"].shape, seed=6, lo=0.5, hi=2.0)
+    mats = [synth.uniform((lx * lx,), seed=10 + m) for m in range(6)]
+    dx, dy, dz, dxt, dyt, dzt = mats
+    n3 = lx ** 3
+    for e in (0, 5):
+        gs = [geo[k][e] for k in ("g11", "g22", "g33", "g12", "g13", "g23")]
+        A = np.zeros((n3, n3))
+        for p in range(n3):
+            u = np.zeros(n3)
+            u[p] = 1.0
+            A[:, p] = oracle.ax_helm(u, dx, dxt, h1[e], *gs, lx, dy=dy, dz=dz, dyt=dyt, dzt=dzt)
+        A_ref = _kron_xyz(lx, mats, h1[e], gs)
+        np.testing.assert_allclose(A, A_ref, atol=1e-12 * np.abs(A_ref).max())
+        swapped = _kron_xyz(lx, [dy, dx, dz, dxt, dyt, dzt], h1[e], gs)
+        assert np.abs(A - swapped).max() > 1e-3 * np.abs(A_ref).max()
+    # with dy = dz = dx and dyt = dzt = dxt it is the one-matrix form, bit for bit
+    u = synth.uniform(geo["jac"].shape, seed=7)
+    gs = [geo[k] for k in ("g11", "g22", "g33", "g12", "g13", "g23")]
+    a = oracle.ax_helm(u, dx, dxt, h1, *gs, lx)
+    b = oracle.ax_helm(u, dx, dxt, h1, *gs, lx, dy=dx, dz=dx, dyt=dxt, dzt=dxt)
+    assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("lx", [2, 4, 8, 12])
 def test_constants_in_kernel(lx):
     v = synth.box_vertices(3, seed=1)
