@@ -98,6 +98,25 @@ int ax_helm_bf16(float *w, const ax_bf16 *u, const float *dx, const float *dxt,
                  const ax_bf16 *g33, const ax_bf16 *g12, const ax_bf16 *g13,
                  const ax_bf16 *g23, int lx, int nelv, void *stream);
 
+/* The full argument list of the paper's interface and kernel (Listings 1
+ * and 2): one lx x lx matrix per direction, dx, dy, dz for the forward
+ * gradient (ur from dx along i, us from dy along j, ut from dz along k) and
+ * dxt, dyt, dzt for the transposed contractions, each in the same layout as
+ * ax_helm's dx (entry [l * lx + i] multiplies the value at l to give the
+ * one at i).  All six are read as given (no relation between them is
+ * assumed).  The paper orders its last two arguments (nelv, lx) and passes a
+ * handle first; here the order is ax_helm's and the operator handle is
+ * ax_op.  fp64-accurate as ax_helm (double-float k-loop kernel for lx <= 12,
+ * fp64 units above).  If dy == dz == dx and dyt == dzt == dxt (the same
+ * pointers) the call is exactly ax_helm.  Device arrays, borrowed;
+ * asynchronous on `stream`.  Errors as ax_helm (the four extra matrices
+ * must not be NULL when nelv > 0). */
+int ax_helm_xyz(double *w, const double *u, const double *dx, const double *dy,
+                const double *dz, const double *dxt, const double *dyt, const double *dzt,
+                const double *h1, const double *g11, const double *g22, const double *g33,
+                const double *g12, const double *g13, const double *g23, int lx, int nelv,
+                void *stream);
+
 /* The operator on host buffers (the paper's interface passes device
  * arrays; this serves callers whose fields live in host memory): w, u, h1
  * and G are host arrays of nelv * lx^3 doubles, dx and dxt host arrays of

@@ -25,7 +25,7 @@ __all__ = [
     "AX_VARIANT_F64_NATIVE", "AX_VARIANT_F64_DF_EO", "df64_roundtrip", "build", "GatherScatter", "Poisson",
     "AX_PREC_F32", "AX_PREC_BF16", "Batch", "tune", "tune_set", "tune_get", "AX_BATCH_F64",
     "AX_BATCH_F32", "fourier_coefficient", "Mlp", "mlp_init_params", "training_pairs", "train_mlp", "axpby", "iterate_pairs",
-    "train_energy", "AX_MLP_TANH", "AX_MLP_SYM", "Operator", "ax_helm_h2", "ax_helm_host", "tune_variant",
+    "train_energy", "AX_MLP_TANH", "AX_MLP_SYM", "Operator", "ax_helm_h2", "ax_helm_xyz", "ax_helm_host", "tune_variant",
     "tune_variant_set", "tune_variant_get",
 ]
 
@@ -137,6 +137,18 @@ def ax_helm(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx: int,
                                g33.data_ptr(), g12.data_ptr(), g13.data_ptr(), g23.data_ptr(),
                                lx, nel, elems_per_block, _stream())
     check("ax_helm", rc)
+
+
+def ax_helm_xyz(w, u, dx, dy, dz, dxt, dyt, dzt, h1, g11, g22, g33, g12, g13, g23,
+                lx: int) -> None:
+    """w <- element-local stiffness apply of u with one matrix per direction
+    (the full argument list of Listings 1-2), fp64 (ax_helm_xyz)."""
+    import torch
+    f = torch.float64
+    nel = _dev_args(lx, w, [u, h1, g11, g22, g33, g12, g13, g23], [f] * 9,
+                    [dx, dy, dz, dxt, dyt, dzt], f)
+    ts = [w, u, dx, dy, dz, dxt, dyt, dzt, h1, g11, g22, g33, g12, g13, g23]
+    check("ax_helm_xyz", lib().ax_helm_xyz(*[t.data_ptr() for t in ts], lx, nel, _stream()))
 
 
 def ax_helm_host(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx: int,

@@ -56,6 +56,7 @@ PROTOTYPES = {
     "ax_mlp_create": (c_int, [P, c_int, c_int]),
     "ax_mlp_create_ex": (c_int, [P, c_int, c_int, c_int]),
     "ax_helm_h2": (c_int, [P] * 13 + [c_int, c_int, P]),
+    "ax_helm_xyz": (c_int, [P] * 15 + [c_int, c_int, P]),
     "ax_helm_host": (c_int, [P] * 11 + [c_int, c_int, c_int, P]),
     "ax_tune_variant_run": (c_int, [c_int, c_int] + [P] * 11 + [c_int, P, P, P]),
     "ax_tune_variant_set": (c_int, [c_int, c_int]),

@@ -21,12 +21,15 @@
 
 namespace ax {
 
-template <int LX>
+// XYZ: one matrix per direction as in the full signature of Listings 1-2
+// (dx, dy, dz forward; dxt, dyt, dzt transposed), six staged matrices;
+// otherwise dx and dxt serve all three directions.
+template <int LX, bool XYZ = false>
 constexpr size_t df64_smem(int epb) {
-  return (2 * (size_t)LX * LX + (size_t)epb * 3 * LX * LX * LX) * sizeof(df::df2);
+  return ((XYZ ? 6 : 2) * (size_t)LX * LX + (size_t)epb * 3 * LX * LX * LX) * sizeof(df::df2);
 }
 
-template <int LX>
+template <int LX, bool XYZ = false>
 __device__ __forceinline__ void df64_body(double *__restrict__ w, const double *__restrict__ u,
                                           const double *__restrict__ dx,
                                           const double *__restrict__ dxt,
@@ -37,24 +40,44 @@ __device__ __forceinline__ void df64_body(double *__restrict__ w, const double *
                                           const double *__restrict__ g12,
                                           const double *__restrict__ g13,
                                           const double *__restrict__ g23, long long e0, int nel,
-                                          int epb, unsigned char *smem_raw) {
+                                          int epb, unsigned char *smem_raw,
+                                          const double *__restrict__ dy = nullptr,
+                                          const double *__restrict__ dz = nullptr,
+                                          const double *__restrict__ dyt = nullptr,
+                                          const double *__restrict__ dzt = nullptr) {
   using namespace df;
   constexpr int N2 = LX * LX;
   constexpr int N3 = LX * N2;
   df2 *sdx = reinterpret_cast<df2 *>(smem_raw);
   df2 *sdxt = sdx + N2;
+  // per-direction matrices (the same two unless XYZ)
+  df2 *sdy = sdx, *sdz = sdx, *sdyt = sdxt, *sdzt = sdxt;
+  df2 *stage = sdxt + N2;
+  if constexpr (XYZ) {
+    sdy = stage;
+    sdz = sdy + N2;
+    sdyt = sdz + N2;
+    sdzt = sdyt + N2;
+    stage = sdzt + N2;
+  }
   const bool own = (int)threadIdx.x < epb * N2;
   const int le = own ? (int)threadIdx.x / N2 : 0;
   const int p = (int)threadIdx.x - le * N2;
   const int i = p % LX;
   const int j = p / LX;
-  df2 *su = sdxt + N2 + (size_t)le * 3 * N3;
+  df2 *su = stage + (size_t)le * 3 * N3;
   df2 *swr = su + N3;
   df2 *sws = swr + N3;
 
   for (int t = threadIdx.x; t < N2; t += blockDim.x) {
     sdx[t] = split(__ldg(dx + t));
     sdxt[t] = split(__ldg(dxt + t));
+    if constexpr (XYZ) {
+      sdy[t] = split(__ldg(dy + t));
+      sdz[t] = split(__ldg(dz + t));
+      sdyt[t] = split(__ldg(dyt + t));
+      sdzt[t] = split(__ldg(dzt + t));
+    }
   }
   const bool active = own && le < nel;
   const size_t base = (size_t)(active ? e0 + le : 0) * N3 + p;
@@ -80,13 +103,13 @@ __device__ __forceinline__ void df64_body(double *__restrict__ w, const double *
 #pragma unroll
     for (int k = 0; k < LX; ++k) {
       acc ar = prod(sdx[i], su[k * N2 + j * LX]);
-      acc as = prod(sdx[j], su[k * N2 + i]);
-      acc at = prod(sdx[k], uk[0]);
+      acc as = prod(sdy[j], su[k * N2 + i]);
+      acc at = prod(sdz[k], uk[0]);
 #pragma unroll
       for (int l = 1; l < LX; ++l) {
         mac(ar, sdx[l * LX + i], su[k * N2 + j * LX + l]);
-        mac(as, sdx[l * LX + j], su[k * N2 + l * LX + i]);
-        mac(at, sdx[l * LX + k], uk[l]);
+        mac(as, sdy[l * LX + j], su[k * N2 + l * LX + i]);
+        mac(at, sdz[l * LX + k], uk[l]);
       }
       const df2 ur = result(ar), us = result(as), ut = result(at);
       df2 wr{0.f, 0.f}, ws{0.f, 0.f}, wt{0.f, 0.f};
@@ -114,9 +137,9 @@ __device__ __forceinline__ void df64_body(double *__restrict__ w, const double *
 #pragma unroll
       for (int kk = 0; kk < LX; ++kk) {
         if (k == 0)
-          wacc[kk] = prod(sdxt[kk], wt);
+          wacc[kk] = prod(sdzt[kk], wt);
         else
-          mac(wacc[kk], sdxt[k * LX + kk], wt);
+          mac(wacc[kk], sdzt[k * LX + kk], wt);
       }
     }
   }
@@ -129,7 +152,7 @@ __device__ __forceinline__ void df64_body(double *__restrict__ w, const double *
 #pragma unroll
       for (int l = 0; l < LX; ++l) {
         mac(a, sdxt[l * LX + i], swr[k * N2 + j * LX + l]);
-        mac(a, sdxt[l * LX + j], sws[k * N2 + l * LX + i]);
+        mac(a, sdyt[l * LX + j], sws[k * N2 + l * LX + i]);
       }
       const df2 r = result(a);
       if (active) w[base + (size_t)k * N2] = join(r.hi, r.lo);

@@ -31,7 +31,11 @@ AX_D float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
 // AHEAD: geometry loads one k-plane ahead (measured faster for the
 // single-mesh fp32-storage kernel only).
-template <int LX, typename SU, typename S, typename T, typename W, bool AHEAD = false>
+// XYZ: one matrix per direction (dx, dy, dz forward; dxt, dyt, dzt
+// transposed) as in the full signature of Listings 1-2; otherwise dx and
+// dxt serve all three directions.
+template <int LX, typename SU, typename S, typename T, typename W, bool AHEAD = false,
+          bool XYZ = false>
 __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restrict__ u,
                                            const T *__restrict__ dx, const T *__restrict__ dxt,
                                            const S *__restrict__ h1, const S *__restrict__ g11,
@@ -39,23 +43,42 @@ __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restri
                                            const S *__restrict__ g12, const S *__restrict__ g13,
                                            const S *__restrict__ g23, long long e0, int nel,
                                            int epb, unsigned char *smem_raw,
-                                           double *__restrict__ dotp = nullptr) {
+                                           double *__restrict__ dotp = nullptr,
+                                           const T *__restrict__ dy = nullptr,
+                                           const T *__restrict__ dz = nullptr,
+                                           const T *__restrict__ dyt = nullptr,
+                                           const T *__restrict__ dzt = nullptr) {
   constexpr int N2 = LX * LX;
   constexpr int N3 = LX * N2;
   T *sdx = reinterpret_cast<T *>(smem_raw);
   T *sdxt = sdx + N2;
+  T *sdy = sdx, *sdz = sdx, *sdyt = sdxt, *sdzt = sdxt;
+  T *stage = sdxt + N2;
+  if constexpr (XYZ) {
+    sdy = stage;
+    sdz = sdy + N2;
+    sdyt = sdz + N2;
+    sdzt = sdyt + N2;
+    stage = sdzt + N2;
+  }
   const bool own = (int)threadIdx.x < epb * N2;
   const int le = own ? (int)threadIdx.x / N2 : 0;
   const int p = (int)threadIdx.x - le * N2;
   const int i = p % LX;
   const int j = p / LX;
-  T *su = sdxt + N2 + (size_t)le * 3 * N3;
+  T *su = stage + (size_t)le * 3 * N3;
   T *swr = su + N3;
   T *sws = swr + N3;
 
   for (int t = threadIdx.x; t < N2; t += blockDim.x) {
     sdx[t] = dx[t];
     sdxt[t] = dxt[t];
+    if constexpr (XYZ) {
+      sdy[t] = dy[t];
+      sdz[t] = dz[t];
+      sdyt[t] = dyt[t];
+      sdzt[t] = dzt[t];
+    }
   }
   const bool active = own && le < nel;
   const size_t base = (size_t)(active ? e0 + le : 0) * N3 + p;
@@ -107,8 +130,8 @@ __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restri
 #pragma unroll
       for (int l = 0; l < LX; ++l) {
         ur = fma_t(sdx[l * LX + i], su[k * N2 + j * LX + l], ur);
-        us = fma_t(sdx[l * LX + j], su[k * N2 + l * LX + i], us);
-        ut = fma_t(sdx[l * LX + k], uk[l], ut);
+        us = fma_t(sdy[l * LX + j], su[k * N2 + l * LX + i], us);
+        ut = fma_t(sdz[l * LX + k], uk[l], ut);
       }
       T wr = T(0), ws = T(0), wt = T(0);
       if (active) {
@@ -122,7 +145,7 @@ __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restri
       swr[k * N2 + p] = wr;
       sws[k * N2 + p] = ws;
 #pragma unroll
-      for (int kk = 0; kk < LX; ++kk) wacc[kk] = fma_t(sdxt[k * LX + kk], wt, wacc[kk]);
+      for (int kk = 0; kk < LX; ++kk) wacc[kk] = fma_t(sdzt[k * LX + kk], wt, wacc[kk]);
     }
   }
   __syncthreads();
@@ -135,7 +158,7 @@ __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restri
 #pragma unroll
       for (int l = 0; l < LX; ++l) {
         acc = fma_t(sdxt[l * LX + i], swr[k * N2 + j * LX + l], acc);
-        acc = fma_t(sdxt[l * LX + j], sws[k * N2 + l * LX + i], acc);
+        acc = fma_t(sdyt[l * LX + j], sws[k * N2 + l * LX + i], acc);
       }
       if (active) w[base + (size_t)k * N2] = (W)acc;
       if (dotp) dsum = fma_t(uk[k], acc, dsum);
@@ -176,9 +199,9 @@ ax_kstep_kernel(W *__restrict__ w, const SU *__restrict__ u, const T *__restrict
 }
 
 // Shared-memory bytes of one block of the k-loop kernel.
-template <int LX, typename T>
+template <int LX, typename T, bool XYZ = false>
 constexpr size_t kstep_smem(int epb) {
-  return (2 * (size_t)LX * LX + (size_t)epb * 3 * LX * LX * LX) * sizeof(T);
+  return ((XYZ ? 6 : 2) * (size_t)LX * LX + (size_t)epb * 3 * LX * LX * LX) * sizeof(T);
 }
 
 // Default elements per block: about 256 threads, at least one element.
