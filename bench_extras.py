@@ -3,7 +3,8 @@
 Each section times one row of the hot path on synthetic, seeded inputs with
 CUDA events (kernels) or wall time around a synchronising solve (solvers):
 
-  modes    fp64-unit, fp32 and bf16 operator kernels on the main mesh
+  modes    fp64-unit, fp32 and bf16 operator kernels on the main mesh, and
+           the fp32 kernel with G formed from the corner vertices
   sweep    fp64 operator (handle, prepared geometry) and ax_helm on fp64
            geometry at E in {4096, 32768} x lx in {6, 8, 10, 12}
   cg       Poisson solve to a 1e-8 relative residual at E = 32768, lx = 8:
@@ -96,6 +97,32 @@ def modes(ax, d, lx, nel, hbm_peak):
                      "hbm_frac": round(bpp * npts / (ms * 1e-3) / 1e9 / hbm_peak, 4),
                      "bytes_per_point": bpp}
         del f, w
+    # fp32 with G formed from the corner vertices (h1 = 1): u and w only.
+    # Two buffer sets alternate (2 x 134 MB > L2) so no launch reads the
+    # previous one's data from L2.
+    from paper_2506_20994_gb300 import synth
+    n = round(nel ** (1.0 / 3.0))
+    if n ** 3 == nel:
+        dev = d["u"].device
+        xi, wq = (torch.as_tensor(a, device=dev) for a in ax.gll(lx))
+        cor = torch.as_tensor(ax.box_corners(synth.box_vertices(n, seed=0)), device=dev)
+        dx32, dxt32 = d["dx"].float(), d["dxt"].float()
+        us = [d["u"].float(), d["u"].float().clone()]
+        ws = [torch.empty_like(us[0]) for _ in range(2)]
+        k = [0]
+
+        def tri():
+            i = k[0] & 1
+            k[0] += 1
+            ax.ax_helm_trilinear_f32(ws[i], us[i], dx32, dxt32, None, cor.reshape(-1), xi, wq,
+                                     lx)
+        ms = _events_ms(tri, 30)
+        bpp = 8.0 + 192.0 / lx ** 3
+        out["f32_trilinear"] = {"gdofs": round(npts / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 4),
+                                "hbm_frac": round(bpp * npts / (ms * 1e-3) / 1e9 / hbm_peak, 4),
+                                "bytes_per_point": round(bpp, 3), "h1": "constant 1",
+                                "l2": "two alternating buffer sets (268 MB)"}
+        del us, ws, cor
     return out
 
 

@@ -117,6 +117,21 @@ int ax_helm_xyz(double *w, const double *u, const double *dx, const double *dy,
                 const double *g12, const double *g13, const double *g23, int lx, int nelv,
                 void *stream);
 
+/* fp32 operator with the geometric factors computed on the fly from each
+ * element's trilinear map instead of read from six stored fields (u and w,
+ * plus h1 unless it is NULL, are the only per-point streams: 8 or 12 bytes
+ * per point against 36).  corners: nelv * 24 fp64 values, the element's
+ * 8 vertices as written by ax_box_corners; xi, wq: the lx GLL nodes and
+ * weights (ax_gll); all device arrays, borrowed.  h1 == NULL means h1 = 1.
+ * Per point G = (w_i w_j w_k / det J) adj(J) adj(J)^T with J the Jacobian of
+ * the trilinear map, the same factors ax_box_geometry writes, then Listing
+ * 2's contractions, all in fp32 (edge vectors formed in fp64, rounded).
+ * Asynchronous on `stream`.  Errors as ax_helm (AX_EINVAL for a NULL
+ * pointer other than h1 when nelv > 0). */
+int ax_helm_trilinear_f32(float *w, const float *u, const float *dx, const float *dxt,
+                          const float *h1, const double *corners, const double *xi,
+                          const double *wq, int lx, int nelv, void *stream);
+
 /* The operator on host buffers (the paper's interface passes device
  * arrays; this serves callers whose fields live in host memory): w, u, h1
  * and G are host arrays of nelv * lx^3 doubles, dx and dxt host arrays of
@@ -492,6 +507,11 @@ int ax_dmat(int lx, double *dx, double *dxt);
 int ax_box_geometry(int nx, int ny, int nz, int lx, const double *vertices,
                     double *g11, double *g22, double *g33, double *g12,
                     double *g13, double *g23, double *mass, double *xyz);
+
+/* The 8 corner vertices of every element of the same box, corners[e*24 +
+ * ((c*2+b)*2+a)*3 + d] = vertex (ex+a, ey+b, ez+c), coordinate d: the input
+ * of ax_helm_trilinear_f32.  AX_EINVAL on bad sizes or NULL pointers. */
+int ax_box_corners(int nx, int ny, int nz, const double *vertices, double *corners);
 
 /* Global node id of every local point of the structured box (x fastest):
  * glob = X + NX*(Y + NY*Z), X = ex*(lx-1)+i, NX = nx*(lx-1)+1, ... */

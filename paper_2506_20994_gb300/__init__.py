@@ -25,7 +25,7 @@ __all__ = [
     "AX_VARIANT_F64_NATIVE", "AX_VARIANT_F64_DF_EO", "df64_roundtrip", "build", "GatherScatter", "Poisson",
     "AX_PREC_F32", "AX_PREC_BF16", "Batch", "tune", "tune_set", "tune_get", "AX_BATCH_F64",
     "AX_BATCH_F32", "fourier_coefficient", "Mlp", "mlp_init_params", "training_pairs", "train_mlp", "axpby", "iterate_pairs",
-    "train_energy", "AX_MLP_TANH", "AX_MLP_SYM", "Operator", "ax_helm_h2", "ax_helm_xyz", "ax_helm_host", "tune_variant",
+    "train_energy", "AX_MLP_TANH", "AX_MLP_SYM", "Operator", "ax_helm_h2", "ax_helm_xyz", "ax_helm_trilinear_f32", "box_corners", "ax_helm_host", "tune_variant",
     "tune_variant_set", "tune_variant_get",
 ]
 
@@ -58,6 +58,16 @@ def dmat(lx: int):
     dxt = np.empty(lx * lx)
     check("ax_dmat", lib().ax_dmat(lx, _addr(dx), _addr(dxt)))
     return dx, dxt
+
+
+def box_corners(vertices: np.ndarray) -> np.ndarray:
+    """(E, 2, 2, 2, 3) corner vertices [e][c][b][a][coord] of a box mesh
+    given its (nz+1, ny+1, nx+1, 3) vertex array (ax_box_corners)."""
+    v = np.ascontiguousarray(vertices, dtype=np.float64)
+    nz, ny, nx = (s - 1 for s in v.shape[:3])
+    out = np.empty((nx * ny * nz, 2, 2, 2, 3))
+    check("ax_box_corners", lib().ax_box_corners(nx, ny, nz, _addr(v), _addr(out)))
+    return out
 
 
 def box_geometry(vertices: np.ndarray, lx: int, want_xyz: bool = False) -> dict:
@@ -149,6 +159,24 @@ def ax_helm_xyz(w, u, dx, dy, dz, dxt, dyt, dzt, h1, g11, g22, g33, g12, g13, g2
                     [dx, dy, dz, dxt, dyt, dzt], f)
     ts = [w, u, dx, dy, dz, dxt, dyt, dzt, h1, g11, g22, g33, g12, g13, g23]
     check("ax_helm_xyz", lib().ax_helm_xyz(*[t.data_ptr() for t in ts], lx, nel, _stream()))
+
+
+def ax_helm_trilinear_f32(w, u, dx, dxt, h1, corners, xi, wq, lx: int) -> None:
+    """fp32 operator with G computed from each element's corner vertices
+    (ax_helm_trilinear_f32).  w, u, dx, dxt, h1: fp32 CUDA tensors (h1 may
+    be None: h1 = 1); corners (E*24), xi, wq (lx): fp64 CUDA tensors."""
+    import torch
+    f = torch.float32
+    fields = [u] if h1 is None else [u, h1]
+    nel = _dev_args(lx, w, fields, [f] * (len(fields) + 1), [dx, dxt], f)
+    for t, size in ((corners, nel * 24), (xi, lx), (wq, lx)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                and t.is_contiguous() and t.numel() == size):
+            raise ValueError("corners, xi, wq must be contiguous fp64 CUDA tensors")
+    check("ax_helm_trilinear_f32", lib().ax_helm_trilinear_f32(
+        w.data_ptr(), u.data_ptr(), dx.data_ptr(), dxt.data_ptr(),
+        None if h1 is None else h1.data_ptr(), corners.data_ptr(), xi.data_ptr(),
+        wq.data_ptr(), lx, nel, _stream()))
 
 
 def ax_helm_host(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx: int,

@@ -28,6 +28,7 @@ PROTOTYPES = {
     "ax_gll": (c_int, [c_int, P, P]),
     "ax_dmat": (c_int, [c_int, P, P]),
     "ax_box_geometry": (c_int, [c_int, c_int, c_int, c_int, P] + [P] * 8),
+    "ax_box_corners": (c_int, [c_int, c_int, c_int, P, P]),
     "ax_box_numbering": (c_int, [c_int, c_int, c_int, c_int, P]),
     "ax_df64_roundtrip": (c_int, [P, P, P, P, c_int64]),
     "ax_gs_setup": (c_int, [P, P, c_int64, c_void_p]),
@@ -57,6 +58,7 @@ PROTOTYPES = {
     "ax_mlp_create_ex": (c_int, [P, c_int, c_int, c_int]),
     "ax_helm_h2": (c_int, [P] * 13 + [c_int, c_int, P]),
     "ax_helm_xyz": (c_int, [P] * 15 + [c_int, c_int, P]),
+    "ax_helm_trilinear_f32": (c_int, [P] * 8 + [c_int, c_int, P]),
     "ax_helm_host": (c_int, [P] * 11 + [c_int, c_int, c_int, P]),
     "ax_tune_variant_run": (c_int, [c_int, c_int] + [P] * 11 + [c_int, P, P, P]),
     "ax_tune_variant_set": (c_int, [c_int, c_int]),

@@ -240,6 +240,22 @@ int ax_box_numbering(int nx, int ny, int nz, int lx, int64_t *glob) {
   return AX_OK;
 }
 
+int ax_box_corners(int nx, int ny, int nz, const double *vertices, double *corners) {
+  if (nx < 1 || ny < 1 || nz < 1 || !vertices || !corners) return AX_EINVAL;
+  const int64_t nel = (int64_t)nx * ny * nz;
+  for (int64_t e = 0; e < nel; ++e) {
+    const int64_t ex = e % nx, ey = (e / nx) % ny, ez = e / ((int64_t)nx * ny);
+    for (int c = 0; c < 2; ++c)
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) {
+          const int64_t v = ((ez + c) * (ny + 1) + (ey + b)) * (nx + 1) + (ex + a);
+          for (int d = 0; d < 3; ++d)
+            corners[e * 24 + ((c * 2 + b) * 2 + a) * 3 + d] = vertices[v * 3 + d];
+        }
+  }
+  return AX_OK;
+}
+
 // Host twin of the device fp64 <-> double-float conversions, so that their
 // bit manipulation can be checked without a GPU.
 int ax_df64_roundtrip(const double *x, float *hi, float *lo, double *back, int64_t n) {

@@ -64,6 +64,12 @@ def test_host_geometry_matches_oracle(lx):
     np.testing.assert_allclose(g["xyz"], go["xyz"], atol=1e-15)
 
 
+def test_host_corners_match_oracle():
+    for dims, seed in (((3, 2, 4), 21), ((1, 1, 1), 2)):
+        v = synth.box_vertices(*dims, seed=seed)
+        np.testing.assert_array_equal(ax.box_corners(v), oracle.element_corners(v))
+
+
 def test_host_numbering_matches_oracle():
     for dims, lx in (((3, 2, 4), 5), ((1, 1, 1), 2), ((2, 5, 3), 8)):
         np.testing.assert_array_equal(ax.box_numbering(*dims, lx), oracle.numbering(*dims, lx))
@@ -129,5 +135,13 @@ def test_argument_checks_need_no_gpu():
     assert lib.ax_helm(*nul, 8, -1, None) == _lib.AX_EINVAL
     assert lib.ax_helm_bf16(*nul, 1, 3, None) == _lib.AX_EINVAL
     assert lib.ax_helm_variant(99, *[1] * 11, 8, 4, 0, None) == _lib.AX_EINVAL
+    # the six-matrix and trilinear forms: same rules
+    assert lib.ax_helm_xyz(*[None] * 15, 8, 0, None) == _lib.AX_OK
+    assert lib.ax_helm_xyz(*[None] * 15, 8, 2, None) == _lib.AX_EINVAL
+    assert lib.ax_helm_xyz(*[None] * 15, 17, 0, None) == _lib.AX_EINVAL
+    assert lib.ax_helm_trilinear_f32(*[None] * 8, 8, 0, None) == _lib.AX_OK
+    assert lib.ax_helm_trilinear_f32(*[None] * 8, 8, 2, None) == _lib.AX_EINVAL
+    assert lib.ax_helm_trilinear_f32(*[None] * 8, 1, 0, None) == _lib.AX_EINVAL
+    assert lib.ax_box_corners(0, 1, 1, None, None) == _lib.AX_EINVAL
     assert lib.ax_gll(1, None, None) == _lib.AX_EINVAL
     assert lib.ax_dmat(17, None, None) == _lib.AX_EINVAL
