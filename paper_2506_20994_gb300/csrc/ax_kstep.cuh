@@ -28,14 +28,32 @@ constexpr bool kPrefetchGeometry = true;
 
 AX_D double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
 AX_D float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+AX_D float4 row4(const float *r, int q) { return reinterpret_cast<const float4 *>(r)[q]; }
+
+// The single-mesh kernel's row-table form (VEC in kstep_body): fp32
+// arithmetic and lx divisible by 4.  Rows padded to RS floats so that the
+// 16-byte loads of different rows fall in different banks.
+template <int LX, typename T>
+constexpr bool kstep_vec() {
+  return sizeof(T) == 4 && LX % 4 == 0;
+}
+template <int LX, bool VEC>
+constexpr int kstep_rs() {
+  return VEC && LX % 8 == 0 ? LX + 4 : LX;
+}
 
 // AHEAD: geometry loads one k-plane ahead (measured faster for the
 // single-mesh fp32-storage kernel only).
 // XYZ: one matrix per direction (dx, dy, dz forward; dxt, dyt, dzt
 // transposed) as in the full signature of Listings 1-2; otherwise dx and
 // dxt serve all three directions.
+// VEC (fp32 arithmetic, lx divisible by 4, one matrix pair): the matrices
+// are staged as row tables padded to RS floats (kstep_rs), so every
+// contraction reads its matrix row, and the r-lines of u and wr, as 16-byte
+// loads; a quarter of the shared-memory load instructions of the scalar form
+// for those operands.  Same summation order as the scalar form.
 template <int LX, typename SU, typename S, typename T, typename W, bool AHEAD = false,
-          bool XYZ = false>
+          bool XYZ = false, bool VEC = false>
 __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restrict__ u,
                                            const T *__restrict__ dx, const T *__restrict__ dxt,
                                            const S *__restrict__ h1, const S *__restrict__ g11,
@@ -50,10 +68,21 @@ __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restri
                                            const T *__restrict__ dzt = nullptr) {
   constexpr int N2 = LX * LX;
   constexpr int N3 = LX * N2;
+  static_assert(!VEC || (sizeof(T) == 4 && LX % 4 == 0 && !XYZ), "VEC: fp32, lx % 4 == 0");
+  constexpr int RS = kstep_rs<LX, VEC>();
   T *sdx = reinterpret_cast<T *>(smem_raw);
   T *sdxt = sdx + N2;
   T *sdy = sdx, *sdz = sdx, *sdyt = sdxt, *sdzt = sdxt;
   T *stage = sdxt + N2;
+  // VEC tables: Fd[a][l] = dx[l*lx + a], Bd[a][l] = dxt[l*lx + a],
+  // Td[a][b] = dxt[a*lx + b]
+  T *Fd = sdx, *Bd = sdx, *Td = sdx;
+  if constexpr (VEC) {
+    Fd = reinterpret_cast<T *>(smem_raw);
+    Bd = Fd + LX * RS;
+    Td = Bd + LX * RS;
+    stage = Td + LX * RS;
+  }
   if constexpr (XYZ) {
     sdy = stage;
     sdz = sdy + N2;
@@ -70,7 +99,13 @@ __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restri
   T *swr = su + N3;
   T *sws = swr + N3;
 
-  for (int t = threadIdx.x; t < N2; t += blockDim.x) {
+  for (int t = threadIdx.x; VEC && t < N2; t += blockDim.x) {
+    const int a = t / LX, b = t % LX;
+    Fd[b * RS + a] = dx[t];
+    Bd[b * RS + a] = dxt[t];
+    Td[a * RS + b] = dxt[t];
+  }
+  for (int t = threadIdx.x; !VEC && t < N2; t += blockDim.x) {
     sdx[t] = dx[t];
     sdxt[t] = dxt[t];
     if constexpr (XYZ) {
@@ -127,11 +162,32 @@ __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restri
         if (active && k + 1 < LX) load_plane(k + 1, gnext);
       }
       T ur = T(0), us = T(0), ut = T(0);
+      if constexpr (VEC) {
 #pragma unroll
-      for (int l = 0; l < LX; ++l) {
-        ur = fma_t(sdx[l * LX + i], su[k * N2 + j * LX + l], ur);
-        us = fma_t(sdy[l * LX + j], su[k * N2 + l * LX + i], us);
-        ut = fma_t(sdz[l * LX + k], uk[l], ut);
+        for (int q = 0; q < LX / 4; ++q) {
+          const float4 fi = row4(Fd + i * RS, q), fj = row4(Fd + j * RS, q);
+          const float4 fk = row4(Fd + k * RS, q), v = row4(su + k * N2 + j * LX, q);
+          const T *c = su + k * N2 + 4 * q * LX + i;
+          ur = fma_t(fi.x, v.x, ur);
+          us = fma_t(fj.x, c[0], us);
+          ut = fma_t(fk.x, uk[4 * q], ut);
+          ur = fma_t(fi.y, v.y, ur);
+          us = fma_t(fj.y, c[LX], us);
+          ut = fma_t(fk.y, uk[4 * q + 1], ut);
+          ur = fma_t(fi.z, v.z, ur);
+          us = fma_t(fj.z, c[2 * LX], us);
+          ut = fma_t(fk.z, uk[4 * q + 2], ut);
+          ur = fma_t(fi.w, v.w, ur);
+          us = fma_t(fj.w, c[3 * LX], us);
+          ut = fma_t(fk.w, uk[4 * q + 3], ut);
+        }
+      } else {
+#pragma unroll
+        for (int l = 0; l < LX; ++l) {
+          ur = fma_t(sdx[l * LX + i], su[k * N2 + j * LX + l], ur);
+          us = fma_t(sdy[l * LX + j], su[k * N2 + l * LX + i], us);
+          ut = fma_t(sdz[l * LX + k], uk[l], ut);
+        }
       }
       T wr = T(0), ws = T(0), wt = T(0);
       if (active) {
@@ -144,8 +200,19 @@ __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restri
       }
       swr[k * N2 + p] = wr;
       sws[k * N2 + p] = ws;
+      if constexpr (VEC) {
 #pragma unroll
-      for (int kk = 0; kk < LX; ++kk) wacc[kk] = fma_t(sdzt[k * LX + kk], wt, wacc[kk]);
+        for (int q = 0; q < LX / 4; ++q) {
+          const float4 t4 = row4(Td + k * RS, q);
+          wacc[4 * q] = fma_t(t4.x, wt, wacc[4 * q]);
+          wacc[4 * q + 1] = fma_t(t4.y, wt, wacc[4 * q + 1]);
+          wacc[4 * q + 2] = fma_t(t4.z, wt, wacc[4 * q + 2]);
+          wacc[4 * q + 3] = fma_t(t4.w, wt, wacc[4 * q + 3]);
+        }
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < LX; ++kk) wacc[kk] = fma_t(sdzt[k * LX + kk], wt, wacc[kk]);
+      }
     }
   }
   __syncthreads();
@@ -155,10 +222,27 @@ __device__ __forceinline__ void kstep_body(W *__restrict__ w, const SU *__restri
 #pragma unroll
     for (int k = 0; k < LX; ++k) {
       T acc = wacc[k];
+      if constexpr (VEC) {
 #pragma unroll
-      for (int l = 0; l < LX; ++l) {
-        acc = fma_t(sdxt[l * LX + i], swr[k * N2 + j * LX + l], acc);
-        acc = fma_t(sdyt[l * LX + j], sws[k * N2 + l * LX + i], acc);
+        for (int q = 0; q < LX / 4; ++q) {
+          const float4 bi = row4(Bd + i * RS, q), bj = row4(Bd + j * RS, q);
+          const float4 v = row4(swr + k * N2 + j * LX, q);
+          const T *c = sws + k * N2 + 4 * q * LX + i;
+          acc = fma_t(bi.x, v.x, acc);
+          acc = fma_t(bj.x, c[0], acc);
+          acc = fma_t(bi.y, v.y, acc);
+          acc = fma_t(bj.y, c[LX], acc);
+          acc = fma_t(bi.z, v.z, acc);
+          acc = fma_t(bj.z, c[2 * LX], acc);
+          acc = fma_t(bi.w, v.w, acc);
+          acc = fma_t(bj.w, c[3 * LX], acc);
+        }
+      } else {
+#pragma unroll
+        for (int l = 0; l < LX; ++l) {
+          acc = fma_t(sdxt[l * LX + i], swr[k * N2 + j * LX + l], acc);
+          acc = fma_t(sdyt[l * LX + j], sws[k * N2 + l * LX + i], acc);
+        }
       }
       if (active) w[base + (size_t)k * N2] = (W)acc;
       if (dotp) dsum = fma_t(uk[k], acc, dsum);
@@ -194,14 +278,17 @@ ax_kstep_kernel(W *__restrict__ w, const SU *__restrict__ u, const T *__restrict
   const long long left = nelv - e0;
   const int nel = left < epb ? (int)left : epb;
   constexpr bool ahead = sizeof(S) == 4 && sizeof(T) == 4;
-  kstep_body<LX, SU, S, T, W, ahead>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, e0, nel,
-                                     epb, smem_raw, DOT ? dotp : nullptr);
+  kstep_body<LX, SU, S, T, W, ahead, false, kstep_vec<LX, T>()>(
+      w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, e0, nel, epb, smem_raw,
+      DOT ? dotp : nullptr);
 }
 
-// Shared-memory bytes of one block of the k-loop kernel.
-template <int LX, typename T, bool XYZ = false>
+// Shared-memory bytes of one block of the k-loop kernel (VEC: the single-mesh
+// kernel's padded matrix tables).
+template <int LX, typename T, bool XYZ = false, bool VEC = false>
 constexpr size_t kstep_smem(int epb) {
-  return ((XYZ ? 6 : 2) * (size_t)LX * LX + (size_t)epb * 3 * LX * LX * LX) * sizeof(T);
+  const size_t tables = VEC ? 3 * (size_t)LX * kstep_rs<LX, VEC>() : (XYZ ? 6 : 2) * (size_t)LX * LX;
+  return (tables + (size_t)epb * 3 * LX * LX * LX) * sizeof(T);
 }
 
 // Default elements per block: about 256 threads, at least one element.
@@ -217,7 +304,7 @@ int launch_kstep(W *w, const SU *u, const T *dx, const T *dxt, const S *h1, cons
                  int nelv, int epb, cudaStream_t stream, double *dotp = nullptr) {
   if (epb <= 0) epb = kstep_default_epb(LX);
   if (epb * LX * LX > 1024) return AX_EINVAL;
-  const size_t smem = kstep_smem<LX, T>(epb);
+  const size_t smem = kstep_smem<LX, T, false, kstep_vec<LX, T>()>(epb);
   auto kern = dotp ? ax_kstep_kernel<LX, SU, S, T, W, true> : ax_kstep_kernel<LX, SU, S, T, W>;
   static size_t granted[2] = {48 * 1024, 48 * 1024};  // per instantiation
   if (smem > granted[dotp != nullptr]) {
