@@ -238,8 +238,11 @@ def run_reference(args, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "ms_per_step": None,
-        "config": {"workload": f"fp64 ax_helm, box {args.n}^3 = {args.n ** 3} hexahedra, "
-                               f"lx={args.lx}", "E": args.n ** 3, "lx": args.lx},
+        "config": {"workload": f"fp64 ax_helm, box {args.n}^3 = {args.n ** 3} perturbed "
+                               f"hexahedra, lx={args.lx}", "E": args.n ** 3, "lx": args.lx,
+                   "points": args.n ** 3 * args.lx ** 3,
+                   "entry": "oracle C loop nest (OpenMP over elements) on the host cores",
+                   "parallelism": "rank 0 only"},
         "cpu_baseline": base,
         "e2e": {"value": base["value"], "unit": "GDOF/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
