@@ -22,6 +22,12 @@
  *    cudaStream_t passed as void*; NULL is the legacy default stream); it
  *    neither allocates nor synchronises unless its comment says so.
  *  - Output buffers must not alias inputs.
+ *  - Devices: a call runs on the device current on the calling host thread
+ *    (cudaSetDevice), and its pointers and stream must belong to that
+ *    device.  A handle (ax_op, ax_gs, ax_poisson, ax_mlp, ax_batch) owns
+ *    memory on the device current at its creation and is used and destroyed
+ *    with that device current.  Several devices may be driven from one
+ *    process; per-kernel launch settings are kept per device.
  *  - Return value: AX_OK (0) on success or a negative AX_E* code.  Launch
  *    failures are reported from cudaPeekAtLastError (AX_ELAUNCH); nothing
  *    aborts the process.

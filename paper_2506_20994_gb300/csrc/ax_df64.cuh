@@ -184,15 +184,8 @@ int launch_df64(double *w, const double *u, const double *dx, const double *dxt,
   if (epb * LX * LX > 256) return AX_EINVAL;
   const size_t smem = df64_smem<LX>(epb);
   auto kern = ax_df64_kernel<LX>;
-  static size_t granted = 48 * 1024;
-  if (smem > granted) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-      (void)cudaGetLastError();
-      return AX_EINVAL;
-    }
-    granted = smem;
-  }
+  static std::atomic<size_t> granted[kMaxDevices];
+  if (!grant_smem(kern, smem, granted)) return AX_EINVAL;
   const unsigned grid = (unsigned)((nelv + epb - 1) / epb);
   kern<<<grid, epb * LX * LX, smem, stream>>>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23,
                                               nelv, epb);

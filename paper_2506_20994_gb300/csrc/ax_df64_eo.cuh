@@ -516,15 +516,8 @@ int launch_df64eo(double *w, const double *u, const double *dx, const double *dx
   if (epb * H3 > 256) return AX_EINVAL;
   const size_t smem = df64eo_smem<LX>(epb);
   auto kern = ax_df64eo_kernel<LX>;
-  static size_t granted = 48 * 1024;
-  if (smem > granted) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-      (void)cudaGetLastError();
-      return AX_EINVAL;
-    }
-    granted = smem;
-  }
+  static std::atomic<size_t> granted[kMaxDevices];
+  if (!grant_smem(kern, smem, granted)) return AX_EINVAL;
   const unsigned grid = (unsigned)((nelv + epb - 1) / epb);
   kern<<<grid, epb * H3, smem, stream>>>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nelv,
                                          epb);
@@ -560,15 +553,8 @@ int launch_df64eo_prep(double *w, const double *u, const double *dx, const doubl
   auto kern = kind == 2   ? ax_df64eo_prep_kernel<LX, true, true>
               : kind == 1 ? ax_df64eo_prep_kernel<LX, true>
                           : ax_df64eo_prep_kernel<LX, false>;
-  static size_t granted[3] = {48 * 1024, 48 * 1024, 48 * 1024};
-  if (smem > granted[kind]) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-      (void)cudaGetLastError();
-      return AX_EINVAL;
-    }
-    granted[kind] = smem;
-  }
+  static std::atomic<size_t> granted[3][kMaxDevices];
+  if (!grant_smem(kern, smem, granted[kind])) return AX_EINVAL;
   const unsigned grid = (unsigned)((nelv + epb - 1) / epb);
   kern<<<grid, epb * H3, smem, stream>>>(w, u, dx, dxt, gp, nelv, epb, dotp, pw, r_in, minv_in,
                                          beta_p, corr_in, use_corr_p);

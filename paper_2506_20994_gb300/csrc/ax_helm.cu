@@ -18,7 +18,8 @@ int check_args(W *w, const S *u, const T *dx, const T *dxt, const S *h1, const S
 }
 
 // variant chosen for AX_VARIANT_AUTO per lx by the tuner; 0 = built-in
-int g_variant[AX_LX_MAX + 1];
+// (atomic: the tuner may run on one host thread while others launch)
+std::atomic<int> g_variant[AX_LX_MAX + 1];
 
 }  // namespace
 
@@ -48,7 +49,10 @@ int ax_helm_variant(int variant, double *w, const double *u, const double *dx,
   // measured on GB300 at E = 32768 / 13824 / 8000: the even-odd kernel wins
   // for lx 8, 10, 12; the k-loop double-float kernel below that; fp64 units
   // above the double-float instantiations
-  if (variant == AX_VARIANT_AUTO && g_variant[lx] != 0) variant = g_variant[lx];
+  if (variant == AX_VARIANT_AUTO) {
+    const int v = g_variant[lx].load(std::memory_order_relaxed);
+    if (v != 0) variant = v;
+  }
   if (variant == AX_VARIANT_AUTO)
     variant = (lx == 8 || lx == 10 || lx == 12) ? AX_VARIANT_F64_DF_EO
               : lx <= ax::AX_DF64_LX_MAX        ? AX_VARIANT_F64_DF
@@ -150,7 +154,7 @@ extern "C" int ax_tune_variant_run(int lx, int nelv, double *w, const double *u,
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (best == 0) return AX_ELAUNCH;
-  g_variant[lx] = best;
+  g_variant[lx].store(best, std::memory_order_relaxed);
   if (best_variant) *best_variant = best;
   if (best_ms) *best_ms = best_t;
   return AX_OK;
@@ -159,12 +163,12 @@ extern "C" int ax_tune_variant_run(int lx, int nelv, double *w, const double *u,
 extern "C" int ax_tune_variant_set(int lx, int variant) {
   if (!ax::lx_ok(lx) || variant < AX_VARIANT_AUTO || variant > AX_VARIANT_F64_DF_EO)
     return AX_EINVAL;
-  g_variant[lx] = variant;
+  g_variant[lx].store(variant, std::memory_order_relaxed);
   return AX_OK;
 }
 
 extern "C" int ax_tune_variant_get(int lx, int *variant) {
   if (!ax::lx_ok(lx) || !variant) return AX_EINVAL;
-  *variant = g_variant[lx];
+  *variant = g_variant[lx].load(std::memory_order_relaxed);
   return AX_OK;
 }

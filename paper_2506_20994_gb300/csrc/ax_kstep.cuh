@@ -306,15 +306,8 @@ int launch_kstep(W *w, const SU *u, const T *dx, const T *dxt, const S *h1, cons
   if (epb * LX * LX > 1024) return AX_EINVAL;
   const size_t smem = kstep_smem<LX, T, false, kstep_vec<LX, T>()>(epb);
   auto kern = dotp ? ax_kstep_kernel<LX, SU, S, T, W, true> : ax_kstep_kernel<LX, SU, S, T, W>;
-  static size_t granted[2] = {48 * 1024, 48 * 1024};  // per instantiation
-  if (smem > granted[dotp != nullptr]) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-      (void)cudaGetLastError();
-      return AX_EINVAL;
-    }
-    granted[dotp != nullptr] = smem;
-  }
+  static std::atomic<size_t> granted[2][kMaxDevices];  // per kernel
+  if (!grant_smem(kern, smem, granted[dotp != nullptr])) return AX_EINVAL;
   const unsigned grid = (unsigned)((nelv + epb - 1) / epb);
   kern<<<grid, epb * LX * LX, smem, stream>>>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23,
                                               nelv, epb, dotp);

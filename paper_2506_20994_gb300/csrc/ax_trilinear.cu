@@ -260,15 +260,8 @@ int launch_tri(float *w, const float *u, const float *dx, const float *dxt, cons
   const int epb = 256 / (LX * LX) < 1 ? 1 : 256 / (LX * LX);
   const size_t smem = tri_smem<LX>(epb);
   auto kern = h1 ? ax_tri_f32_kernel<LX, true> : ax_tri_f32_kernel<LX, false>;
-  static size_t granted[2] = {48 * 1024, 48 * 1024};
-  if (smem > granted[h1 != nullptr]) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-      (void)cudaGetLastError();
-      return AX_EINVAL;
-    }
-    granted[h1 != nullptr] = smem;
-  }
+  static std::atomic<size_t> granted[2][kMaxDevices];
+  if (!grant_smem(kern, smem, granted[h1 != nullptr])) return AX_EINVAL;
   const unsigned grid = (unsigned)((nelv + epb - 1) / epb);
   kern<<<grid, epb * LX * LX, smem, st>>>(w, u, dx, dxt, h1, corners, xi, wq, nelv, epb);
   return launch_status();

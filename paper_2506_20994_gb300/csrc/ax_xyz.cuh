@@ -56,15 +56,8 @@ int launch_xyz(AX_XYZ_PARAMS, cudaStream_t st) {
     smem = kstep_smem<LX, double, true>(epb);
     kern = ax_kstep_xyz_kernel<LX>;
   }
-  static size_t granted = 48 * 1024;
-  if (smem > granted) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-      (void)cudaGetLastError();
-      return AX_EINVAL;
-    }
-    granted = smem;
-  }
+  static std::atomic<size_t> granted[kMaxDevices];
+  if (!grant_smem(kern, smem, granted)) return AX_EINVAL;
   const unsigned grid = (unsigned)((nelv + epb - 1) / epb);
   kern<<<grid, epb * LX * LX, smem, st>>>(AX_XYZ_ARGS);
   return launch_status();

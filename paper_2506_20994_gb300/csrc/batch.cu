@@ -80,12 +80,12 @@ struct Group {
 }  // namespace
 
 // process-wide tuned elements-per-block table, [dtype][lx]; 0 = default
-static int g_tuned_epb[3][AX_LX_MAX + 1];
+static std::atomic<int> g_tuned_epb[3][AX_LX_MAX + 1];  // written by the tuner
 
 namespace ax {
 int tuned_epb(int dtype, int lx) {
   if (dtype < 1 || dtype > 2 || lx < 0 || lx > AX_LX_MAX) return 0;
-  return g_tuned_epb[dtype][lx];
+  return g_tuned_epb[dtype][lx].load(std::memory_order_relaxed);
 }
 }  // namespace ax
 
@@ -332,14 +332,14 @@ int ax_tune_set(int dtype, int lx, int elems_per_block) {
   if ((dtype != AX_BATCH_F64 && dtype != AX_BATCH_F32) || !ax::lx_ok(lx) ||
       elems_per_block < 0 || elems_per_block * lx * lx > 256)
     return AX_EINVAL;
-  g_tuned_epb[dtype][lx] = elems_per_block;
+  g_tuned_epb[dtype][lx].store(elems_per_block, std::memory_order_relaxed);
   return AX_OK;
 }
 
 int ax_tune_get(int dtype, int lx, int *elems_per_block) {
   if ((dtype != AX_BATCH_F64 && dtype != AX_BATCH_F32) || !ax::lx_ok(lx) || !elems_per_block)
     return AX_EINVAL;
-  *elems_per_block = g_tuned_epb[dtype][lx];
+  *elems_per_block = g_tuned_epb[dtype][lx].load(std::memory_order_relaxed);
   return AX_OK;
 }
 
@@ -389,7 +389,7 @@ int ax_tune_run(int dtype, int lx, int nelv, void *w, const void *u, const void 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (best == 0) return AX_ELAUNCH;
-  g_tuned_epb[dtype][lx] = best;
+  g_tuned_epb[dtype][lx].store(best, std::memory_order_relaxed);
   if (best_epb) *best_epb = best;
   if (best_ms) *best_ms = best_t;
   return AX_OK;

@@ -2,6 +2,9 @@
 // element-field loaders for each storage type, and launch bookkeeping.
 #pragma once
 
+#include <atomic>
+#include <mutex>
+
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -40,17 +43,34 @@ AX_D T ld_cvt(const float *p) { return (T)__ldg(p); }
 template <typename T>
 AX_D T ld_cvt(const __nv_bfloat16 *p) { return (T)__bfloat162float(__ldg(p)); }
 
-// Sets the dynamic shared-memory limit of a kernel once per process
-// (per kernel and per size class); returns false if the device refuses.
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device when that is above the 48 KB default and above what this kernel was
+// granted on this device before (the attribute is per device, so a process
+// driving several GPUs raises it on each).  `granted` is the caller's table
+// for one kernel, zero-initialised; raises are serialised so the recorded
+// size only grows.  False if the device refuses or its index is out of range.
+constexpr int kMaxDevices = 64;
+inline std::mutex &smem_grant_mutex() {
+  static std::mutex m;
+  return m;
+}
 template <typename K>
-inline bool ensure_smem(K kernel, size_t bytes) {
+inline bool grant_smem(K kernel, size_t bytes, std::atomic<size_t> (&granted)[kMaxDevices]) {
   if (bytes <= 48 * 1024) return true;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)bytes);
-  if (e != cudaSuccess) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     (void)cudaGetLastError();
     return false;
   }
+  if (bytes <= granted[dev].load(std::memory_order_acquire)) return true;
+  std::lock_guard<std::mutex> lock(smem_grant_mutex());
+  if (bytes <= granted[dev].load(std::memory_order_relaxed)) return true;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+      cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  granted[dev].store(bytes, std::memory_order_release);
   return true;
 }
 
