@@ -48,6 +48,7 @@ extern "C" {
 #define AX_ENOMEM (-4)     /* an allocation the call documents failed     */
 #define AX_ENOTCONV (-5)   /* a solver hit maxit before its tolerance     */
 #define AX_EBREAKDOWN (-6) /* a solver met p.Ap <= 0 or a non-finite value */
+#define AX_EIO (-7)        /* a file could not be opened, read or written  */
 
 #define AX_LX_MIN 2
 #define AX_LX_MAX 16
@@ -438,6 +439,18 @@ int ax_tune_variant_run(int lx, int nelv, double *w, const double *u, const doub
                         float *best_ms, void *stream);
 int ax_tune_variant_set(int lx, int variant);
 int ax_tune_variant_get(int lx, int *variant);
+
+/* The two tuning tables above as a text file (host only, no GPU needed):
+ * one line per recorded entry, "epb <dtype> <lx> <elems_per_block>" and
+ * "variant <lx> <variant>", '#' lines are comments; entries at 0 (built-in
+ * choice) are not written.  ax_tune_load reads the whole file, checks every
+ * entry against the rules of ax_tune_set / ax_tune_variant_set and only then
+ * applies them (tables not named in the file keep their values).  Errors:
+ * AX_EINVAL for a NULL path, an unknown line or an entry the setters would
+ * refuse (nothing applied); AX_EIO if the file cannot be opened, read or
+ * written. */
+int ax_tune_save(const char *path);
+int ax_tune_load(const char *path);
 
 /* y = a x + b y on device fp64 vectors of n values (asynchronous). */
 int ax_axpby(double *y, double a, const double *x, double b, int64_t n, void *stream);

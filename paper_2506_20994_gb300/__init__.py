@@ -10,6 +10,8 @@ in the library's kernels.  PyTorch supplies device memory and streams only.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 from . import _lib
@@ -26,7 +28,7 @@ __all__ = [
     "AX_PREC_F32", "AX_PREC_BF16", "Batch", "tune", "tune_set", "tune_get", "AX_BATCH_F64",
     "AX_BATCH_F32", "fourier_coefficient", "Mlp", "mlp_init_params", "training_pairs", "train_mlp", "axpby", "iterate_pairs",
     "train_energy", "AX_MLP_TANH", "AX_MLP_SYM", "Operator", "ax_helm_h2", "ax_helm_xyz", "ax_helm_trilinear_f32", "box_corners", "ax_helm_host", "tune_variant",
-    "tune_variant_set", "tune_variant_get",
+    "tune_variant_set", "tune_variant_get", "tune_save", "tune_load",
 ]
 
 
@@ -546,6 +548,18 @@ def tune_get(dtype: int, lx: int) -> int:
     e = ctypes.c_int()
     check("ax_tune_get", lib().ax_tune_get(dtype, lx, ctypes.addressof(e)))
     return e.value
+
+
+def tune_save(path: str) -> None:
+    """Writes the tuned elements-per-block and fp64-variant tables to a text
+    file (ax_tune_save)."""
+    check("ax_tune_save", lib().ax_tune_save(os.fsencode(path)))
+
+
+def tune_load(path: str) -> None:
+    """Reads tables written by tune_save and applies them, all or nothing
+    (ax_tune_load)."""
+    check("ax_tune_load", lib().ax_tune_load(os.fsencode(path)))
 
 
 def tune_variant(lx: int, fields: dict, reps: int = 5):

@@ -29,6 +29,8 @@ PROTOTYPES = {
     "ax_dmat": (c_int, [c_int, P, P]),
     "ax_box_geometry": (c_int, [c_int, c_int, c_int, c_int, P] + [P] * 8),
     "ax_box_corners": (c_int, [c_int, c_int, c_int, P, P]),
+    "ax_tune_save": (c_int, [ctypes.c_char_p]),
+    "ax_tune_load": (c_int, [ctypes.c_char_p]),
     "ax_box_numbering": (c_int, [c_int, c_int, c_int, c_int, P]),
     "ax_df64_roundtrip": (c_int, [P, P, P, P, c_int64]),
     "ax_gs_setup": (c_int, [P, P, c_int64, c_void_p]),
@@ -108,6 +110,7 @@ AX_ELAUNCH = -3
 AX_ENOMEM = -4
 AX_ENOTCONV = -5
 AX_EBREAKDOWN = -6
+AX_EIO = -7
 AX_VARIANT_AUTO = 0
 AX_VARIANT_F64_NATIVE = 1
 AX_VARIANT_F64_DF = 2

@@ -33,6 +33,7 @@ const char *ax_strerror(int code) {
     case AX_ENOMEM: return "allocation failed";
     case AX_ENOTCONV: return "solver did not converge within maxit";
     case AX_EBREAKDOWN: return "solver breakdown (p.Ap <= 0 or non-finite value)";
+    case AX_EIO: return "file could not be opened, read or written";
     default: return "unknown status";
   }
 }

@@ -14,6 +14,8 @@
 //     eight vertices; G = W * adj(J) adj(J)^T / det(J), the same matrix as
 //     det(J) W J^{-1} J^{-T}.
 #include <cmath>
+#include <cstdio>
+#include <cstring>
 #include <cstdint>
 #include <thread>
 #include <vector>
@@ -252,6 +254,71 @@ int ax_box_corners(int nx, int ny, int nz, const double *vertices, double *corne
           for (int d = 0; d < 3; ++d)
             corners[e * 24 + ((c * 2 + b) * 2 + a) * 3 + d] = vertices[v * 3 + d];
         }
+  }
+  return AX_OK;
+}
+
+int ax_tune_save(const char *path) {
+  if (!path) return AX_EINVAL;
+  FILE *f = std::fopen(path, "w");
+  if (!f) return AX_EIO;
+  bool ok = std::fprintf(f, "# axhelm tuning table: epb <dtype> <lx> <n> | variant <lx> <v>\n") > 0;
+  for (int dtype : {AX_BATCH_F64, AX_BATCH_F32})
+    for (int lx = AX_LX_MIN; lx <= AX_LX_MAX; ++lx) {
+      int v = 0;
+      if (ax_tune_get(dtype, lx, &v) == AX_OK && v > 0)
+        ok = ok && std::fprintf(f, "epb %d %d %d\n", dtype, lx, v) > 0;
+    }
+  for (int lx = AX_LX_MIN; lx <= AX_LX_MAX; ++lx) {
+    int v = 0;
+    if (ax_tune_variant_get(lx, &v) == AX_OK && v > 0)
+      ok = ok && std::fprintf(f, "variant %d %d\n", lx, v) > 0;
+  }
+  if (std::fclose(f) != 0) ok = false;
+  return ok ? AX_OK : AX_EIO;
+}
+
+int ax_tune_load(const char *path) {
+  if (!path) return AX_EINVAL;
+  FILE *f = std::fopen(path, "r");
+  if (!f) return AX_EIO;
+  struct Entry {
+    bool epb;
+    int a, b, c;
+  };
+  std::vector<Entry> entries;
+  char line[256];
+  bool bad = false;
+  while (!bad && std::fgets(line, sizeof line, f)) {
+    char kw[16] = {0};
+    if (std::sscanf(line, "%15s", kw) != 1 || kw[0] == '#') continue;  // blank or comment
+    int a = 0, b = 0, c = 0;
+    char extra[2];
+    if (!std::strcmp(kw, "epb") && std::sscanf(line, "epb %d %d %d %1s", &a, &b, &c, extra) == 3)
+      entries.push_back({true, a, b, c});
+    else if (!std::strcmp(kw, "variant") && std::sscanf(line, "variant %d %d %1s", &a, &b, extra) == 2)
+      entries.push_back({false, a, b, 0});
+    else
+      bad = true;
+  }
+  const bool read_error = std::ferror(f) != 0;
+  std::fclose(f);
+  if (read_error) return AX_EIO;
+  if (bad) return AX_EINVAL;
+  // the setters' rules, checked for every entry before any is applied
+  for (const Entry &e : entries) {
+    if (e.epb) {
+      if ((e.a != AX_BATCH_F64 && e.a != AX_BATCH_F32) || e.b < AX_LX_MIN || e.b > AX_LX_MAX ||
+          e.c < 0 || e.c * e.b * e.b > 256)
+        return AX_EINVAL;
+    } else if (e.a < AX_LX_MIN || e.a > AX_LX_MAX || e.b < AX_VARIANT_AUTO ||
+               e.b > AX_VARIANT_F64_DF_EO) {
+      return AX_EINVAL;
+    }
+  }
+  for (const Entry &e : entries) {
+    const int rc = e.epb ? ax_tune_set(e.a, e.b, e.c) : ax_tune_variant_set(e.a, e.b);
+    if (rc != AX_OK) return rc;
   }
   return AX_OK;
 }

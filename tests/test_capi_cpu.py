@@ -145,3 +145,43 @@ def test_argument_checks_need_no_gpu():
     assert lib.ax_box_corners(0, 1, 1, None, None) == _lib.AX_EINVAL
     assert lib.ax_gll(1, None, None) == _lib.AX_EINVAL
     assert lib.ax_dmat(17, None, None) == _lib.AX_EINVAL
+
+
+def test_tune_tables_save_and_load(tmp_path):
+    """The tuning tables round-trip through a text file; a bad file applies
+    nothing; a missing one is an I/O error."""
+    saved = {(d, lx): ax.tune_get(d, lx) for d in (ax.AX_BATCH_F64, ax.AX_BATCH_F32)
+             for lx in (5, 8)}
+    saved_v = {lx: ax.tune_variant_get(lx) for lx in (6, 8)}
+    try:
+        ax.tune_set(ax.AX_BATCH_F64, 8, 3)
+        ax.tune_set(ax.AX_BATCH_F32, 5, 7)
+        ax.tune_variant_set(8, ax.AX_VARIANT_F64_DF)
+        ax.tune_variant_set(6, ax.AX_VARIANT_F64_NATIVE)
+        path = tmp_path / "tune.txt"
+        ax.tune_save(str(path))
+        text = path.read_text()
+        assert "epb 1 8 3" in text and "epb 2 5 7" in text and "variant 8 2" in text
+        for d, lx in saved:
+            ax.tune_set(d, lx, 0)
+        ax.tune_variant_set(8, 0)
+        ax.tune_variant_set(6, 0)
+        ax.tune_load(str(path))
+        assert ax.tune_get(ax.AX_BATCH_F64, 8) == 3 and ax.tune_get(ax.AX_BATCH_F32, 5) == 7
+        assert ax.tune_variant_get(8) == ax.AX_VARIANT_F64_DF
+        assert ax.tune_variant_get(6) == ax.AX_VARIANT_F64_NATIVE
+        # a refused entry (9 x 8 x 8 > 256 threads) after a valid one: nothing applied
+        bad = tmp_path / "bad.txt"
+        bad.write_text("epb 1 8 1\nepb 1 8 9\n")
+        lib = _lib.lib()
+        assert lib.ax_tune_load(str(bad).encode()) == _lib.AX_EINVAL
+        assert ax.tune_get(ax.AX_BATCH_F64, 8) == 3
+        bad.write_text("bogus 1 2\n")
+        assert lib.ax_tune_load(str(bad).encode()) == _lib.AX_EINVAL
+        assert lib.ax_tune_load(str(tmp_path / "missing.txt").encode()) == _lib.AX_EIO
+        assert lib.ax_tune_load(None) == _lib.AX_EINVAL
+    finally:
+        for (d, lx), v in saved.items():
+            ax.tune_set(d, lx, v)
+        for lx, v in saved_v.items():
+            ax.tune_variant_set(lx, v)
