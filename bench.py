@@ -199,8 +199,10 @@ def time_region(fn, steps: int, warmup: int, stream, barrier=None):
     return e0.elapsed_time(e1), (t_wall0, t_wall1)
 
 
-def cpu_baseline(lx: int, n: int, target_s: float = 10.0):
-    """The oracle on a bounded sample (2048 elements) of the workload."""
+def cpu_baseline(lx: int, n: int, target_s: float = 10.0, single_s: float = 0.0):
+    """The oracle on a bounded sample (2048 elements) of the workload, with
+    all host threads; with single_s > 0 also one thread for about single_s
+    seconds."""
     import numpy as np
     import oracle
     from paper_2506_20994_gb300 import synth
@@ -214,19 +216,31 @@ def cpu_baseline(lx: int, n: int, target_s: float = 10.0):
     h1 = np.ones_like(u)
     dx, dxt = oracle.d_buffers(lx)
     G = [go[k] for k in GKEYS]
-    oracle.ax_helm(u, dx, dxt, h1, *G, lx)  # warm
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        oracle.ax_helm(u, dx, dxt, h1, *G, lx)
-        reps += 1
-        el = time.perf_counter() - t0
-        if el >= target_s or reps >= 10000:
-            break
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": reps * m * lx ** 3 / el / 1e9, "unit": "GDOF/s", "cores": threads,
-            "kind": "oracle",
-            "sample": f"{reps} applies of the oracle loop nest on {m} of the {nel} elements "
-                      f"(lx={lx}), {el:.1f} s"}
+    def timed(seconds):
+        oracle.ax_helm(u, dx, dxt, h1, *G, lx)  # warm
+        reps, t0 = 0, time.perf_counter()
+        while True:
+            oracle.ax_helm(u, dx, dxt, h1, *G, lx)
+            reps += 1
+            el = time.perf_counter() - t0
+            if el >= seconds or reps >= 10000:
+                return reps, el
+
+    threads = oracle.set_threads(0)
+    reps, el = timed(target_s)
+    out = {"value": reps * m * lx ** 3 / el / 1e9, "unit": "GDOF/s", "cores": threads,
+           "kind": "oracle",
+           "sample": f"{reps} applies of the oracle loop nest on {m} of the {nel} elements "
+                     f"(lx={lx}), {el:.1f} s, {threads} OpenMP threads"}
+    if single_s > 0:
+        oracle.set_threads(1)
+        try:
+            r1, e1 = timed(single_s)
+        finally:
+            oracle.set_threads(threads)
+        out["single_thread"] = {"value": r1 * m * lx ** 3 / e1 / 1e9, "unit": "GDOF/s",
+                                "sample": f"{r1} applies, 1 thread, {e1:.1f} s"}
+    return out
 
 
 def run_reference(args, rank):
@@ -358,7 +372,7 @@ def main():
     if extras:
         line["extras"] = extras
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(lx, n)
+        line["cpu_baseline"] = cpu_baseline(lx, n, single_s=5.0)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -77,8 +77,16 @@ def _load():
             lib.oracle_gs_sum.argtypes = [dp, ctypes.POINTER(ctypes.c_longlong),
                                           ctypes.c_longlong, ctypes.c_longlong]
             lib.oracle_gs_sum.restype = ctypes.c_int
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Sets the OpenMP threads of the C loops (n > 0) and returns the count
+    in effect; timing only, results are independent of it."""
+    return int(_load().oracle_set_threads(int(n)))
 
 
 def _dp(a: np.ndarray):

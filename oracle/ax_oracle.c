@@ -29,6 +29,22 @@
  */
 #include <stddef.h>
 #include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the element loop (timing only; results do not depend on it). */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0)
+        omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 static size_t at(int lx, size_t e, int k, int j, int i)
 {
