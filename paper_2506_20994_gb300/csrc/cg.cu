@@ -168,8 +168,10 @@ __global__ void cg_alpha_kernel(const double *__restrict__ partials, int nblk,
 
 // x += alpha p; r -= alpha w; partials rz' = sum cm r^2, rr' = sum c r^2
 // MASKW: w is not masked yet (fused apply); the Dirichlet rows, where
-// cm = c * minv is 0, keep r = 0.
-template <typename T, bool MASKW = false>
+// cm = c * minv is 0, keep r = 0.  RR: also the rr partials; rr only feeds
+// the host's convergence test, so iterations it does not check skip that sum
+// and the read of c (their rr partials are written as 0).
+template <typename T, bool MASKW = false, bool RR = true>
 __global__ void cg_update_kernel(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
                                  const T *__restrict__ w, const T *__restrict__ cm,
                                  const T *__restrict__ c, const CgScalars *__restrict__ s,
@@ -183,7 +185,7 @@ __global__ void cg_update_kernel(T *__restrict__ x, T *__restrict__ r, const T *
     rq = rv;
     const T r2 = rv * rv;
     a_rz += cmq * r2;
-    a_rr += cq * r2;
+    if constexpr (RR) a_rr += cq * r2;
   };
   int64_t q0 = 0;
   if constexpr (sizeof(T) == 4) {
@@ -194,7 +196,8 @@ __global__ void cg_update_kernel(T *__restrict__ x, T *__restrict__ r, const T *
            v += (int64_t)gridDim.x * blockDim.x) {
         V xv = reinterpret_cast<V *>(x)[v], rv = reinterpret_cast<V *>(r)[v];
         const V pv = reinterpret_cast<const V *>(p)[v], wv = reinterpret_cast<const V *>(w)[v];
-        const V mv = reinterpret_cast<const V *>(cm)[v], cv = reinterpret_cast<const V *>(c)[v];
+        const V mv = reinterpret_cast<const V *>(cm)[v];
+        const V cv = RR ? reinterpret_cast<const V *>(c)[v] : V{0.f, 0.f, 0.f, 0.f};
         point(xv.x, rv.x, pv.x, wv.x, mv.x, cv.x);
         point(xv.y, rv.y, pv.y, wv.y, mv.y, cv.y);
         point(xv.z, rv.z, pv.z, wv.z, mv.z, cv.z);
@@ -207,7 +210,7 @@ __global__ void cg_update_kernel(T *__restrict__ x, T *__restrict__ r, const T *
   }
   for (int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x)
-    point(x[q], r[q], p[q], w[q], cm[q], c[q]);
+    point(x[q], r[q], p[q], w[q], cm[q], RR ? c[q] : T(0));
   double v[2] = {(double)a_rz, (double)a_rr};
   ax::block_sum<2>(v, sh);
   if (threadIdx.x == 0) {
@@ -483,8 +486,14 @@ int pcg_loop(ax_poisson *P, T *x, const T *b, T *r, T *p, T *w, const T *mask, c
                                : apply_fused(P, w, p, st);
       if (rc) return rc;
       cg_alpha_kernel<<<1, 1024, 0, st>>>(P->dotp, nparts, P->scal);
-      cg_update_kernel<T, true><<<nb, kRedThreads, 0, st>>>(x, r, p, w, cm, c, P->scal,
-                                                            P->partials, n);
+      // rr only where the host will test it (after this iteration)
+      const bool checked = (it + 1) % P->check_every == 0 || it + 1 == maxit;
+      if (checked)
+        cg_update_kernel<T, true, true><<<nb, kRedThreads, 0, st>>>(x, r, p, w, cm, c, P->scal,
+                                                                    P->partials, n);
+      else
+        cg_update_kernel<T, true, false><<<nb, kRedThreads, 0, st>>>(x, r, p, w, cm, c,
+                                                                     P->scal, P->partials, n);
     } else {
       rc = apply(w, p, st);
       if (rc) return rc;
@@ -890,7 +899,9 @@ namespace {
 
 // x += alpha p; r_old = r; r -= alpha w; partial rr = sum c r^2.  MASKW: w is
 // not masked yet (fused apply); rows where cm = c * minv is 0 keep r = 0.
-template <typename T, bool MASKW = false>
+// RR: the rr partials (read by the host's convergence test only); without
+// it the kernel neither reads c nor reduces.
+template <typename T, bool MASKW = false, bool RR = true>
 __global__ void fcg_update_kernel(T *__restrict__ x, T *__restrict__ r, T *__restrict__ r_old,
                                   const T *__restrict__ p, const T *__restrict__ w,
                                   const T *__restrict__ c, const T *__restrict__ cm,
@@ -903,7 +914,7 @@ __global__ void fcg_update_kernel(T *__restrict__ x, T *__restrict__ r, T *__res
     xq += alpha * pq;
     roq = rq;
     rq = (MASKW && cmq == T(0)) ? rq : rq - alpha * wq;
-    a_rr += cq * rq * rq;
+    if constexpr (RR) a_rr += cq * rq * rq;
   };
   int64_t q0 = 0;
   if constexpr (sizeof(T) == 4) {
@@ -914,7 +925,7 @@ __global__ void fcg_update_kernel(T *__restrict__ x, T *__restrict__ r, T *__res
            v += (int64_t)gridDim.x * blockDim.x) {
         V xv = reinterpret_cast<V *>(x)[v], rv = reinterpret_cast<V *>(r)[v], ov;
         const V pv = reinterpret_cast<const V *>(p)[v], wv = reinterpret_cast<const V *>(w)[v];
-        const V cv = reinterpret_cast<const V *>(c)[v];
+        const V cv = RR ? reinterpret_cast<const V *>(c)[v] : V{0.f, 0.f, 0.f, 0.f};
         const V mv = MASKW ? reinterpret_cast<const V *>(cm)[v] : V{1.f, 1.f, 1.f, 1.f};
         point(xv.x, rv.x, ov.x, pv.x, wv.x, cv.x, mv.x);
         point(xv.y, rv.y, ov.y, pv.y, wv.y, cv.y, mv.y);
@@ -929,10 +940,12 @@ __global__ void fcg_update_kernel(T *__restrict__ x, T *__restrict__ r, T *__res
   }
   for (int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x)
-    point(x[q], r[q], r_old[q], p[q], w[q], c[q], MASKW ? cm[q] : T(1));
-  double v[1] = {(double)a_rr};
-  ax::block_sum<1>(v, sh);
-  if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+    point(x[q], r[q], r_old[q], p[q], w[q], RR ? c[q] : T(0), MASKW ? cm[q] : T(1));
+  if constexpr (RR) {
+    double v[1] = {(double)a_rr};
+    ax::block_sum<1>(v, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+  }
 }
 
 // partials of <zj, r>, <corr, r>, <zj, r_old>, <corr, r_old> (zj = minv r),
@@ -1128,6 +1141,7 @@ int fcg_loop(ax_poisson *P, const ax_mlp *M, T *x, const T *b, T *r, T *r_old, T
   const bool fused = nparts > 0;
   int applied = 0;  // applies so far: the first uses the p formed above
   while (status != AX_OK && it < maxit) {
+    const bool checked = (it + 1) % P->check_every == 0 || it + 1 == maxit;
     if (fused) {
       rc = (fused_p && applied > 0)
                ? apply_fused_update(P, w, p, r, minv, beta_dev, st, corr, use_corr_dev)
@@ -1135,8 +1149,13 @@ int fcg_loop(ax_poisson *P, const ax_mlp *M, T *x, const T *b, T *r, T *r_old, T
       ++applied;
       if (rc) return rc;
       cg_alpha_kernel<<<1, 1024, 0, st>>>(P->dotp, nparts, P->scal);
-      fcg_update_kernel<T, true><<<nb, kRedThreads, 0, st>>>(x, r, r_old, p, w, c, cm, P->scal,
-                                                             P->partials, n);
+      // rr only where the host will test it (after this iteration)
+      if (checked)
+        fcg_update_kernel<T, true, true><<<nb, kRedThreads, 0, st>>>(x, r, r_old, p, w, c, cm,
+                                                                     P->scal, P->partials, n);
+      else
+        fcg_update_kernel<T, true, false><<<nb, kRedThreads, 0, st>>>(x, r, r_old, p, w, c, cm,
+                                                                      P->scal, P->partials, n);
     } else {
       if ((rc = apply(w, p, st))) return rc;
       mask_dot_kernel<T><<<nb, kRedThreads, 0, st>>>(w, p, mask, c, P->partials, n);
@@ -1144,7 +1163,7 @@ int fcg_loop(ax_poisson *P, const ax_mlp *M, T *x, const T *b, T *r, T *r_old, T
       fcg_update_kernel<T><<<nb, kRedThreads, 0, st>>>(x, r, r_old, p, w, c, cm, P->scal,
                                                        P->partials, n);
     }
-    fcg_rr_kernel<<<1, 32, 0, st>>>(P->partials, nb, P->scal, 0);
+    if (checked || !fused) fcg_rr_kernel<<<1, 32, 0, st>>>(P->partials, nb, P->scal, 0);
     ++it;
     if (it % P->check_every == 0 || it == maxit) {
       if ((rc = read_scalars())) return rc;
