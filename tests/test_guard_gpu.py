@@ -1,5 +1,5 @@
-"""Out-of-bounds write check for every operator entry point (the GPU pool
-has no compute-sanitizer): each output is a slice of a larger buffer whose
+"""Out-of-bounds write check for every operator entry point, in place of a
+memory sanitizer: each output is a slice of a larger buffer whose
 guard bands before and after hold a canary value; after the call the bands
 must be untouched and every output value written (the slice starts as NaN).
 Sizes are ragged against the kernels' elements per block.
