@@ -205,11 +205,13 @@ def test_f64_even_odd_adversarial():
     assert np.all(w[::4] == 0.0)
 
 
-@pytest.mark.parametrize("chunk", [0, 100, 567])
+@pytest.mark.parametrize("chunk", [0, 1, 100, 567, 100000])
 def test_host_buffers_streamed_in_chunks(chunk):
     """ax_helm_host on host tensors (pinned and pageable), chunks with a
-    ragged tail, against the oracle and bit for bit against ax_helm on the
-    device (the same kernel runs on every chunk)."""
+    ragged tail (one element per chunk cycles both device buffer sets 567
+    times; a chunk above the element count is clamped), against the oracle
+    and bit for bit against ax_helm on the device (the same kernel runs on
+    every chunk)."""
     lx = 8
     case = operator_case((9, 9, 7), lx, seed=90)
     keys = ("u", "dx", "dxt", "h1") + GKEYS
