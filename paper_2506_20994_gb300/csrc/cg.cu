@@ -207,6 +207,23 @@ __global__ void cg_update_kernel(T *__restrict__ x, T *__restrict__ r, const T *
       }
       q0 = n4 * 4;
     }
+  } else {
+    if (aligned16(x, r, p, w, cm, c)) {  // fp64: 16-byte accesses, two points each
+      using V = double2;
+      const int64_t n2 = n / 2;
+      for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n2;
+           v += (int64_t)gridDim.x * blockDim.x) {
+        V xv = reinterpret_cast<V *>(x)[v], rv = reinterpret_cast<V *>(r)[v];
+        const V pv = reinterpret_cast<const V *>(p)[v], wv = reinterpret_cast<const V *>(w)[v];
+        const V mv = reinterpret_cast<const V *>(cm)[v];
+        const V cv = RR ? reinterpret_cast<const V *>(c)[v] : V{0.0, 0.0};
+        point(xv.x, rv.x, pv.x, wv.x, mv.x, cv.x);
+        point(xv.y, rv.y, pv.y, wv.y, mv.y, cv.y);
+        reinterpret_cast<V *>(x)[v] = xv;
+        reinterpret_cast<V *>(r)[v] = rv;
+      }
+      q0 = n2 * 2;
+    }
   }
   for (int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x)
@@ -936,6 +953,24 @@ __global__ void fcg_update_kernel(T *__restrict__ x, T *__restrict__ r, T *__res
         reinterpret_cast<V *>(r_old)[v] = ov;
       }
       q0 = n4 * 4;
+    }
+  } else {
+    if (aligned16(x, r, r_old, p, w, c, cm)) {  // fp64: 16-byte accesses, two points each
+      using V = double2;
+      const int64_t n2 = n / 2;
+      for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n2;
+           v += (int64_t)gridDim.x * blockDim.x) {
+        V xv = reinterpret_cast<V *>(x)[v], rv = reinterpret_cast<V *>(r)[v], ov;
+        const V pv = reinterpret_cast<const V *>(p)[v], wv = reinterpret_cast<const V *>(w)[v];
+        const V cv = RR ? reinterpret_cast<const V *>(c)[v] : V{0.0, 0.0};
+        const V mv = MASKW ? reinterpret_cast<const V *>(cm)[v] : V{1.0, 1.0};
+        point(xv.x, rv.x, ov.x, pv.x, wv.x, cv.x, mv.x);
+        point(xv.y, rv.y, ov.y, pv.y, wv.y, cv.y, mv.y);
+        reinterpret_cast<V *>(x)[v] = xv;
+        reinterpret_cast<V *>(r)[v] = rv;
+        reinterpret_cast<V *>(r_old)[v] = ov;
+      }
+      q0 = n2 * 2;
     }
   }
   for (int64_t q = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
