@@ -80,7 +80,7 @@ def _rank_main(rank, world, port, dims, lx, outdir):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world,dims,lx", [(2, (2, 2, 4), 4), (3, (2, 3, 3), 3)])
+@pytest.mark.parametrize("world,dims,lx", [(2, (2, 2, 4), 4), (3, (2, 3, 3), 3), (4, (2, 2, 4), 3)])
 def test_partitioned_pcg_matches_single_domain(world, dims, lx, tmp_path):
     mp.spawn(_rank_main, args=(world, _free_port(), dims, lx, str(tmp_path)), nprocs=world,
              join=True)
