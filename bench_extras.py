@@ -147,6 +147,21 @@ def sweep(ax, synth, dev, hbm_peak):
                                          nel * (lx - 1) ** 3 / (ms * 1e-3) / 1e9, 2),
                                      "raw_geometry_ms": round(ms_raw, 4)}
             del d, w, op
+    # high order: the double-float k-loop kernel (ax_helm's choice) against the
+    # fp64 units, E = 4096
+    for lx in (14, 16):
+        d, nel = _mesh_tensors(ax, synth, 16, lx, dev)
+        w = torch.empty_like(d["u"])
+        G = [d[k] for k in GKEYS]
+        args = (w, d["u"], d["dx"], d["dxt"], d["h1"], *G, lx)
+        ms = _events_ms(lambda: ax.ax_helm(*args), 5)
+        ms_native = _events_ms(lambda: ax.ax_helm(*args, variant=ax.AX_VARIANT_F64_NATIVE), 5)
+        npts = nel * lx ** 3
+        out[f"E{nel}_lx{lx}"] = {"gdofs": round(npts / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 4),
+                                 "hbm_frac": round(72.0 * npts / (ms * 1e-3) / 1e9 / hbm_peak, 4),
+                                 "kernel": "double-float k-loop",
+                                 "fp64_units_ms": round(ms_native, 4)}
+        del d, w
     return out
 
 

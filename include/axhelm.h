@@ -81,7 +81,9 @@ int ax_helm(double *w, const double *u, const double *dx, const double *dxt,
             const double *g33, const double *g12, const double *g13,
             const double *g23, int lx, int nelv, void *stream);
 
-/* Explicit fp64 variants (same arguments and errors as ax_helm). */
+/* Explicit fp64 variants (same arguments and errors as ax_helm).  AUTO:
+ * the even-odd kernel for lx 8, 10, 12, the double-float k-loop kernel for
+ * every other lx, unless ax_tune_variant_run / _set recorded another. */
 #define AX_VARIANT_AUTO 0
 #define AX_VARIANT_F64_NATIVE 1 /* fp64 FMA units                           */
 #define AX_VARIANT_F64_DF 2     /* pairs of fp32 (double-float) arithmetic   */
@@ -426,8 +428,8 @@ int ax_tune_get(int dtype, int lx, int *elems_per_block);
 
 /* Variant selection for AX_VARIANT_AUTO, process-wide (Neko times its
  * kernel variants at run time and keeps the fastest, Sec. "Methodology").
- * ax_tune_variant_run times AX_VARIANT_F64_NATIVE, AX_VARIANT_F64_DF (lx <=
- * 12) and AX_VARIANT_F64_DF_EO (even lx in 4..12) with default elements per
+ * ax_tune_variant_run times AX_VARIANT_F64_NATIVE, AX_VARIANT_F64_DF (every
+ * lx) and AX_VARIANT_F64_DF_EO (even lx in 4..12) with default elements per
  * block on the caller's fp64 buffers (w is overwritten; reps timed launches
  * each, after one warm-up), records the fastest for lx and returns it.
  * ax_tune_variant_set / _get write and read the table (0 = the built-in

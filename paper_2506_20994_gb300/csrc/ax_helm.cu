@@ -48,8 +48,8 @@ int ax_helm_variant(int variant, double *w, const double *u, const double *dx,
   if (rc != AX_OK) return rc > 0 ? AX_OK : rc;
   cudaStream_t st = (cudaStream_t)stream;
   // measured on GB300 at E = 32768 / 13824 / 8000: the even-odd kernel wins
-  // for lx 8, 10, 12; the k-loop double-float kernel below that; fp64 units
-  // above the double-float instantiations
+  // for lx 8, 10, 12; the k-loop double-float kernel for the other lx (13-16
+  // included: the fp64 units run only on request)
   if (variant == AX_VARIANT_AUTO) {
     const int v = g_variant[lx].load(std::memory_order_relaxed);
     if (v != 0) variant = v;

@@ -42,10 +42,11 @@ __global__ void __launch_bounds__(256) ax_kstep_xyz_kernel(AX_XYZ_PARAMS) {
 }
 
 // about 256 threads per block, whole elements (lx*lx threads each)
-// (double-float kernel for lx <= AX_DF64_LX_MAX, fp64 units above)
+// (double-float kernel for lx <= 12, fp64 units above: the six-matrix form
+// is not a benchmark path, and this keeps its instantiations quick to build)
 template <int LX>
 int launch_xyz(AX_XYZ_PARAMS, cudaStream_t st) {
-  constexpr bool DF = LX <= AX_DF64_LX_MAX;
+  constexpr bool DF = LX <= 12;
   epb = 256 / (LX * LX) < 1 ? 1 : 256 / (LX * LX);
   size_t smem;
   void (*kern)(AX_XYZ_PARAMS);

@@ -12,8 +12,8 @@ namespace ax {
 // Tuned elements per block for (AX_BATCH_F64 | AX_BATCH_F32, lx); 0 if untuned.
 int tuned_epb(int dtype, int lx);
 
-// Largest lx with a double-float instantiation.
-constexpr int AX_DF64_LX_MAX = 12;
+// Largest lx with a double-float instantiation (every lx the library takes).
+constexpr int AX_DF64_LX_MAX = 16;
 
 // k-loop kernel: fp64 storage and fp64 units.
 int dispatch_kstep_f64(int lx, double *w, const double *u, const double *dx, const double *dxt,
@@ -71,8 +71,8 @@ int dispatch_eo_prepare(int lx, df::dd2 *gp, const double *h1, const double *g11
                         const double *g13, const double *g23, int nelv, int fmask,
                         cudaStream_t st);
 
-// fp64-accurate double-float kernel, lx in 2..7 (a), 8..10 (b), 11..12 (c);
-// AX_EINVAL above AX_DF64_LX_MAX.
+// fp64-accurate double-float kernel, lx in 2..7 (a), 8..10 (b), 11..12 (c),
+// 13..14 (d), 15..16 (e); AX_EINVAL above AX_DF64_LX_MAX.
 #define AX_DF64_DECL(X)                                                                        \
   int dispatch_df64_##X(int lx, double *w, const double *u, const double *dx,                  \
                         const double *dxt, const double *h1, const double *g11,                \
@@ -82,6 +82,8 @@ int dispatch_eo_prepare(int lx, df::dd2 *gp, const double *h1, const double *g11
 AX_DF64_DECL(a)
 AX_DF64_DECL(b)
 AX_DF64_DECL(c)
+AX_DF64_DECL(d)
+AX_DF64_DECL(e)
 #undef AX_DF64_DECL
 
 inline int dispatch_df64(int lx, double *w, const double *u, const double *dx, const double *dxt,
@@ -89,7 +91,11 @@ inline int dispatch_df64(int lx, double *w, const double *u, const double *dx, c
                   const double *g12, const double *g13, const double *g23, int nelv, int epb,
                   cudaStream_t st) {
   if (lx > AX_DF64_LX_MAX) return AX_EINVAL;
-  auto f = lx <= 7 ? dispatch_df64_a : (lx <= 10 ? dispatch_df64_b : dispatch_df64_c);
+  auto f = lx <= 7    ? dispatch_df64_a
+           : lx <= 10 ? dispatch_df64_b
+           : lx <= 12 ? dispatch_df64_c
+           : lx <= 14 ? dispatch_df64_d
+                      : dispatch_df64_e;
   return f(lx, w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nelv, epb, st);
 }
 

@@ -61,8 +61,18 @@ def test_f64_native_parity(lx):
     assert rel_l2(w, case["w"]) <= TOL["f64"]
 
 
+@pytest.mark.parametrize("lx", [13, 14, 15, 16])
+@pytest.mark.parametrize("dims", [(7, 1, 1), (3, 2, 2)], ids=["E7", "E12"])
+def test_f64_df_parity_high_order(lx, dims):
+    """The double-float k-loop kernel at lx 13-16 (one element, lx^2 threads,
+    per block; ragged against nothing but the element count)."""
+    case = operator_case(dims, lx, seed=50 + lx)
+    w = _run_f64(case, ax.AX_VARIANT_F64_DF)
+    assert rel_l2(w, case["w"]) <= TOL["f64"]
+
+
 @pytest.mark.parametrize("lx", [13, 16])
-def test_auto_variant_above_df_range(lx):
+def test_auto_variant_high_order(lx):
     case = operator_case((2, 1, 1), lx, seed=7)
     w = _run_f64(case, ax.AX_VARIANT_AUTO)
     assert rel_l2(w, case["w"]) <= TOL["f64"]
