@@ -16,6 +16,8 @@ CUDA events (kernels) or wall time around a synchronising solve (solvers):
            symmetric linear form (trained here by the library's kernels on
            residual/error pairs of 20 plain-CG iterates on an 8^3 mesh: 10,240
            element pairs), in fp64 and inside mixed refinement
+  rates    multiply-add throughput per SM and clock (fp64, fp32, packed
+           f32x2), the rates that decide the fp64 design
   batch    64 meshes, E log-uniform in [64, 8192], lx in {5, 6, 8, 10}: one
            persistent launch (and its CUDA-graph replay) against one launch
            per mesh, fp64 and fp32
@@ -282,6 +284,20 @@ def batch(ax, synth, dev, hbm_peak):
     return out
 
 
+def rates(ax):
+    """Multiply-add throughput per SM and clock (fp64, fp32, packed f32x2)
+    and what the fp64 one implies for an fp64-unit operator at lx = 8."""
+    import torch
+    r = ax.probe_rates()
+    props = torch.cuda.get_device_properties(0)
+    r["sms"] = props.multi_processor_count
+    # Listing 2's flops per fp64 byte at lx = 8: (12 lx^4 + 18 lx^3) / (72 lx^3)
+    intensity = (12 * 8 ** 4 + 18 * 8 ** 3) / (72 * 8 ** 3)
+    r["fp64_ratio_to_fp32"] = round(r["fp64_fma"] / r["fp32_fma"], 4)
+    r["lx8_fp64_flop_per_byte"] = round(intensity, 3)
+    return r
+
+
 def run_extras(ax, host, d, lx, nel, stream, hbm_peak, which):
     from paper_2506_20994_gb300 import synth
     dev = d["u"].device
@@ -293,6 +309,7 @@ def run_extras(ax, host, d, lx, nel, stream, hbm_peak, which):
         "cg_sweep": lambda: cg_sweep(ax, synth, synth.poisson_source, dev),
         "learned": lambda: learned(ax, synth, synth.poisson_source, dev),
         "batch": lambda: batch(ax, synth, dev, hbm_peak),
+        "rates": lambda: rates(ax),
     }
     for name, fn in sections.items():
         if name not in which:
