@@ -185,3 +185,37 @@ def test_tune_tables_save_and_load(tmp_path):
             ax.tune_set(d, lx, v)
         for lx, v in saved_v.items():
             ax.tune_variant_set(lx, v)
+
+
+def test_header_is_a_c_abi(tmp_path):
+    """The boundary is plain C: a C99 program includes the header, links the
+    library and calls host entry points (GLL nodes for lx = 3 are -1, 0, 1
+    with weights 1/3, 4/3, 1/3)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    _lib.lib()  # builds the library if needed
+    lib_dir = os.path.dirname(_lib.LIB_PATH)
+    src = tmp_path / "abi.c"
+    src.write_text(
+        '#include <math.h>\n#include <stdio.h>\n#include "axhelm.h"\n'
+        "int main(void) {\n"
+        "  double x[3], w[3];\n"
+        "  if (ax_gll(3, x, w) != AX_OK) return 2;\n"
+        "  if (fabs(x[0] + 1) > 1e-15 || fabs(x[1]) > 1e-15 || fabs(x[2] - 1) > 1e-15) return 3;\n"
+        "  if (fabs(w[0] - 1.0 / 3) > 1e-15 || fabs(w[1] - 4.0 / 3) > 1e-15) return 4;\n"
+        "  if (ax_helm(0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 8, 5, 0) != AX_EINVAL) return 5;\n"
+        '  printf("%s\\n", ax_version());\n'
+        "  return 0;\n}\n")
+    exe = tmp_path / "abi"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(root, "include"),
+                        str(src), "-L", lib_dir, "-laxhelm", "-lm", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    env = dict(os.environ, LD_LIBRARY_PATH=lib_dir + os.pathsep + os.environ.get("LD_LIBRARY_PATH", ""))
+    run = subprocess.run([str(exe)], capture_output=True, text=True, env=env, timeout=60)
+    assert run.returncode == 0, (run.returncode, run.stderr)
+    assert "axhelm" in run.stdout
