@@ -37,3 +37,24 @@ def test_shared_input_module_holds_no_binding():
     names = _imports(os.path.join(ROOT, "paper_2506_20994_gb300", "synth.py"))
     assert not any("oracle" in n or "_lib" in n or "ctypes" in n or "torch" in n
                    for n in names), names
+
+
+def test_missing_library_fails_loudly():
+    """No fallback: without libaxhelm.so every device entry point raises
+    (checked in a child interpreter with the library path pointed away)."""
+    import subprocess
+    import sys
+    code = (
+        "import paper_2506_20994_gb300 as ax\n"
+        "from paper_2506_20994_gb300 import _lib\n"
+        "_lib._lib = None\n"
+        "_lib.LIB_PATH = '/nonexistent/libaxhelm.so'\n"
+        "try:\n"
+        "    _lib.lib()\n"
+        "except RuntimeError as e:\n"
+        "    print('raised:', e)\n"
+        "else:\n"
+        "    raise SystemExit(3)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0 and "raised:" in r.stdout, (r.returncode, r.stdout, r.stderr)
