@@ -75,15 +75,28 @@ const char *ax_version(void);
 
 /* fp64 in, fp64 out, fp64-accurate (relative L2 error against exact fp64
  * arithmetic below 1e-12).  Dispatches to the fastest fp64-accurate variant
- * for lx (see ax_helm_variant). */
+ * for lx (see ax_helm_variant).
+ * Range: any fp64 input and any dx, dxt.  The double-float variants carry
+ * each value as two fp32 numbers; per element they record the largest
+ * exponent of u, of G and of h1, and an element whose product chain
+ * D, u, G, h1 leaves the fp32 exponent window with room for the tails (for
+ * example |u| beyond ~1e27 or below ~1e-23 with O(1) geometry, or any Inf or
+ * NaN) is recomputed with fp64 units, with IEEE fp64 semantics (Inf and NaN
+ * propagate as in the loop nest of Listing 2).  The even-odd variant reads
+ * only half the rows of dx and dxt, which is exact for centro-antisymmetric
+ * matrices (D[N-i][N-l] = -D[i][l], as the GLL matrix is); it checks that
+ * property to 2^-46 of the largest entry on every launch, and when it does
+ * not hold every element runs on fp64 units (correct, several times slower).
+ * fp64 values below 2^-1022 (subnormals) may be flushed to zero. */
 int ax_helm(double *w, const double *u, const double *dx, const double *dxt,
             const double *h1, const double *g11, const double *g22,
             const double *g33, const double *g12, const double *g13,
             const double *g23, int lx, int nelv, void *stream);
 
-/* Explicit fp64 variants (same arguments and errors as ax_helm).  AUTO:
- * the even-odd kernel for lx 8, 10, 12, the double-float k-loop kernel for
- * every other lx, unless ax_tune_variant_run / _set recorded another. */
+/* Explicit fp64 variants (same arguments, errors and range as ax_helm).
+ * AUTO: the even-odd kernel for lx 8, 10, 12, the double-float k-loop
+ * kernel for every other lx, unless ax_tune_variant_run / _set recorded
+ * another. */
 #define AX_VARIANT_AUTO 0
 #define AX_VARIANT_F64_NATIVE 1 /* fp64 FMA units                           */
 #define AX_VARIANT_F64_DF 2     /* pairs of fp32 (double-float) arithmetic   */
@@ -183,12 +196,15 @@ typedef struct ax_op ax_op;
 /* Creates the handle.  dx, dxt, h1 and G are borrowed device arrays in
  * ax_helm's conventions and must outlive the handle.  For lx in {6, 8, 10,
  * 12} the handle also converts the geometry once into the even-odd
- * kernel's prepared order (device memory of 56 lx^3 bytes per element,
- * owned; the same 8 bytes per value, split into double-float pairs exactly
- * as the on-the-fly kernel splits them; results agree with
- * AX_VARIANT_F64_DF_EO to ~1e-16 relative, the pointwise step running two
- * points per packed instruction).  Synchronises stream.  Returns
- * AX_EINVAL on bad arguments, AX_ENOMEM when the copy cannot be allocated. */
+ * kernel's prepared order (device memory of 56 lx^3 + 8 bytes per element,
+ * owned: the same 8 bytes per value, split into double-float pairs exactly
+ * as the on-the-fly kernel splits them, plus two exponent records per
+ * element; results agree with AX_VARIANT_F64_DF_EO to ~1e-16 relative, the
+ * pointwise step running two points per packed instruction).  Range as
+ * ax_helm: elements outside the double-float window, and all elements when
+ * dx or dxt is not centro-antisymmetric, are computed from the borrowed
+ * fp64 arrays with fp64 units.  Synchronises stream.  Returns AX_EINVAL on
+ * bad arguments, AX_ENOMEM when the copy cannot be allocated. */
 int ax_op_create(ax_op **op, int lx, int nelv, const double *dx, const double *dxt,
                  const double *h1, const double *g11, const double *g22, const double *g33,
                  const double *g12, const double *g13, const double *g23, void *stream);

@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "df64.cuh"
+#include "guard.cuh"
 
 namespace ax {
 
@@ -69,14 +70,27 @@ __device__ __forceinline__ void df64_body(double *__restrict__ w, const double *
   df2 *swr = su + N3;
   df2 *sws = swr + N3;
 
+  // range record of this block (guard.cuh)
+  __shared__ guard::Record rec;
+  guard::clear(rec, epb);
+  __syncthreads();
+
   for (int t = threadIdx.x; t < N2; t += blockDim.x) {
-    sdx[t] = split(__ldg(dx + t));
-    sdxt[t] = split(__ldg(dxt + t));
+    const double a = __ldg(dx + t), at = __ldg(dxt + t);
+    guard::note_d(rec, a);
+    guard::note_d(rec, at);
+    sdx[t] = split(a);
+    sdxt[t] = split(at);
     if constexpr (XYZ) {
-      sdy[t] = split(__ldg(dy + t));
-      sdz[t] = split(__ldg(dz + t));
-      sdyt[t] = split(__ldg(dyt + t));
-      sdzt[t] = split(__ldg(dzt + t));
+      const double b = __ldg(dy + t), c = __ldg(dz + t), bt = __ldg(dyt + t), ct = __ldg(dzt + t);
+      guard::note_d(rec, b);
+      guard::note_d(rec, c);
+      guard::note_d(rec, bt);
+      guard::note_d(rec, ct);
+      sdy[t] = split(b);
+      sdz[t] = split(c);
+      sdyt[t] = split(bt);
+      sdzt[t] = split(ct);
     }
   }
   const bool active = own && le < nel;
@@ -89,12 +103,16 @@ __device__ __forceinline__ void df64_body(double *__restrict__ w, const double *
   }
 
   df2 uk[LX];
+  unsigned ukey = 0u, gkey = 0u, hkey = 0u;  // exponent keys of u, G, h1
   if (own) {
 #pragma unroll
     for (int k = 0; k < LX; ++k) {
-      uk[k] = active ? split(__ldg(u + base + (size_t)k * N2)) : df2{0.f, 0.f};
+      const double x = active ? __ldg(u + base + (size_t)k * N2) : 0.0;
+      ukey = max(ukey, guard::key(x));
+      uk[k] = split(x);
       su[k * N2 + p] = uk[k];
     }
+    if (active) atomicMax(&rec.ex[le][0], ukey);
   }
   __syncthreads();
 
@@ -115,10 +133,17 @@ __device__ __forceinline__ void df64_body(double *__restrict__ w, const double *
       df2 wr{0.f, 0.f}, ws{0.f, 0.f}, wt{0.f, 0.f};
       if (active) {
         const size_t q = base + (size_t)k * N2;
-        const df2 a11 = split(__ldg(g11 + q)), a22 = split(__ldg(g22 + q));
-        const df2 a33 = split(__ldg(g33 + q)), a12 = split(__ldg(g12 + q));
-        const df2 a13 = split(__ldg(g13 + q)), a23 = split(__ldg(g23 + q));
-        const df2 hh = split(__ldg(h1 + q));
+        const double v11 = __ldg(g11 + q), v22 = __ldg(g22 + q), v33 = __ldg(g33 + q);
+        const double v12 = __ldg(g12 + q), v13 = __ldg(g13 + q), v23 = __ldg(g23 + q);
+        const double vh = __ldg(h1 + q);
+        gkey = max(gkey, max(max(guard::key(v11), guard::key(v22)),
+                             max(max(guard::key(v33), guard::key(v12)),
+                                 max(guard::key(v13), guard::key(v23)))));
+        hkey = max(hkey, guard::key(vh));
+        const df2 a11 = split(v11), a22 = split(v22);
+        const df2 a33 = split(v33), a12 = split(v12);
+        const df2 a13 = split(v13), a23 = split(v23);
+        const df2 hh = split(vh);
         acc a = prod(a11, ur);
         mac(a, a12, us);
         mac(a, a13, ut);
@@ -142,9 +167,15 @@ __device__ __forceinline__ void df64_body(double *__restrict__ w, const double *
           mac(wacc[kk], sdzt[k * LX + kk], wt);
       }
     }
+    if (active) {
+      atomicMax(&rec.ex[le][1], gkey);
+      atomicMax(&rec.ex[le][2], hkey);
+    }
   }
   __syncthreads();
 
+  // an element outside the double-float range is recomputed with fp64 units
+  const bool bad = active && !guard::elem_ok(rec, le);
   if (own) {
 #pragma unroll
     for (int k = 0; k < LX; ++k) {
@@ -155,8 +186,16 @@ __device__ __forceinline__ void df64_body(double *__restrict__ w, const double *
         mac(a, sdyt[l * LX + j], sws[k * N2 + l * LX + i]);
       }
       const df2 r = result(a);
-      if (active) w[base + (size_t)k * N2] = join(r.hi, r.lo);
+      if (active && !bad) w[base + (size_t)k * N2] = join(r.hi, r.lo);
     }
+  }
+  if (__syncthreads_or(bad)) {  // block-uniform; the barrier also frees the scratch
+    const double *ddy = XYZ ? dy : dx, *ddz = XYZ ? dz : dx;
+    const double *ddyt = XYZ ? dyt : dxt, *ddzt = XYZ ? dzt : dxt;
+    guard::element_f64<LX>(bad, w, u, dx, ddy, ddz, dxt, ddyt, ddzt, h1, g11, g22, g33, g12, g13,
+                           g23, (size_t)(active ? e0 + le : 0) * N3,
+                           reinterpret_cast<double *>(su), own ? p : 0, N2,
+                           [] { __syncthreads(); }, nullptr);
   }
 }
 

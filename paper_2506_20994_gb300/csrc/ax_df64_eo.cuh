@@ -39,6 +39,7 @@
 
 #include "common.cuh"
 #include "df64.cuh"
+#include "guard.cuh"
 
 namespace ax {
 
@@ -97,7 +98,8 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
                                             const double *__restrict__ g12,
                                             const double *__restrict__ g13,
                                             const double *__restrict__ g23,
-                                            const df::dd2 *__restrict__ gp, long long e0,
+                                            const df::dd2 *__restrict__ gp,
+                                            const unsigned *__restrict__ gstat, long long e0,
                                             int nel, int epb, unsigned char *smem_raw,
                                             double *__restrict__ dotp = nullptr,
                                             double *__restrict__ pw = nullptr,
@@ -126,13 +128,22 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
   dd2 *As = Ar + DE;                                                    // lines [k][i]
   dd2 *At = As + DE;                                                    // lines [j][i]
 
-  // coefficients (dx[l*LX+i] = D_il, dxt[l*LX+i] = D_li)
+  // range record of this block (guard.cuh), cleared before any thread notes
+  __shared__ guard::Record rec;
+  guard::clear(rec, epb);
+  __syncthreads();
+
+  // coefficients (dx[l*LX+i] = D_il, dxt[l*LX+i] = D_li); every entry of
+  // both matrices is also checked against its centro-antisymmetric mirror
   for (int q = threadIdx.x; q < H2; q += blockDim.x) {
     const int i = q / H, l = q % H;
 #pragma unroll
     for (int tr = 0; tr < 2; ++tr) {
       const double *m = tr ? dxt : dx;
-      const df2 a = split(__ldg(m + l * LX + i)), b = split(__ldg(m + (N - l) * LX + i));
+      const double da = __ldg(m + l * LX + i), db = __ldg(m + (N - l) * LX + i);
+      guard::note_pair(rec, da, __ldg(m + (N - l) * LX + (N - i)));
+      guard::note_pair(rec, db, __ldg(m + l * LX + (N - i)));
+      const df2 a = split(da), b = split(db);
       // lanes: x = (a + b)/2, y = (a - b)/2 (exact halving)
       dd2 s = dsum2(dd2{pk(a.hi, a.hi), pk(a.lo, a.lo)}, dd2{pk(b.hi, -b.hi), pk(b.lo, -b.lo)});
       const df2 P = norm(lx_(s.hi), lx_(s.lo)), M = norm(ly_(s.hi), ly_(s.lo));
@@ -211,6 +222,7 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
   };
 
   df2 gr[2][2][2], gs_[2][2][2], gt[2][2][2];
+  unsigned ukey = 0u, gkey = 0u, hkey = 0u;  // exponent keys of u, G, h1 (guard.cuh)
   // ---- phase 1: own values of u, (e, o) along each direction
   if (own) {
     if constexpr (PUPD) {
@@ -230,6 +242,7 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
               if (uc) z = __dadd_rn(z, __ldg(corr_in + q));
               const double pn = __fma_rn(beta, pw[q], z);
               pw[q] = pn;
+              ukey = max(ukey, guard::key(pn));
               gr[c][b][a] = split(pn);
             }
           }
@@ -239,9 +252,13 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
 #pragma unroll
         for (int b = 0; b < 2; ++b)
 #pragma unroll
-          for (int a = 0; a < 2; ++a)
-            gr[c][b][a] = active ? split(__ldg(u + gidx(c, b, a))) : df2{0.f, 0.f};
+          for (int a = 0; a < 2; ++a) {
+            const double x = active ? __ldg(u + gidx(c, b, a)) : 0.0;
+            ukey = max(ukey, guard::key(x));
+            gr[c][b][a] = split(x);
+          }
     }
+    if (active) atomicMax(&rec.ex[le][0], ukey);
     publish(gr);
   }
   phase_sync();
@@ -285,6 +302,10 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
 
   // ---- phase 3: pointwise h1 G, the next geometry loading meanwhile
   if constexpr (PREP) {  // point pairs a = 0, 1 as packed lanes
+    if (active && t == 0) {  // the geometry's exponent keys, recorded when it was prepared
+      atomicMax(&rec.ex[le][1], __ldg(gstat + 2 * (e0 + le)));
+      atomicMax(&rec.ex[le][2], __ldg(gstat + 2 * (e0 + le) + 1));
+    }
     if (own) {
       const u64 zero = pk(0.f, 0.f);
 #pragma unroll
@@ -335,6 +356,9 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
         df2 wr{0.f, 0.f}, ws{0.f, 0.f}, wt{0.f, 0.f};
         if (active) {
           const double(&g)[7] = geo[q & 1].v;
+#pragma unroll
+          for (int f = 0; f < 6; ++f) gkey = max(gkey, guard::key(g[f]));
+          hkey = max(hkey, guard::key(g[6]));
           const df2 a11 = split(g[0]), a22 = split(g[1]), a33 = split(g[2]);
           const df2 a12 = split(g[3]), a13 = split(g[4]), a23 = split(g[5]);
           const df2 hh = split(g[6]);
@@ -356,9 +380,17 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
         gs_[c][b][a] = ws;
         gt[c][b][a] = wt;
       }
+      if (active) {
+        atomicMax(&rec.ex[le][1], gkey);
+        atomicMax(&rec.ex[le][2], hkey);
+      }
     }
   }
   phase_sync();  // every thread of the element has read its gradient lines
+
+  // elements outside the double-float window, or matrices whose mirrored rows
+  // the split below would misread, go to fp64 units after phase 5
+  const bool bad = active && !(guard::elem_ok(rec, le) && guard::centro_ok(rec));
 
   // ---- phase 4: (e, o) of the weighted gradient, one direction each
   if (own) {
@@ -375,7 +407,21 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
 #pragma unroll
       for (int a = 0; a < 2; ++a) At[lt(b, a) + kp] = eo_pair(gt[0][b][a], gt[1][b][a]);
   }
-  phase_sync();
+  // the phase barrier also tells every thread whether its element (named
+  // barriers) or block (block barrier) holds an element for the fallback
+  bool any_bad;
+  if (elem_bar) {
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)bad), "r"(1 + le), "r"(H3)
+        : "memory");
+    any_bad = r != 0u;
+  } else {
+    any_bad = __syncthreads_or(bad) != 0;
+  }
 
   double dsum = 0.0;
   // ---- phase 5: transposed half-size contractions, summed, stored
@@ -393,7 +439,7 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
     for (int b = 0; b < 2; ++b)
 #pragma unroll
       for (int a = 0; a < 2; ++a) contract(At + lt(b, a), tf, tn, kp, gt[0][b][a], gt[1][b][a]);
-    if (active) {
+    if (active && !bad) {
 #pragma unroll
       for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -419,6 +465,24 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
             }
           }
         }
+    }
+  }
+  if (any_bad) {  // fp64 units for the flagged elements (element- or block-uniform branch)
+    const double *uu = PUPD ? pw : u;
+    const int rank = (int)threadIdx.x - le * H3;
+    if (elem_bar) {
+      auto sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(1 + le), "r"(H3) : "memory"); };
+      sync();  // phase 5 has read the lines that serve as scratch
+      guard::element_f64<LX>(true, w, uu, dx, dx, dx, dxt, dxt, dxt, h1, g11, g22, g33, g12, g13, g23,
+                             eb, reinterpret_cast<double *>(Ar), rank, H3, sync,
+                             dotp ? &dsum : nullptr);
+    } else {
+      auto sync = [&]() { __syncthreads(); };
+      sync();
+      // every thread takes part in the barriers; only flagged elements compute
+      guard::element_f64<LX>(bad, w, uu, dx, dx, dx, dxt, dxt, dxt, h1, g11, g22, g33, g12,
+                                g13, g23, eb, reinterpret_cast<double *>(Ar), own ? rank : 0,
+                                H3, sync, dotp ? &dsum : nullptr);
     }
   }
   if (dotp) {  // one partial per block, fixed order (block-uniform branch)
@@ -448,8 +512,8 @@ ax_df64eo_kernel(double *__restrict__ w, const double *__restrict__ u,
   const long long e0 = (long long)blockIdx.x * epb;
   const long long left = nelv - e0;
   const int nel = left < epb ? (int)left : epb;
-  df64eo_body<LX, false>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nullptr, e0, nel,
-                         epb, smem_raw);
+  df64eo_body<LX, false>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nullptr, nullptr, e0,
+                         nel, epb, smem_raw);
 }
 
 // Same operator on geometry prepared by eo_prepare_kernel; DOT adds the
@@ -459,7 +523,8 @@ template <int LX, bool DOT, bool PUPD = false>
 __global__ void __launch_bounds__(256, 2)
 ax_df64eo_prep_kernel(double *__restrict__ w, const double *__restrict__ u,
                       const double *__restrict__ dx, const double *__restrict__ dxt,
-                      const df::dd2 *__restrict__ gp, int nelv, int epb,
+                      const df::dd2 *__restrict__ gp, const unsigned *__restrict__ gstat,
+                      guard::RawGeo raw, int nelv, int epb,
                       double *__restrict__ dotp, double *__restrict__ pw,
                       const double *__restrict__ r_in, const double *__restrict__ minv_in,
                       const double *__restrict__ beta_p, const double *__restrict__ corr_in,
@@ -468,16 +533,18 @@ ax_df64eo_prep_kernel(double *__restrict__ w, const double *__restrict__ u,
   const long long e0 = (long long)blockIdx.x * epb;
   const long long left = nelv - e0;
   const int nel = left < epb ? (int)left : epb;
-  df64eo_body<LX, true, PUPD, false>(w, u, dx, dxt, nullptr, nullptr, nullptr, nullptr, nullptr,
-                              nullptr, nullptr, gp, e0, nel, epb, smem_raw,
-                              DOT ? dotp : nullptr, pw, r_in, minv_in, beta_p, corr_in,
-                              use_corr_p);
+  df64eo_body<LX, true, PUPD, false>(w, u, dx, dxt, raw.h1, raw.g11, raw.g22, raw.g33, raw.g12,
+                                     raw.g13, raw.g23, gp, gstat, e0, nel, epb, smem_raw,
+                                     DOT ? dotp : nullptr, pw, r_in, minv_in, beta_p, corr_in,
+                                     use_corr_p);
 }
 
 // Prepared geometry: entry ((e*4 + cp)*7 + f)*H3 + t holds field f at the
 // two points a = 0, 1 of corner pair cp = (c, b) of thread t, split into
 // double-float pairs exactly as the kernel above splits them.  fmask selects
-// the fields to (re)write (bit f; bit 6 = h1).
+// the fields to (re)write (bit f; bit 6 = h1).  The buffer ends with two
+// exponent keys per element (largest of the six G fields, of h1; guard.cuh),
+// written by geo_keys_kernel.
 template <int LX>
 __global__ void eo_prepare_kernel(df::dd2 *__restrict__ gp, const double *__restrict__ h1,
                                   const double *__restrict__ g11,
@@ -505,6 +572,14 @@ __global__ void eo_prepare_kernel(df::dd2 *__restrict__ gp, const double *__rest
     gp[q] = dd2{pk(a0.hi, a1.hi), pk(a0.lo, a1.lo)};
   }
 }
+
+// Exponent keys of each element's fp64 geometry: keys[2e] over g11..g23,
+// keys[2e+1] over h1 (one warp per element).
+__global__ void geo_keys_kernel(unsigned *__restrict__ keys, const double *__restrict__ h1,
+                                const double *__restrict__ g11, const double *__restrict__ g22,
+                                const double *__restrict__ g33, const double *__restrict__ g12,
+                                const double *__restrict__ g13, const double *__restrict__ g23,
+                                int nelv, int n3);
 
 template <int LX>
 int launch_df64eo(double *w, const double *u, const double *dx, const double *dxt,
@@ -536,7 +611,8 @@ int prep_blocks(int nelv, int epb) {
 // pw (with dotp, r_in, minv_in, beta_p): the fused direction update.
 template <int LX>
 int launch_df64eo_prep(double *w, const double *u, const double *dx, const double *dxt,
-                       const df::dd2 *gp, int nelv, int epb, cudaStream_t stream,
+                       const df::dd2 *gp, const guard::RawGeo &raw, int nelv, int epb,
+                       cudaStream_t stream,
                        double *dotp = nullptr, double *pw = nullptr,
                        const double *r_in = nullptr, const double *minv_in = nullptr,
                        const double *beta_p = nullptr, const double *corr_in = nullptr,
@@ -556,8 +632,9 @@ int launch_df64eo_prep(double *w, const double *u, const double *dx, const doubl
   static std::atomic<size_t> granted[3][kMaxDevices];
   if (!grant_smem(kern, smem, granted[kind])) return AX_EINVAL;
   const unsigned grid = (unsigned)((nelv + epb - 1) / epb);
-  kern<<<grid, epb * H3, smem, stream>>>(w, u, dx, dxt, gp, nelv, epb, dotp, pw, r_in, minv_in,
-                                         beta_p, corr_in, use_corr_p);
+  const unsigned *gstat = reinterpret_cast<const unsigned *>(gp + (size_t)nelv * eo::prep_entries<LX>());
+  kern<<<grid, epb * H3, smem, stream>>>(w, u, dx, dxt, gp, gstat, raw, nelv, epb, dotp, pw, r_in,
+                                         minv_in, beta_p, corr_in, use_corr_p);
   return launch_status();
 }
 
@@ -569,6 +646,11 @@ int launch_eo_prepare(df::dd2 *gp, const double *h1, const double *g11, const do
   const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
   eo_prepare_kernel<LX><<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, stream>>>(
       gp, h1, g11, g22, g33, g12, g13, g23, nelv, fmask);
+  int rc = launch_status();
+  if (rc) return rc;
+  unsigned *keys = reinterpret_cast<unsigned *>(gp + (size_t)nelv * eo::prep_entries<LX>());
+  geo_keys_kernel<<<(unsigned)std::max<int64_t>(((int64_t)nelv + 7) / 8, 1), 256, 0, stream>>>(
+      keys, h1, g11, g22, g33, g12, g13, g23, nelv, LX * LX * LX);
   return launch_status();
 }
 

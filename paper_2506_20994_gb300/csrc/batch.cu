@@ -233,7 +233,7 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
     const ax_batch_mesh &s = meshes[m];
     if (mbody[m] != ax::kBodyEvenOdd || s.nelv == 0) continue;
     void *gp = nullptr;
-    if (cudaMalloc(&gp, (size_t)s.nelv * 56 * s.lx * s.lx * s.lx) != cudaSuccess) {
+    if (cudaMalloc(&gp, ax::eo_prep_bytes(s.lx, s.nelv)) != cudaSuccess) {
       (void)cudaGetLastError();
       ax_batch_destroy(B);
       return AX_ENOMEM;
@@ -248,6 +248,8 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
       return rc;
     }
     mh[m].gp = static_cast<const ax::df::dd2 *>(gp);
+    mh[m].gstat = reinterpret_cast<const unsigned *>(static_cast<const char *>(gp) +
+                                                     (size_t)s.nelv * 56 * s.lx * s.lx * s.lx);
   }
   B->dtype = dtype;
   B->nmesh = nmesh;

@@ -13,7 +13,7 @@ int launch_one(int nblocks, size_t smem, const BatchMeshDev *meshes, const Batch
 template <int LX>
 int setup_one(size_t smem, int *bps) {
   auto k = batch_lx_kernel<false, LX>;
-  if (smem > 48 * 1024 &&
+  if (smem + kStaticSmemMargin > 48 * 1024 &&
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess) {
     (void)cudaGetLastError();

@@ -14,7 +14,7 @@ int launch_one(int nblocks, size_t smem, const BatchMeshDev *meshes, const Batch
 template <int LX, int BODY>
 int setup_one(size_t smem, int *bps) {
   auto k = batch_lx_kernel<true, LX, BODY>;
-  if (smem > 48 * 1024 &&
+  if (smem + kStaticSmemMargin > 48 * 1024 &&
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess) {
     (void)cudaGetLastError();

@@ -17,6 +17,7 @@ struct BatchMeshDev {
   void *w;
   const void *u, *dx, *dxt, *h1, *g[6];
   const df::dd2 *gp;  // geometry prepared for the even-odd kernel, or null
+  const unsigned *gstat;  // its per-element exponent keys (guard.cuh)
 };
 
 struct BatchItem {
@@ -49,8 +50,10 @@ batch_lx_kernel(const BatchMeshDev *__restrict__ meshes, const BatchItem *__rest
     if constexpr (F64 && BODY == kBodyEvenOdd) {
       // every mesh of this group has prepared geometry (the plan made it)
       df64eo_body<LX, true>((double *)m.w, (const double *)m.u, (const double *)m.dx,
-                            (const double *)m.dxt, nullptr, nullptr, nullptr, nullptr, nullptr,
-                            nullptr, nullptr, m.gp, itm.e0, itm.nel, m.epb, smem_raw);
+                            (const double *)m.dxt, (const double *)m.h1, (const double *)m.g[0],
+                            (const double *)m.g[1], (const double *)m.g[2], (const double *)m.g[3],
+                            (const double *)m.g[4], (const double *)m.g[5], m.gp, m.gstat,
+                            itm.e0, itm.nel, m.epb, smem_raw);
     } else if constexpr (F64) {
       df64_body<LX>((double *)m.w, (const double *)m.u, (const double *)m.dx,
                     (const double *)m.dxt, (const double *)m.h1, (const double *)m.g[0],

@@ -54,9 +54,12 @@ inline std::mutex &smem_grant_mutex() {
   static std::mutex m;
   return m;
 }
+// Static shared memory of the kernels (guard record, reduction buffers) stays
+// below this; the 48 KB default covers static and dynamic bytes together.
+constexpr size_t kStaticSmemMargin = 4 * 1024;
 template <typename K>
 inline bool grant_smem(K kernel, size_t bytes, std::atomic<size_t> (&granted)[kMaxDevices]) {
-  if (bytes <= 48 * 1024) return true;
+  if (bytes + kStaticSmemMargin <= 48 * 1024) return true;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     (void)cudaGetLastError();

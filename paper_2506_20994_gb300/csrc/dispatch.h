@@ -3,6 +3,7 @@
 #pragma once
 
 #include "df64.cuh"
+#include "guard.cuh"
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -59,13 +60,20 @@ inline bool df64eo_supported(int lx) { return lx >= 4 && lx <= 12 && lx % 2 == 0
 // nelv) of them (default elements per block).
 // pw, r_in, minv_in, beta_p (optional, with dotp): u is replaced by the
 // search direction formed in place, pw = minv_in .* r_in + (*beta_p) pw.
+// raw: the fp64 geometry the prepared copy came from (elements outside the
+// double-float range are recomputed from it with fp64 units).
 int dispatch_df64eo_prep(int lx, double *w, const double *u, const double *dx,
-                         const double *dxt, const df::dd2 *gp, int nelv, int epb,
-                         cudaStream_t st, double *dotp = nullptr, double *pw = nullptr,
+                         const double *dxt, const df::dd2 *gp, const guard::RawGeo &raw,
+                         int nelv, int epb, cudaStream_t st, double *dotp = nullptr, double *pw = nullptr,
                          const double *r_in = nullptr, const double *minv_in = nullptr,
                          const double *beta_p = nullptr, const double *corr_in = nullptr,
                          const int *use_corr_p = nullptr);
 int df64eo_prep_blocks(int lx, int nelv);
+// Bytes of a prepared-geometry buffer: 56 lx^3 per element of double-float
+// pairs, then two exponent keys per element.
+inline size_t eo_prep_bytes(int lx, int nelv) {
+  return (size_t)nelv * 56 * lx * lx * lx + (size_t)nelv * 8;
+}
 int dispatch_eo_prepare(int lx, df::dd2 *gp, const double *h1, const double *g11,
                         const double *g22, const double *g33, const double *g12,
                         const double *g13, const double *g23, int nelv, int fmask,

@@ -34,6 +34,10 @@ namespace {
 // for these orders
 bool op_prepares(int lx) { return lx == 6 || lx == 8 || lx == 10 || lx == 12; }
 
+ax::guard::RawGeo raw_geo(const ax_op *op) {
+  return ax::guard::RawGeo{op->h1, op->g[0], op->g[1], op->g[2], op->g[3], op->g[4], op->g[5]};
+}
+
 }  // namespace
 
 extern "C" int ax_op_destroy(ax_op *op) {
@@ -62,7 +66,7 @@ extern "C" int ax_op_create(ax_op **out, int lx, int nelv, const double *dx, con
   const double *gg[6] = {g11, g22, g33, g12, g13, g23};
   for (int k = 0; k < 6; ++k) op->g[k] = gg[k];
   if (op_prepares(lx) && nelv > 0) {
-    const size_t bytes = (size_t)nelv * 56 * lx * lx * lx;
+    const size_t bytes = ax::eo_prep_bytes(lx, nelv);
     if (cudaMalloc((void **)&op->gp, bytes) != cudaSuccess) {
       (void)cudaGetLastError();
       delete op;
@@ -114,8 +118,8 @@ extern "C" int ax_op_apply(ax_op *op, double *w, const double *u, void *stream) 
   if (op->nelv == 0) return AX_OK;
   int rc;
   if (op->gp) {
-    rc = ax::dispatch_df64eo_prep(op->lx, w, u, op->dx, op->dxt, op->gp, op->nelv, 0,
-                                  (cudaStream_t)stream);
+    rc = ax::dispatch_df64eo_prep(op->lx, w, u, op->dx, op->dxt, op->gp, raw_geo(op), op->nelv,
+                                  0, (cudaStream_t)stream);
   } else {
     const double *const *g = op->g;
     rc = ax_helm(w, u, op->dx, op->dxt, op->h1, g[0], g[1], g[2], g[3], g[4], g[5], op->lx,
@@ -134,15 +138,16 @@ int op_dot_blocks(const ax_op *op) {
 
 int op_apply_dot(ax_op *op, double *w, const double *u, double *partials, cudaStream_t st) {
   if (!op || !op->gp || !partials) return AX_EINVAL;
-  return dispatch_df64eo_prep(op->lx, w, u, op->dx, op->dxt, op->gp, op->nelv, 0, st, partials);
+  return dispatch_df64eo_prep(op->lx, w, u, op->dx, op->dxt, op->gp, raw_geo(op), op->nelv, 0, st,
+                              partials);
 }
 
 int op_update_apply_dot(ax_op *op, double *w, double *p, const double *r, const double *minv,
                         const double *beta, double *partials, cudaStream_t st,
                         const double *corr, const int *use_corr) {
   if (!op || !op->gp || !partials || !p || !r || !minv || !beta) return AX_EINVAL;
-  return dispatch_df64eo_prep(op->lx, w, nullptr, op->dx, op->dxt, op->gp, op->nelv, 0, st,
-                              partials, p, r, minv, beta, corr, use_corr);
+  return dispatch_df64eo_prep(op->lx, w, nullptr, op->dx, op->dxt, op->gp, raw_geo(op), op->nelv,
+                              0, st, partials, p, r, minv, beta, corr, use_corr);
 }
 
 }  // namespace ax
@@ -151,6 +156,6 @@ extern "C" int ax_op_info(const ax_op *op, int *prepared, int64_t *device_bytes)
   if (!op) return AX_EINVAL;
   if (prepared) *prepared = op->gp != nullptr;
   if (device_bytes)
-    *device_bytes = op->gp ? (int64_t)op->nelv * 56 * op->lx * op->lx * op->lx : 0;
+    *device_bytes = op->gp ? (int64_t)ax::eo_prep_bytes(op->lx, op->nelv) : 0;
   return AX_OK;
 }
