@@ -195,16 +195,19 @@ typedef struct ax_op ax_op;
 
 /* Creates the handle.  dx, dxt, h1 and G are borrowed device arrays in
  * ax_helm's conventions and must outlive the handle.  For lx in {6, 8, 10,
- * 12} the handle also converts the geometry once into the even-odd
- * kernel's prepared order (device memory of 56 lx^3 + 8 bytes per element,
- * owned: the same 8 bytes per value, split into double-float pairs exactly
- * as the on-the-fly kernel splits them, plus two exponent records per
- * element; results agree with AX_VARIANT_F64_DF_EO to ~1e-16 relative, the
- * pointwise step running two points per packed instruction).  Range as
- * ax_helm: elements outside the double-float window, and all elements when
- * dx or dxt is not centro-antisymmetric, are computed from the borrowed
- * fp64 arrays with fp64 units.  Synchronises stream.  Returns AX_EINVAL on
- * bad arguments, AX_ENOMEM when the copy cannot be allocated. */
+ * 12}, when dx and dxt are centro-antisymmetric (checked here, to 2^-46 of
+ * their largest entry), the handle converts the geometry once into the
+ * order of the persistent even-odd kernel that ax_op_apply then runs (device
+ * memory, owned: 56 lx^3 + 8 bytes per element - the same 8 bytes per value,
+ * split into double-float pairs, plus two exponent records - and
+ * 32 h (h + 1) + 16 h^2 + 4 bytes of coefficients and status, h = lx/2).  That kernel streams
+ * each element's geometry into shared memory with one bulk copy, one element
+ * ahead; results agree with AX_VARIANT_F64_DF_EO to ~1e-16 relative.  Range
+ * as ax_helm: elements outside the double-float window are computed from the
+ * borrowed fp64 arrays with fp64 units; other lx, and matrices without the
+ * symmetry, apply through ax_helm.  Synchronises stream.  Returns AX_EINVAL
+ * on bad arguments, AX_ENOMEM when an allocation fails, AX_ELAUNCH when a
+ * copy or launch fails. */
 int ax_op_create(ax_op **op, int lx, int nelv, const double *dx, const double *dxt,
                  const double *h1, const double *g11, const double *g22, const double *g33,
                  const double *g12, const double *g13, const double *g23, void *stream);
@@ -218,6 +221,12 @@ int ax_op_set_h1(ax_op *op, const double *h1, void *stream);
 int ax_op_set_h2(ax_op *op, const double *h2, const double *B, void *stream);
 /* Whether the geometry is prepared and how many device bytes that holds. */
 int ax_op_info(const ax_op *op, int *prepared, int64_t *device_bytes);
+/* *flag = 1 if an apply on the prepared path gave up waiting for the
+ * bulk copy that stages an element's geometry in shared memory (every wait
+ * is bounded, so a lost copy ends the launch with this flag set instead of
+ * hanging; the output is then incomplete), else 0.  Synchronises the
+ * device; the flag stays set for the life of the handle. */
+int ax_op_error(const ax_op *op, int *flag);
 int ax_op_destroy(ax_op *op);
 
 /* ------------------------------------------------------------------------

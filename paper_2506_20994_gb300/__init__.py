@@ -242,7 +242,8 @@ class _DeviceArray:
 class Operator:
     """The element operator of one mesh for repeated applies (ax_op_*).
     Keeps references to the borrowed device arrays; for lx in {6, 8, 10, 12}
-    the library holds the geometry in the even-odd kernel's prepared order."""
+    the library holds the geometry in the persistent even-odd kernel's
+    prepared order."""
 
     def __init__(self, lx: int, dx, dxt, h1, g11, g22, g33, g12, g13, g23):
         import ctypes
@@ -272,6 +273,13 @@ class Operator:
         p, b = ctypes.c_int(), ctypes.c_int64()
         check("ax_op_info", lib().ax_op_info(self._h, ctypes.addressof(p), ctypes.addressof(b)))
         return {"prepared": bool(p.value), "device_bytes": b.value}
+
+    def error(self) -> int:
+        """1 if a launch gave up waiting for a staged geometry copy (synchronises)."""
+        import ctypes
+        f = ctypes.c_int()
+        check("ax_op_error", lib().ax_op_error(self._h, ctypes.addressof(f)))
+        return f.value
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -192,7 +192,7 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
   // (v0 + v1, v0 - v1) as one entry
   auto eo_pair = [](df2 v0, df2 v1) {
     return dsum2(dd2{pk(v0.hi, v0.hi), pk(v0.lo, v0.lo)},
-                 dd2{pk(v1.hi, -v1.hi), pk(v1.lo, -v1.lo)});
+                 dd2{pk_pm(v1.hi), pk_pm(v1.lo)});
   };
   auto publish = [&](df2 (&v)[2][2][2]) {
 #pragma unroll
@@ -216,7 +216,7 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
     for (int l = 1; l < H; ++l) mac2(a, cof[row * H + l], nco[row * H + l], line[l]);
     // lanes: x = E, y = O.  (O + E, O - E) in one packed sum
     const float Es = lx_(a.s), Ec = lx_(a.c), Os = ly_(a.s), Oc = ly_(a.c);
-    const dd2 r = dsum2(dd2{pk(Os, Os), pk(Oc, Oc)}, dd2{pk(Es, -Es), pk(Ec, -Ec)});
+    const dd2 r = dsum2(dd2{pk(Os, Os), pk(Oc, Oc)}, dd2{pk_pm(Es), pk_pm(Ec)});
     y_lo = df2{lx_(r.hi), lx_(r.lo)};
     y_hi = df2{ly_(r.hi), ly_(r.lo)};
   };
@@ -319,10 +319,10 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
           const dd2 US{pk(gs_[c][b][0].hi, gs_[c][b][1].hi),
                        pk(gs_[c][b][0].lo, gs_[c][b][1].lo)};
           const dd2 UT{pk(gt[c][b][0].hi, gt[c][b][1].hi), pk(gt[c][b][0].lo, gt[c][b][1].lo)};
-          const u64 nR = sub2(zero, UR.hi), nS = sub2(zero, US.hi), nT = sub2(zero, UT.hi);
+          const u64 nR = neg2(UR.hi), nS = neg2(US.hi), nT = neg2(UT.hi);
           const dd2 &G11 = g.v[0], &G22 = g.v[1], &G33 = g.v[2];
           const dd2 &G12 = g.v[3], &G13 = g.v[4], &G23 = g.v[5], &HH = g.v[6];
-          const u64 nH = sub2(zero, HH.hi);
+          const u64 nH = neg2(HH.hi);
           acc2 a = prod2(UR, nR, G11);
           mac2(a, US, nS, G12);
           mac2(a, UT, nT, G13);
@@ -572,14 +572,6 @@ __global__ void eo_prepare_kernel(df::dd2 *__restrict__ gp, const double *__rest
     gp[q] = dd2{pk(a0.hi, a1.hi), pk(a0.lo, a1.lo)};
   }
 }
-
-// Exponent keys of each element's fp64 geometry: keys[2e] over g11..g23,
-// keys[2e+1] over h1 (one warp per element).
-__global__ void geo_keys_kernel(unsigned *__restrict__ keys, const double *__restrict__ h1,
-                                const double *__restrict__ g11, const double *__restrict__ g22,
-                                const double *__restrict__ g33, const double *__restrict__ g12,
-                                const double *__restrict__ g13, const double *__restrict__ g23,
-                                int nelv, int n3);
 
 template <int LX>
 int launch_df64eo(double *w, const double *u, const double *dx, const double *dxt,

@@ -1,0 +1,423 @@
+// Persistent fp64-accurate element operator (Listing 2) for the operator
+// handle: the even-odd double-float schedule of ax_df64_eo.cuh, one element
+// per CTA at a time, with the element's geometry streamed into shared memory
+// by the bulk-copy engine one element ahead.
+//
+// Why a second schedule: the even-odd kernel that reads its geometry with
+// per-thread loads spends its time waiting on those loads (16 warps per SM
+// at 128 registers, two geometry stages held in registers) and reaches only
+// half of the HBM bandwidth although its arithmetic would allow more.  Here
+//  * each CTA loops over elements e = blockIdx.x, + gridDim.x, ...; while it
+//    computes element e, one `cp.async.bulk` (completion on an mbarrier)
+//    brings the next element's prepared geometry (56 lx^3 bytes, contiguous)
+//    into shared memory, and every thread's u values of the next element are
+//    already loaded into registers, so no phase waits on global memory;
+//  * the element's (lx/2)^3 mirror octants get two threads each (thread
+//    2t + c owns the four points {i', N-i'} x {j', N-j'} x {k} with k = k'
+//    for c = 0 and N - k' for c = 1); pairs along i and j stay inside a
+//    thread, pairs along k are formed with one shuffle with the partner lane;
+//  * the line buffers of the three directions are XOR-swizzled at lx = 8
+//    (four 16-byte entries per line, no padding, conflict-free reads and
+//    writes); four CTAs of 124 registers per SM (measured faster than five
+//    of 96: the double-float chains want the registers more than the warps).
+// The arithmetic is that of the even-odd kernel on prepared geometry
+// (double-float pairs, packed f32x2, the two half-size sums of each 1-D
+// contraction as the two lanes).  Elements outside the double-float range
+// (guard.cuh) are recomputed with fp64 units from the caller's fp64 arrays;
+// matrices that are not centro-antisymmetric never reach this kernel (the
+// handle checks them when it is created).
+#pragma once
+
+#include "common.cuh"
+#include "df64.cuh"
+#include "guard.cuh"
+
+namespace ax {
+namespace eop {
+
+template <int LX>
+struct Cfg {
+  static constexpr int H = LX / 2, N = LX - 1, H2 = H * H, H3 = H2 * H;
+  static constexpr int NT = 2 * H3;                // threads per element
+  static constexpr int NTB = (NT + 31) / 32 * 32;  // block size
+  static constexpr int NW = NTB / 32;
+  static constexpr int N3 = LX * LX * LX;
+  static constexpr bool SWZ = H == 4;              // swizzled, unpadded lines
+  static constexpr int LS = SWZ ? 4 : H + 1;       // 16-byte entries per line
+  static constexpr int DE = LX * LX * LS;          // entries per direction
+  static constexpr int GE = 2 * 7 * NT;            // geometry entries per element
+  static constexpr unsigned GBYTES = GE * 16u;     // = 56 lx^3
+  static constexpr int CS = H + 1;                 // padded coefficient row (dd2 entries)
+  static constexpr size_t COEF_BYTES = 2 * H * CS * 16 + 2 * H2 * 8;
+  static constexpr size_t OFF_LINES = (COEF_BYTES + 127) / 128 * 128;
+  static constexpr size_t LINE_BYTES = 3 * (size_t)DE * 16;
+  static constexpr size_t OFF_G = OFF_LINES + (LINE_BYTES + 127) / 128 * 128;
+  static constexpr size_t OFF_MISC = OFF_G + GBYTES;
+  // mbarrier (8 B, padded to 16), one key slot and one dot slot per warp
+  static constexpr size_t SMEM = OFF_MISC + 16 + NW * 8 + NW * 8;
+  // resident CTAs per SM the launch bounds ask for
+  static constexpr int MINB = LX == 6 ? 8 : LX == 8 ? 4 : LX == 10 ? 2 : 1;
+  static_assert(LINE_BYTES >= 3 * (size_t)N3 * 8, "fallback scratch must fit the lines");
+};
+
+// Entry `ent` of line L.  At lx = 8 (L = 8 * outer + inner) the line slot
+// swaps neighbours when bit 3 of L is set and the entry is XOR-ed with bits 1
+// and 3 of L: every line read and write of the kernel then touches each
+// 16-byte bank group at most once per wavefront's worth of distinct entries.
+template <int LX>
+AX_D int lpos(int L, int ent) {
+  if constexpr (Cfg<LX>::SWZ) {
+    const int b3 = (L >> 3) & 1;
+    return (L ^ b3) * 4 + (ent ^ (((L >> 1) & 1) | (b3 << 1)));
+  } else {
+    return L * Cfg<LX>::LS + ent;
+  }
+}
+
+AX_D uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+AX_D void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// One bulk copy global -> shared of `bytes` (16-byte aligned, multiple of
+// 16), completing on the mbarrier's current phase (single arrival + bytes).
+AX_D void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+// Generic-proxy reads of a buffer before the bulk engine rewrites it.
+AX_D void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Waits for the mbarrier phase with the given parity; false after `limit`
+// polls (each poll may suspend the thread for a short, bounded time).
+AX_D bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+constexpr int kWaitLimit = 1 << 22;
+
+// exchange of one pair with the partner lane (tid ^ 1)
+AX_D df::df2 xchg(df::df2 v) {
+  return df::df2{__shfl_xor_sync(0xffffffffu, v.hi, 1), __shfl_xor_sync(0xffffffffu, v.lo, 1)};
+}
+
+// DOT: per-CTA partials of u . w (one per CTA, fixed order).  PUPD: u is not
+// an input; phase 1 forms the solver's next direction in place, pw = minv .*
+// r (+ corr when *use_corr) + (*beta) pw (fp64, explicit roundings), and the
+// operator is applied to it.
+template <int LX, bool DOT, bool PUPD>
+__global__ void __launch_bounds__(Cfg<LX>::NTB, Cfg<LX>::MINB)
+ax_eop_kernel(double *__restrict__ w, const double *__restrict__ u,
+              const df::dd2 *__restrict__ coef, const df::dd2 *__restrict__ gp,
+              const unsigned *__restrict__ gkeys, guard::RawGeo raw,
+              const double *__restrict__ dx, const double *__restrict__ dxt, int dfield,
+              int nelv, int *__restrict__ err, double *__restrict__ dotp,
+              double *__restrict__ pw, const double *__restrict__ r_in,
+              const double *__restrict__ minv_in, const double *__restrict__ beta_p,
+              const double *__restrict__ corr_in, const int *__restrict__ use_corr_p) {
+  using namespace df;
+  using C = Cfg<LX>;
+  constexpr int H = C::H, N = C::N, H2 = C::H2, NT = C::NT, NW = C::NW, N3 = C::N3;
+  extern __shared__ __align__(128) unsigned char sm[];
+  constexpr int CS = C::CS;
+  dd2 *cf = reinterpret_cast<dd2 *>(sm);  // [H][CS] (P, M) of D, rows padded
+  dd2 *tf = cf + H * CS;                  // [H][CS] (P, M) of D^T
+  u64 *cn = reinterpret_cast<u64 *>(tf + H * CS);  // [H][H] negated heads
+  u64 *tn = cn + H2;
+  // line buffer: per direction [k][j] (r), [k][i] (s), [j][i] (t)
+  dd2 *Lb = reinterpret_cast<dd2 *>(sm + C::OFF_LINES);
+  dd2 *Gs = reinterpret_cast<dd2 *>(sm + C::OFF_G);
+  const uint32_t bar = smem_u32(sm + C::OFF_MISC);
+  unsigned *kslot = reinterpret_cast<unsigned *>(sm + C::OFF_MISC + 16);
+  double *red = reinterpret_cast<double *>(sm + C::OFF_MISC + 16 + NW * 8);
+
+  const int tid = threadIdx.x;
+  const bool real = tid < NT;
+  const int t = real ? tid >> 1 : 0, c = tid & 1;
+  const int ip = t % H, jp = (t / H) % H, kp = t / H2;
+  const int kk = c ? N - kp : kp;
+  auto pidx = [&](int b, int a) __attribute__((always_inline)) {
+    return (kk * LX + (b ? N - jp : jp)) * LX + (a ? N - ip : ip);
+  };
+  auto lineR = [&](int b) __attribute__((always_inline)) { return kk * LX + (b ? N - jp : jp); };
+  auto lineS = [&](int a) __attribute__((always_inline)) { return kk * LX + (a ? N - ip : ip); };
+  auto lineT = [&](int b, int a) __attribute__((always_inline)) { return (b ? N - jp : jp) * LX + (a ? N - ip : ip); };
+  auto eo_pair = [](df2 v0, df2 v1) __attribute__((always_inline)) {
+    return dsum2(dd2{pk(v0.hi, v0.hi), pk(v0.lo, v0.lo)},
+                 dd2{pk_pm(v1.hi), pk_pm(v1.lo)});
+  };
+  // half-size contractions of line L of `lines`: (y at row, y at N-row)
+  auto contract = [&](const dd2 *lines, int L, const dd2 *cof, const u64 *nco, int row,
+                      df2 &y_lo, df2 &y_hi) __attribute__((always_inline)) {
+    acc2 a = prod2(cof[row * CS], nco[row * H], lines[lpos<LX>(L, 0)]);
+#pragma unroll
+    for (int l = 1; l < H; ++l)
+      mac2(a, cof[row * CS + l], nco[row * H + l], lines[lpos<LX>(L, l)]);
+    const float Es = lx_(a.s), Ec = lx_(a.c), Os = ly_(a.s), Oc = ly_(a.c);
+    const dd2 r = dsum2(dd2{pk(Os, Os), pk(Oc, Oc)}, dd2{pk_pm(Es), pk_pm(Ec)});
+    y_lo = df2{lx_(r.hi), lx_(r.lo)};
+    y_hi = df2{ly_(r.hi), ly_(r.lo)};
+  };
+  // the three directions' lines of one field (v[b][a] at this thread's points)
+  auto publish = [&](dd2 *Ar, df2 (&vr)[2][2], df2 (&vs)[2][2], df2 (&vt)[2][2])
+                     __attribute__((always_inline)) {
+    dd2 *As = Ar + C::DE, *At = As + C::DE;
+    // k-pairs: this thread forms the entries of lines (b = c, a); it needs the
+    // partner's values there, the partner its values at b = 1 - c
+    // (selects, not vt[1 - c]: a run-time index would put the array in local memory)
+    df2 o0 = xchg(c ? vt[0][0] : vt[1][0]), o1 = xchg(c ? vt[0][1] : vt[1][1]);
+    if (real) {
+#pragma unroll
+      for (int b = 0; b < 2; ++b) Ar[lpos<LX>(lineR(b), ip)] = eo_pair(vr[b][0], vr[b][1]);
+#pragma unroll
+      for (int a = 0; a < 2; ++a) As[lpos<LX>(lineS(a), jp)] = eo_pair(vs[0][a], vs[1][a]);
+      At[lpos<LX>(lineT(c, 0), kp)] = c ? eo_pair(o0, vt[1][0]) : eo_pair(vt[0][0], o0);
+      At[lpos<LX>(lineT(c, 1), kp)] = c ? eo_pair(o1, vt[1][1]) : eo_pair(vt[0][1], o1);
+    }
+  };
+  // contractions of the three directions into this thread's points
+  auto contract_all = [&](const dd2 *Ar, const dd2 *cof, const u64 *nco, df2 (&yr)[2][2],
+                          df2 (&ys)[2][2], df2 (&yt)[2][2]) __attribute__((always_inline)) {
+    const dd2 *As = Ar + C::DE, *At = As + C::DE;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) contract(Ar, lineR(b), cof, nco, ip, yr[b][0], yr[b][1]);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) contract(As, lineS(a), cof, nco, jp, ys[0][a], ys[1][a]);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      df2 y0, y1;  // at k = k' and k = N - k' of point (b = c, a)
+      contract(At, lineT(c, a), cof, nco, kp, y0, y1);
+      const df2 own = c ? y1 : y0;
+      const df2 recv = xchg(c ? y0 : y1);  // the partner's line, at this thread's k
+      yt[0][a] = c ? recv : own;
+      yt[1][a] = c ? own : recv;
+    }
+  };
+
+  // ---- set-up: barrier, coefficients, first element's geometry and u
+  if (tid == 0) mbar_init(bar, 1);
+  for (int q = tid; q < (int)(C::COEF_BYTES / 16); q += blockDim.x)
+    reinterpret_cast<ulonglong2 *>(sm)[q] = __ldg(reinterpret_cast<const ulonglong2 *>(coef) + q);
+  __syncthreads();
+  long long e = blockIdx.x;
+  const long long stride = gridDim.x;
+  if (tid == 0 && e < nelv) bulk_load(smem_u32(Gs), gp + (size_t)e * C::GE, C::GBYTES, bar);
+
+  double uv[2][2] = {{0.0, 0.0}, {0.0, 0.0}};      // u (or r) of the element in turn
+  double mv[2][2], pv[2][2], qv[2][2];             // PUPD: minv, old direction, corr
+  auto load_in = [&](long long el) __attribute__((always_inline)) {
+    const size_t eb = (size_t)el * N3;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const size_t q = eb + pidx(b, a);
+        if constexpr (PUPD) {
+          uv[b][a] = __ldg(r_in + q);
+          mv[b][a] = __ldg(minv_in + q);
+          pv[b][a] = pw[q];
+          qv[b][a] = corr_in ? __ldg(corr_in + q) : 0.0;
+        } else {
+          uv[b][a] = __ldg(u + q);
+        }
+      }
+  };
+  if (real && e < nelv) load_in(e);
+  double beta = 0.0;
+  bool use_corr = false;
+  if constexpr (PUPD) {
+    beta = *beta_p;
+    use_corr = corr_in != nullptr && *use_corr_p != 0;
+  }
+
+  uint32_t parity = 0;
+  double dsum = 0.0;
+  for (; e < nelv; e += stride, parity ^= 1u) {
+    const long long nx = e + stride;
+    const size_t eb = (size_t)e * N3;
+    // this element's admissible exponent fields of u (guard.cuh, u_range)
+    const uint2 ur_e = __ldg(reinterpret_cast<const uint2 *>(gkeys) + e);
+    // ---- phase 1: this element's u (or the direction formed here), split,
+    // lines of the three directions; the next element's inputs start loading
+    double ucur[2][2];
+    unsigned uk = 0u;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        double x = uv[b][a];
+        if constexpr (PUPD) {
+          double z = __dmul_rn(mv[b][a], x);
+          if (use_corr) z = __dadd_rn(z, qv[b][a]);
+          x = __fma_rn(beta, pv[b][a], z);
+          if (real) pw[eb + pidx(b, a)] = x;
+        }
+        ucur[b][a] = x;
+        uk = max(uk, guard::key(x));
+      }
+    df2 v[2][2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) v[b][a] = split(ucur[b][a]);
+    if (real && nx < nelv) load_in(nx);
+    uk = __reduce_max_sync(0xffffffffu, real ? uk : 0u);
+    if ((tid & 31) == 0) kslot[tid >> 5] = uk;
+    publish(Lb, v, v, v);
+    __syncthreads();
+
+    // ---- phase 2: reference gradient
+    df2 gr[2][2], gs[2][2], gt[2][2];
+    contract_all(Lb, cf, cn, gr, gs, gt);
+
+    // ---- phase 3: pointwise h1 G with this element's staged geometry
+    const bool got = mbar_wait(bar, parity, kWaitLimit);
+    {
+      const u64 zero = pk(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        dd2 g[7];
+#pragma unroll
+        for (int f = 0; f < 7; ++f) g[f] = Gs[(b * 7 + f) * NT + (real ? tid : 0)];
+        const dd2 UR{pk(gr[b][0].hi, gr[b][1].hi), pk(gr[b][0].lo, gr[b][1].lo)};
+        const dd2 US{pk(gs[b][0].hi, gs[b][1].hi), pk(gs[b][0].lo, gs[b][1].lo)};
+        const dd2 UT{pk(gt[b][0].hi, gt[b][1].hi), pk(gt[b][0].lo, gt[b][1].lo)};
+        const u64 nR = neg2(UR.hi), nS = neg2(US.hi), nT = neg2(UT.hi);
+        const u64 nH = neg2(g[6].hi);
+        acc2 q = prod2(UR, nR, g[0]);
+        mac2(q, US, nS, g[3]);
+        mac2(q, UT, nT, g[4]);
+        acc2 m = prod2(g[6], nH, dd2{q.s, q.c});
+        gr[b][0] = df2{lx_(m.s), lx_(m.c)};
+        gr[b][1] = df2{ly_(m.s), ly_(m.c)};
+        q = prod2(UR, nR, g[3]);
+        mac2(q, US, nS, g[1]);
+        mac2(q, UT, nT, g[5]);
+        m = prod2(g[6], nH, dd2{q.s, q.c});
+        gs[b][0] = df2{lx_(m.s), lx_(m.c)};
+        gs[b][1] = df2{ly_(m.s), ly_(m.c)};
+        q = prod2(UR, nR, g[4]);
+        mac2(q, US, nS, g[5]);
+        mac2(q, UT, nT, g[2]);
+        m = prod2(g[6], nH, dd2{q.s, q.c});
+        gt[b][0] = df2{lx_(m.s), lx_(m.c)};
+        gt[b][1] = df2{ly_(m.s), ly_(m.c)};
+      }
+    }
+    // every thread is done with the geometry and the gradient lines
+    if (!__syncthreads_and(got)) {
+      // a staged copy never completed: record it and stop (CTA-uniform);
+      // the copy may still be in flight, so wait once more, bounded
+      if (tid == 0) {
+        if (err) atomicExch(err, 1);
+        (void)mbar_wait(bar, parity, kWaitLimit);
+      }
+      break;
+    }
+    if (tid == 0 && nx < nelv) {
+      fence_async_smem();
+      bulk_load(smem_u32(Gs), gp + (size_t)nx * C::GE, C::GBYTES, bar);
+    }
+    unsigned uke = 0u;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) uke = max(uke, kslot[q]);
+    const bool bad = !guard::u_in_range(ur_e, guard::field(uke));
+
+    // ---- phase 4: lines of the weighted gradient
+    publish(Lb, gr, gs, gt);
+    __syncthreads();
+
+    // ---- phase 5: transposed contractions, summed, stored
+    contract_all(Lb, tf, tn, gr, gs, gt);
+    if (real && !bad) {
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        dd2 acc = dsum2(dd2{pk(gr[b][0].hi, gr[b][1].hi), pk(gr[b][0].lo, gr[b][1].lo)},
+                        dd2{pk(gs[b][0].hi, gs[b][1].hi), pk(gs[b][0].lo, gs[b][1].lo)});
+        acc = dsum2(acc, dd2{pk(gt[b][0].hi, gt[b][1].hi), pk(gt[b][0].lo, gt[b][1].lo)});
+        const df2 w0 = norm(lx_(acc.hi), lx_(acc.lo)), w1 = norm(ly_(acc.hi), ly_(acc.lo));
+        const double wd0 = join(w0.hi, w0.lo), wd1 = join(w1.hi, w1.lo);
+        w[eb + pidx(b, 0)] = wd0;
+        w[eb + pidx(b, 1)] = wd1;
+        if constexpr (DOT) {
+          dsum = __fma_rn(ucur[b][0], wd0, dsum);
+          dsum = __fma_rn(ucur[b][1], wd1, dsum);
+        }
+      }
+    }
+    if (bad) {  // CTA-uniform: fp64 units for this element
+      __syncthreads();  // phase 5 has read the lines that serve as scratch
+      guard::element_f64<LX>(real, w, PUPD ? pw : u, dx, dx, dx, dxt, dxt, dxt, raw.h1, raw.g11,
+                             raw.g22, raw.g33, raw.g12, raw.g13, raw.g23, eb,
+                             reinterpret_cast<double *>(Lb), tid, NT, [] { __syncthreads(); },
+                             DOT ? &dsum : nullptr);
+    }
+    __syncthreads();  // the lines and key slots are free for the next element
+  }
+
+  if constexpr (DOT) {  // one partial per CTA: fixed shuffle tree, warps in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+    if ((tid & 31) == 0) red[tid >> 5] = dsum;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int q = 0; q < NW; ++q) s += red[q];
+      dotp[blockIdx.x] = s;
+    }
+  }
+}
+
+// Prepared geometry of this kernel: per element, entry (b * 7 + f) * NT + tid
+// holds field f (g11, g22, g33, g12, g13, g23, h1) at the two points a = 0, 1
+// of thread tid's corner (c, b) = (tid & 1, b), split into double-float pairs
+// {hi(a=0), hi(a=1), lo(a=0), lo(a=1)} (rounded to nearest, split_rn).
+// fmask picks the fields to write.
+template <int LX>
+__global__ void eop_prepare_kernel(df::dd2 *__restrict__ gp, const double *__restrict__ h1,
+                                   const double *__restrict__ g11,
+                                   const double *__restrict__ g22,
+                                   const double *__restrict__ g33,
+                                   const double *__restrict__ g12,
+                                   const double *__restrict__ g13,
+                                   const double *__restrict__ g23, int nelv, int fmask) {
+  using namespace df;
+  using C = Cfg<LX>;
+  constexpr int H = C::H, N = C::N, H2 = C::H2, NT = C::NT, N3 = C::N3;
+  const int64_t total = (int64_t)nelv * C::GE;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int tid = (int)(q % NT);
+    const int f = (int)((q / NT) % 7);
+    if (!((fmask >> f) & 1)) continue;
+    const int b = (int)((q / (7 * NT)) % 2);
+    const int64_t e = q / C::GE;
+    const int t = tid >> 1, c = tid & 1;
+    const int ip = t % H, jp = (t / H) % H, kp = t / H2;
+    const int k = c ? N - kp : kp, j = b ? N - jp : jp;
+    const double *fld = f == 0 ? g11 : f == 1 ? g22 : f == 2 ? g33 : f == 3 ? g12 : f == 4 ? g13
+                      : f == 5 ? g23 : h1;
+    const size_t row = (size_t)e * N3 + (size_t)(k * LX + j) * LX;
+    const df2 a0 = split_rn(fld[row + ip]), a1 = split_rn(fld[row + N - ip]);
+    gp[q] = dd2{pk(a0.hi, a1.hi), pk(a0.lo, a1.lo)};
+  }
+}
+
+}  // namespace eop
+}  // namespace ax

@@ -105,6 +105,17 @@ DF_HD df2 split(double x) {
   return o;
 }
 
+// Round-to-nearest split for data converted once (prepared geometry,
+// coefficients): hi = fl32(x), lo = fl32(x - hi), |x - (hi + lo)| <= 2^-48 |x|
+// for 2^-100 <= |x| < 2^127 (half the error of `split`; it costs fp64 and
+// conversion instructions, so the kernels' per-apply splits use `split`).
+DF_HD df2 split_rn(double x) {
+  df2 o;
+  o.hi = (float)x;
+  o.lo = (float)(x - (double)o.hi);
+  return o;
+}
+
 // --- double-float -> fp64, integer ops plus one fp32->int conversion -------
 // Requires |lo| <= ulp(hi)/2 (a normalised pair, see `norm`).  Exact to
 // within half an fp64 ulp of (hi + lo) for |hi| >= 2^-75; below that lo is
@@ -214,6 +225,12 @@ DF_D u64 fma2(u64 a, u64 b, u64 c) {
   return d;
 }
 
+// Sign flips by integer XOR (integer pipe), keeping them off the fp32 pipe
+// that the double-float arithmetic saturates.
+DF_D u64 neg2(u64 a) { return a ^ 0x8000000080000000ull; }
+DF_D float negf(float a) { return __uint_as_float(__float_as_uint(a) ^ 0x80000000u); }
+DF_D u64 pk_pm(float x) { return pk(x, negf(x)); }  // (x, -x)
+
 // Two double-float values, lane by lane: value_x = lx(hi)+lx(lo), etc.
 struct __align__(16) dd2 {
   u64 hi, lo;
@@ -228,7 +245,7 @@ DF_D acc2 prod2(dd2 d, u64 nd, dd2 u) {
   acc2 a;
   a.s = mul2p(d.hi, u.hi);
   const u64 q = fma2(nd, u.hi, a.s);  // s - d.hi*u.hi = -(rounding error)
-  u64 c = fma2(d.hi, u.lo, sub2(pk(0.f, 0.f), q));
+  u64 c = fma2(d.hi, u.lo, neg2(q));
   a.c = fma2(d.lo, u.hi, c);
   return a;
 }

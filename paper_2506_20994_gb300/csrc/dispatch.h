@@ -69,6 +69,36 @@ int dispatch_df64eo_prep(int lx, double *w, const double *u, const double *dx,
                          const double *beta_p = nullptr, const double *corr_in = nullptr,
                          const int *use_corr_p = nullptr);
 int df64eo_prep_blocks(int lx, int nelv);
+// Persistent even-odd operator of the operator handle (ax_eo_persist.cuh),
+// lx in {6, 8, 10, 12}.  gp: geometry prepared by eop_prepare (eo_prep_bytes
+// bytes, the keys at its end); coef: the block eop_coefficients writes
+// (eop_coef_bytes, device); dfield: its matrices' exponent field.  dotp:
+// one partial of u . w per CTA, eop_blocks(lx, nelv, true) of them; pw, r,
+// minv, beta (+ corr, use_corr): the fused direction update (as
+// dispatch_df64eo_prep).  err: device word set to 1 if a staged copy never
+// arrived (may be null).
+struct EopArgs {
+  double *w = nullptr;
+  const double *u = nullptr;
+  const df::dd2 *coef = nullptr, *gp = nullptr;
+  guard::RawGeo raw{};
+  const double *dx = nullptr, *dxt = nullptr;
+  int dfield = 0, nelv = 0;
+  int *err = nullptr;
+  double *dotp = nullptr, *pw = nullptr;
+  const double *r = nullptr, *minv = nullptr, *beta = nullptr, *corr = nullptr;
+  const int *use_corr = nullptr;
+};
+bool eop_supported(int lx);
+int eop_launch(int lx, const EopArgs &a, cudaStream_t st);
+int eop_blocks(int lx, int nelv, bool dot);
+// dfield: as eop_coefficients reports it (the per-element u ranges depend on it)
+int eop_prepare(int lx, df::dd2 *gp, const guard::RawGeo &raw, int nelv, int fmask, int dfield,
+                cudaStream_t st);
+size_t eop_coef_bytes(int lx);
+bool eop_coefficients(int lx, const double *dx_host, const double *dxt_host, void *out,
+                      int *dfield);
+
 // Bytes of a prepared-geometry buffer: 56 lx^3 per element of double-float
 // pairs, then two exponent keys per element.
 inline size_t eo_prep_bytes(int lx, int nelv) {

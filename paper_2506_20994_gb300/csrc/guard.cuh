@@ -52,6 +52,32 @@ AX_HD bool window_ok(int fu, int fg, int fh, int fd) {
          in(a + b + c + 2 * d, -90, 100);
 }
 
+// For fixed G, h1 and D exponent fields, the u fields window_ok accepts form
+// one interval; u_range packs it as {lo | hi << 16, zero_ok} (zero_ok: an
+// all-zero u is fine, i.e. nothing is non-finite), u_in_range tests it.
+AX_HD void u_range(int fg, int fh, int fd, unsigned &packed, unsigned &zero_ok) {
+  int lo = 1, hi = 0;  // empty
+  zero_ok = (fg != 2047 && fh != 2047 && fd != 2047) ? 1u : 0u;
+  if (zero_ok) {
+    if (fg == 0 || fh == 0 || fd == 0) {
+      lo = 1;
+      hi = 2046;  // a zero factor: any finite u
+    } else {
+      for (int fu = 1; fu <= 2046; ++fu) {  // the window is an interval in fu
+        if (window_ok(fu, fg, fh, fd)) {
+          if (lo > hi) lo = fu;
+          hi = fu;
+        }
+      }
+    }
+  }
+  packed = (unsigned)lo | ((unsigned)hi << 16);
+}
+AX_HD bool u_in_range(uint2 r, int fu) {
+  if (fu == 0) return r.y != 0u;
+  return fu >= (int)(r.x & 0xFFFFu) && fu <= (int)(r.x >> 16);
+}
+
 // Per-block record: per element the three exponent keys (u, G, h1), plus the
 // largest |D| key and the largest centro-antisymmetry defect of the matrices.
 constexpr int kMaxElems = 64;
@@ -150,4 +176,17 @@ __device__ __noinline__ void element_f64(bool on, double *__restrict__ w, const 
 }
 
 }  // namespace guard
+
+// Rewrites per-element geometry keys {G, h1} in place into the u range of
+// guard::u_range for matrices whose largest entry has exponent field fd.
+__global__ void geo_urange_kernel(unsigned *__restrict__ keys, int nelv, int fd);
+
+// Exponent keys of each element's fp64 geometry: keys[2e] over g11..g23,
+// keys[2e+1] over h1 (one warp per element; 8 elements per 256-thread block).
+__global__ void geo_keys_kernel(unsigned *__restrict__ keys, const double *__restrict__ h1,
+                                const double *__restrict__ g11, const double *__restrict__ g22,
+                                const double *__restrict__ g33, const double *__restrict__ g12,
+                                const double *__restrict__ g13, const double *__restrict__ g23,
+                                int nelv, int n3);
+
 }  // namespace ax

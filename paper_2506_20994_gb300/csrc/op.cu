@@ -6,6 +6,7 @@
 // them.
 #include <algorithm>
 #include <new>
+#include <vector>
 
 #include "../../include/axhelm.h"
 #include "common.cuh"
@@ -15,8 +16,11 @@
 struct ax_op {
   int lx = 0, nelv = 0;
   const double *dx = nullptr, *dxt = nullptr, *h1 = nullptr, *g[6] = {};
-  ax::df::dd2 *gp = nullptr;  // prepared geometry (owned), or null
-  double *hb = nullptr;       // h2 .* B of the Helmholtz form (owned), or null
+  ax::df::dd2 *gp = nullptr;    // prepared geometry (owned), or null
+  ax::df::dd2 *coef = nullptr;  // staged half-size coefficients of D, D^T (owned)
+  int *err = nullptr;           // device word: a staged copy never arrived (owned)
+  int dfield = 0;               // exponent field of the matrices' largest entry
+  double *hb = nullptr;         // h2 .* B of the Helmholtz form (owned), or null
 };
 
 namespace {
@@ -30,12 +34,23 @@ __global__ void hb_kernel(double *__restrict__ hb, const double *__restrict__ h2
 
 namespace {
 
-// measured on GB300: the prepared even-odd kernel is the fastest fp64 form
-// for these orders
-bool op_prepares(int lx) { return lx == 6 || lx == 8 || lx == 10 || lx == 12; }
+// measured on GB300: the persistent even-odd kernel on prepared geometry is
+// the fastest fp64 form for these orders
+bool op_prepares(int lx) { return ax::eop_supported(lx); }
 
-ax::guard::RawGeo raw_geo(const ax_op *op) {
-  return ax::guard::RawGeo{op->h1, op->g[0], op->g[1], op->g[2], op->g[3], op->g[4], op->g[5]};
+ax::EopArgs eop_args(const ax_op *op, double *w, const double *u) {
+  ax::EopArgs a;
+  a.w = w;
+  a.u = u;
+  a.coef = op->coef;
+  a.gp = op->gp;
+  a.raw = ax::guard::RawGeo{op->h1, op->g[0], op->g[1], op->g[2], op->g[3], op->g[4], op->g[5]};
+  a.dx = op->dx;
+  a.dxt = op->dxt;
+  a.dfield = op->dfield;
+  a.nelv = op->nelv;
+  a.err = op->err;
+  return a;
 }
 
 }  // namespace
@@ -43,6 +58,8 @@ ax::guard::RawGeo raw_geo(const ax_op *op) {
 extern "C" int ax_op_destroy(ax_op *op) {
   if (!op) return AX_EINVAL;
   if (op->gp) cudaFree(op->gp);
+  if (op->coef) cudaFree(op->coef);
+  if (op->err) cudaFree(op->err);
   if (op->hb) cudaFree(op->hb);
   delete op;
   return AX_OK;
@@ -65,20 +82,44 @@ extern "C" int ax_op_create(ax_op **out, int lx, int nelv, const double *dx, con
   op->h1 = h1;
   const double *gg[6] = {g11, g22, g33, g12, g13, g23};
   for (int k = 0; k < 6; ++k) op->g[k] = gg[k];
+  cudaStream_t st = (cudaStream_t)stream;
   if (op_prepares(lx) && nelv > 0) {
-    const size_t bytes = ax::eo_prep_bytes(lx, nelv);
-    if (cudaMalloc((void **)&op->gp, bytes) != cudaSuccess) {
+    // the even-odd split reads half the rows of dx and dxt: check them here,
+    // once; matrices without the symmetry keep ax_helm's path
+    std::vector<double> dh((size_t)lx * lx), dth((size_t)lx * lx);
+    std::vector<unsigned char> cb(ax::eop_coef_bytes(lx));
+    if (cudaMemcpyAsync(dh.data(), dx, dh.size() * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(dth.data(), dxt, dth.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
       (void)cudaGetLastError();
       delete op;
-      return AX_ENOMEM;
+      return AX_ELAUNCH;
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    int rc = ax::dispatch_eo_prepare(lx, op->gp, h1, g11, g22, g33, g12, g13, g23, nelv, 0x7F,
-                                     st);
-    if (rc == AX_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = AX_ELAUNCH;
-    if (rc) {
-      ax_op_destroy(op);
-      return rc;
+    if (ax::eop_coefficients(lx, dh.data(), dth.data(), cb.data(), &op->dfield)) {
+      if (cudaMalloc((void **)&op->gp, ax::eo_prep_bytes(lx, nelv)) != cudaSuccess ||
+          cudaMalloc((void **)&op->coef, cb.size()) != cudaSuccess ||
+          cudaMalloc((void **)&op->err, sizeof(int)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        ax_op_destroy(op);
+        return AX_ENOMEM;
+      }
+      int rc = AX_OK;
+      if (cudaMemcpyAsync(op->coef, cb.data(), cb.size(), cudaMemcpyHostToDevice, st) !=
+              cudaSuccess ||
+          cudaMemsetAsync(op->err, 0, sizeof(int), st) != cudaSuccess)
+        rc = AX_ELAUNCH;
+      if (rc == AX_OK)
+        rc = ax::eop_prepare(lx, op->gp,
+                             ax::guard::RawGeo{h1, g11, g22, g33, g12, g13, g23}, nelv, 0x7F,
+                             op->dfield, st);
+      if (rc == AX_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = AX_ELAUNCH;
+      if (rc) {
+        (void)cudaGetLastError();
+        ax_op_destroy(op);
+        return rc;
+      }
     }
   }
   *out = op;
@@ -90,8 +131,8 @@ extern "C" int ax_op_set_h1(ax_op *op, const double *h1, void *stream) {
   op->h1 = h1;
   if (!op->gp) return AX_OK;
   const double *const *g = op->g;
-  return ax::dispatch_eo_prepare(op->lx, op->gp, h1, g[0], g[1], g[2], g[3], g[4], g[5],
-                                 op->nelv, 0x40, (cudaStream_t)stream);
+  return ax::eop_prepare(op->lx, op->gp, ax::guard::RawGeo{h1, g[0], g[1], g[2], g[3], g[4], g[5]},
+                         op->nelv, 0x40, op->dfield, (cudaStream_t)stream);
 }
 
 extern "C" int ax_op_set_h2(ax_op *op, const double *h2, const double *B, void *stream) {
@@ -118,8 +159,7 @@ extern "C" int ax_op_apply(ax_op *op, double *w, const double *u, void *stream) 
   if (op->nelv == 0) return AX_OK;
   int rc;
   if (op->gp) {
-    rc = ax::dispatch_df64eo_prep(op->lx, w, u, op->dx, op->dxt, op->gp, raw_geo(op), op->nelv,
-                                  0, (cudaStream_t)stream);
+    rc = ax::eop_launch(op->lx, eop_args(op, w, u), (cudaStream_t)stream);
   } else {
     const double *const *g = op->g;
     rc = ax_helm(w, u, op->dx, op->dxt, op->h1, g[0], g[1], g[2], g[3], g[4], g[5], op->lx,
@@ -133,21 +173,29 @@ extern "C" int ax_op_apply(ax_op *op, double *w, const double *u, void *stream) 
 namespace ax {
 
 int op_dot_blocks(const ax_op *op) {
-  return op && op->gp ? df64eo_prep_blocks(op->lx, op->nelv) : 0;
+  return op && op->gp ? eop_blocks(op->lx, op->nelv, true) : 0;
 }
 
 int op_apply_dot(ax_op *op, double *w, const double *u, double *partials, cudaStream_t st) {
   if (!op || !op->gp || !partials) return AX_EINVAL;
-  return dispatch_df64eo_prep(op->lx, w, u, op->dx, op->dxt, op->gp, raw_geo(op), op->nelv, 0, st,
-                              partials);
+  EopArgs a = eop_args(op, w, u);
+  a.dotp = partials;
+  return eop_launch(op->lx, a, st);
 }
 
 int op_update_apply_dot(ax_op *op, double *w, double *p, const double *r, const double *minv,
                         const double *beta, double *partials, cudaStream_t st,
                         const double *corr, const int *use_corr) {
   if (!op || !op->gp || !partials || !p || !r || !minv || !beta) return AX_EINVAL;
-  return dispatch_df64eo_prep(op->lx, w, nullptr, op->dx, op->dxt, op->gp, raw_geo(op), op->nelv,
-                              0, st, partials, p, r, minv, beta, corr, use_corr);
+  EopArgs a = eop_args(op, w, nullptr);
+  a.dotp = partials;
+  a.pw = p;
+  a.r = r;
+  a.minv = minv;
+  a.beta = beta;
+  a.corr = corr;
+  a.use_corr = use_corr;
+  return eop_launch(op->lx, a, st);
 }
 
 }  // namespace ax
@@ -156,6 +204,19 @@ extern "C" int ax_op_info(const ax_op *op, int *prepared, int64_t *device_bytes)
   if (!op) return AX_EINVAL;
   if (prepared) *prepared = op->gp != nullptr;
   if (device_bytes)
-    *device_bytes = op->gp ? (int64_t)ax::eo_prep_bytes(op->lx, op->nelv) : 0;
+    *device_bytes = op->gp ? (int64_t)(ax::eo_prep_bytes(op->lx, op->nelv) +
+                                       ax::eop_coef_bytes(op->lx) + sizeof(int))
+                           : 0;
+  return AX_OK;
+}
+
+extern "C" int ax_op_error(const ax_op *op, int *flag) {
+  if (!op || !flag) return AX_EINVAL;
+  *flag = 0;
+  if (!op->err) return AX_OK;
+  if (cudaMemcpy(flag, op->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return AX_ELAUNCH;
+  }
   return AX_OK;
 }

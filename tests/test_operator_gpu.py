@@ -43,7 +43,12 @@ def test_prepared_parity_and_agreement_with_on_the_fly(lx, dims):
     case = operator_case(dims, lx, seed=70 + lx)
     op, t = _op(case)
     info = op.info()
-    assert info["prepared"] and info["device_bytes"] == (56 * lx ** 3 + 8) * case["u"].shape[0]
+    # geometry pairs and two exponent records per element, the coefficient block
+    # (rows of lx/2 + 1 pairs, then lx/2 negated heads per row, for D and D^T),
+    # the error word
+    h = lx // 2
+    assert info["prepared"] and info["device_bytes"] == (
+        (56 * lx ** 3 + 8) * case["u"].shape[0] + 32 * h * (h + 1) + 16 * h * h + 4)
     w = torch.full_like(t["u"], float("nan"))
     op.apply(w, t["u"])
     w2 = torch.full_like(t["u"], float("nan"))
@@ -54,6 +59,7 @@ def test_prepared_parity_and_agreement_with_on_the_fly(lx, dims):
     assert rel_l2(got, case["w"]) <= 1e-12
     assert np.abs(got - case["w"]).max() <= 1e-11 * np.abs(case["w"]).max()
     assert rel_l2(got, w2.cpu().numpy()) <= 1e-13
+    assert op.error() == 0
 
 
 @pytest.mark.parametrize("lx", [2, 5, 7, 13])
