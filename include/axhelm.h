@@ -403,8 +403,9 @@ int ax_mlp_forward(const ax_mlp *M, const float *r, const float *minv, const flo
  * Batched operator over many independent meshes of uneven size and mixed
  * lx in one persistent launch.  The paper applies Listing 2 to one mesh per
  * launch and Neko picks its kernel variant by run-time timing (Sec.
- * "Methodology"); the plan below generalises both: work items of tuned
- * elements-per-block, statically balanced across persistent blocks.
+ * "Methodology"); the plan below generalises both: one kernel per dtype
+ * whose CTAs walk statically balanced work items, grouped by lx and thread
+ * layout, with each group run by the single-mesh body of that layout.
  * ------------------------------------------------------------------------ */
 typedef struct ax_batch ax_batch;
 
@@ -421,12 +422,16 @@ typedef struct {
 
 /* Builds the plan (host array meshes[nmesh], copied; the device arrays are
  * borrowed and must outlive the plan).  blocks_per_sm <= 0 picks the
- * default residency.  Allocates the device work list; synchronises stream.
- * Uses the tuned elements-per-block of each lx (ax_tune_*), else a default.
- * For AX_BATCH_F64 meshes with lx in {8, 10, 12} the plan also keeps a copy
- * of h1 and G prepared for the even-odd kernel (56 lx^3 bytes per element,
- * as ax_op_create; results equal ax_op_apply's bit for bit); a change of
- * those meshes' h1 or G needs a new plan. */
+ * kernel's full residency.  Allocates the device work list; synchronises
+ * stream.  Thread layout per mesh: for AX_BATCH_F64 meshes with lx in
+ * {6, 8, 10} the persistent even-odd body of the operator handle,
+ * unless the variant table (ax_tune_variant_*) records a k-loop variant for
+ * that lx or the mesh's dx / dxt are not centro-antisymmetric; the plan then
+ * keeps h1 and G prepared as ax_op_create does (56 lx^3 + 8 bytes per
+ * element plus the coefficient block; results equal ax_op_apply's bit for
+ * bit; a change of those meshes' h1 or G needs a new plan).  Every other
+ * mesh runs the k-loop body (double-float or fp32) in chunks of
+ * 256 / lx^2 elements, with the bits of ax_helm / ax_helm_f32. */
 int ax_batch_create(ax_batch **B, int dtype, int nmesh, const ax_batch_mesh *meshes,
                     int blocks_per_sm, void *stream);
 /* All meshes of the plan in one persistent kernel launch (asynchronous). */
@@ -436,14 +441,18 @@ int ax_batch_graph_launch(ax_batch *B, void *stream);
 /* Plan sizes and the algorithmic flops / bytes of one launch. */
 int ax_batch_info(const ax_batch *B, int *nitems, int *nblocks, int64_t *smem_bytes,
                   double *flops, double *bytes);
+/* *flag = 1 if a launch gave up waiting for a staged geometry copy (every
+ * wait is bounded; the output is then incomplete), else 0.  Synchronises
+ * the device. */
+int ax_batch_error(const ax_batch *B, int *flag);
 int ax_batch_destroy(ax_batch *B);
 
 /* Autotuner: elements per block for (dtype, lx), process-wide.  ax_tune_run
  * times every admissible value on the caller's buffers (nelv elements of
  * the given dtype; w is overwritten; reps timed launches each) and records
  * the fastest; ax_tune_set / ax_tune_get read and write the table (0 means
- * the built-in default).  The single-mesh dispatch and ax_batch_create use
- * the table. */
+ * the built-in default).  The single-mesh k-loop dispatch uses the table;
+ * the batched kernel sizes its k-loop chunks to its 256-thread CTAs. */
 int ax_tune_run(int dtype, int lx, int nelv, void *w, const void *u, const void *dx,
                 const void *dxt, const void *h1, const void *g11, const void *g22,
                 const void *g33, const void *g12, const void *g13, const void *g23, int reps,

@@ -527,6 +527,13 @@ class Batch:
         return {"items": a.value, "blocks": b.value, "smem": s.value, "flops": f.value,
                 "bytes": y.value}
 
+    def error(self) -> int:
+        """1 if a launch gave up waiting for a staged geometry copy (synchronises)."""
+        import ctypes
+        f = ctypes.c_int()
+        check("ax_batch_error", lib().ax_batch_error(self._h, ctypes.addressof(f)))
+        return f.value
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and h.value and _lib._lib is not None:

@@ -52,6 +52,7 @@ PROTOTYPES = {
     "ax_batch_launch": (c_int, [c_void_p, c_void_p]),
     "ax_batch_graph_launch": (c_int, [c_void_p, c_void_p]),
     "ax_batch_info": (c_int, [c_void_p, P, P, P, P, P]),
+    "ax_batch_error": (c_int, [P, P]),
     "ax_batch_destroy": (c_int, [c_void_p]),
     "ax_tune_run": (c_int, [c_int, c_int, c_int] + [P] * 11 + [c_int, P, P, c_void_p]),
     "ax_tune_set": (c_int, [c_int, c_int, c_int]),

@@ -58,10 +58,19 @@ int eop_launch_t(const EopArgs &a, cudaStream_t st) {
   const int g = DOT ? eop_grid_dot<LX>() : eop_grid<LX, DOT, PUPD>();
   if (g <= 0) return AX_ELAUNCH;
   const unsigned grid = (unsigned)std::min<long long>(g, std::max(a.nelv, 1));
-  const unsigned *keys = reinterpret_cast<const unsigned *>(a.gp + (size_t)a.nelv * C::GE);
-  eop::ax_eop_kernel<LX, DOT, PUPD><<<grid, C::NTB, C::SMEM, st>>>(
-      a.w, a.u, a.coef, a.gp, keys, a.raw, a.dx, a.dxt, a.dfield, a.nelv, a.err, a.dotp, a.pw,
-      a.r, a.minv, a.beta, a.corr, a.use_corr);
+  eop::EopMesh m;
+  m.w = a.w;
+  m.u = a.u;
+  m.coef = a.coef;
+  m.gp = a.gp;
+  m.urange = reinterpret_cast<const uint2 *>(a.gp + (size_t)a.nelv * C::GE);
+  m.raw = a.raw;
+  m.dx = a.dx;
+  m.dxt = a.dxt;
+  eop::EopUpd up{a.pw, a.r, a.minv, a.corr, 0.0, false};
+  eop::ax_eop_kernel<LX, DOT, PUPD><<<grid, C::NTB, C::SMEM, st>>>(m, (long long)a.nelv, a.err,
+                                                                  a.dotp, up, a.beta,
+                                                                  a.use_corr);
   return launch_status();
 }
 

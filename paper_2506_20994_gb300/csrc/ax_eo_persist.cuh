@@ -117,24 +117,65 @@ AX_D df::df2 xchg(df::df2 v) {
   return df::df2{__shfl_xor_sync(0xffffffffu, v.hi, 1), __shfl_xor_sync(0xffffffffu, v.lo, 1)};
 }
 
-// DOT: per-CTA partials of u . w (one per CTA, fixed order).  PUPD: u is not
-// an input; phase 1 forms the solver's next direction in place, pw = minv .*
-// r (+ corr when *use_corr) + (*beta) pw (fp64, explicit roundings), and the
-// operator is applied to it.
-template <int LX, bool DOT, bool PUPD>
-__global__ void __launch_bounds__(Cfg<LX>::NTB, Cfg<LX>::MINB)
-ax_eop_kernel(double *__restrict__ w, const double *__restrict__ u,
-              const df::dd2 *__restrict__ coef, const df::dd2 *__restrict__ gp,
-              const unsigned *__restrict__ gkeys, guard::RawGeo raw,
-              const double *__restrict__ dx, const double *__restrict__ dxt, int dfield,
-              int nelv, int *__restrict__ err, double *__restrict__ dotp,
-              double *__restrict__ pw, const double *__restrict__ r_in,
-              const double *__restrict__ minv_in, const double *__restrict__ beta_p,
-              const double *__restrict__ corr_in, const int *__restrict__ use_corr_p) {
+// Operands of one mesh for the persistent body: w = Ax(u), the prepared
+// geometry (gp) and its per-element u exponent ranges, the staged
+// coefficient block, and the fp64 arrays an element falls back to.
+struct EopMesh {
+  double *w;
+  const double *u;
+  const df::dd2 *coef, *gp;
+  const uint2 *urange;
+  guard::RawGeo raw;
+  const double *dx, *dxt;
+};
+
+// Solver operands of the fused direction update (PUPD): pw = minv .* r
+// (+ corr when use_corr) + beta pw, formed in place in front of the apply.
+struct EopUpd {
+  double *pw;
+  const double *r, *minv, *corr;
+  double beta;
+  bool use_corr;
+};
+
+// A position in a body's element sequence: item index and element offset.
+struct EopPos {
+  int it;
+  long long off;
+};
+
+// The operator handle's sequence: elements blockIdx.x, + gridDim.x, ... of
+// one mesh.
+struct SeqOne {
+  const EopMesh *m;
+  long long nelv;
+  AX_D bool first(EopPos &p) const {
+    p = EopPos{0, (long long)blockIdx.x};
+    return p.off < nelv;
+  }
+  AX_D bool advance(const EopPos &p, EopPos &q) const {
+    q = EopPos{0, p.off + (long long)gridDim.x};
+    return q.off < nelv;
+  }
+  AX_D int mesh_of(const EopPos &) const { return 0; }
+  AX_D long long elem(const EopPos &p) const { return p.off; }
+  AX_D const EopMesh &mesh(int) const { return *m; }
+};
+
+// Persistent even-odd body over the element sequence `seq` of one group of
+// NTB threads (`tid` in [0, NTB)) with `sm` its shared memory (Cfg<LX>::SMEM
+// bytes, 128-byte aligned).  sync() / sync_and(p) synchronise exactly that
+// group (the second also ANDs a predicate over it).  DOT: adds this thread's
+// share of u . w to dsum.  PUPD: u is not an input; phase 1 forms the
+// solver's next direction in place (EopUpd), fp64 with explicit roundings,
+// and the operator is applied to it.  err: set to 1 if a staged copy never
+// arrived (the body then stops).
+template <int LX, bool DOT, bool PUPD, class Seq, class Sync, class SyncAnd>
+AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd sync_and,
+                  int *err, const EopUpd &up, double &dsum) {
   using namespace df;
   using C = Cfg<LX>;
   constexpr int H = C::H, N = C::N, H2 = C::H2, NT = C::NT, NW = C::NW, N3 = C::N3;
-  extern __shared__ __align__(128) unsigned char sm[];
   constexpr int CS = C::CS;
   dd2 *cf = reinterpret_cast<dd2 *>(sm);  // [H][CS] (P, M) of D, rows padded
   dd2 *tf = cf + H * CS;                  // [H][CS] (P, M) of D^T
@@ -145,9 +186,7 @@ ax_eop_kernel(double *__restrict__ w, const double *__restrict__ u,
   dd2 *Gs = reinterpret_cast<dd2 *>(sm + C::OFF_G);
   const uint32_t bar = smem_u32(sm + C::OFF_MISC);
   unsigned *kslot = reinterpret_cast<unsigned *>(sm + C::OFF_MISC + 16);
-  double *red = reinterpret_cast<double *>(sm + C::OFF_MISC + 16 + NW * 8);
 
-  const int tid = threadIdx.x;
   const bool real = tid < NT;
   const int t = real ? tid >> 1 : 0, c = tid & 1;
   const int ip = t % H, jp = (t / H) % H, kp = t / H2;
@@ -210,49 +249,58 @@ ax_eop_kernel(double *__restrict__ w, const double *__restrict__ u,
     }
   };
 
-  // ---- set-up: barrier, coefficients, first element's geometry and u
+  auto load_coef = [&](const EopMesh &M) __attribute__((always_inline)) {
+    for (int q = tid; q < (int)(C::COEF_BYTES / 16); q += C::NTB)
+      reinterpret_cast<ulonglong2 *>(sm)[q] =
+          __ldg(reinterpret_cast<const ulonglong2 *>(M.coef) + q);
+  };
+
+  // ---- set-up: barrier, first element's geometry and inputs
   if (tid == 0) mbar_init(bar, 1);
-  for (int q = tid; q < (int)(C::COEF_BYTES / 16); q += blockDim.x)
-    reinterpret_cast<ulonglong2 *>(sm)[q] = __ldg(reinterpret_cast<const ulonglong2 *>(coef) + q);
-  __syncthreads();
-  long long e = blockIdx.x;
-  const long long stride = gridDim.x;
-  if (tid == 0 && e < nelv) bulk_load(smem_u32(Gs), gp + (size_t)e * C::GE, C::GBYTES, bar);
+  EopPos pos;
+  bool have = seq.first(pos);
+  int cmesh = -1;  // mesh whose coefficients are staged
+  sync();
+  if (tid == 0 && have) {
+    const EopMesh &M = seq.mesh(seq.mesh_of(pos));
+    bulk_load(smem_u32(Gs), M.gp + (size_t)seq.elem(pos) * C::GE, C::GBYTES, bar);
+  }
 
   double uv[2][2] = {{0.0, 0.0}, {0.0, 0.0}};      // u (or r) of the element in turn
   double mv[2][2], pv[2][2], qv[2][2];             // PUPD: minv, old direction, corr
-  auto load_in = [&](long long el) __attribute__((always_inline)) {
-    const size_t eb = (size_t)el * N3;
+  auto load_in = [&](const EopPos &p) __attribute__((always_inline)) {
+    const EopMesh &M = seq.mesh(seq.mesh_of(p));
+    const size_t eb = (size_t)seq.elem(p) * N3;
 #pragma unroll
     for (int b = 0; b < 2; ++b)
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         const size_t q = eb + pidx(b, a);
         if constexpr (PUPD) {
-          uv[b][a] = __ldg(r_in + q);
-          mv[b][a] = __ldg(minv_in + q);
-          pv[b][a] = pw[q];
-          qv[b][a] = corr_in ? __ldg(corr_in + q) : 0.0;
+          uv[b][a] = __ldg(up.r + q);
+          mv[b][a] = __ldg(up.minv + q);
+          pv[b][a] = up.pw[q];
+          qv[b][a] = up.corr ? __ldg(up.corr + q) : 0.0;
         } else {
-          uv[b][a] = __ldg(u + q);
+          uv[b][a] = __ldg(M.u + q);
         }
       }
   };
-  if (real && e < nelv) load_in(e);
-  double beta = 0.0;
-  bool use_corr = false;
-  if constexpr (PUPD) {
-    beta = *beta_p;
-    use_corr = corr_in != nullptr && *use_corr_p != 0;
-  }
+  if (real && have) load_in(pos);
 
   uint32_t parity = 0;
-  double dsum = 0.0;
-  for (; e < nelv; e += stride, parity ^= 1u) {
-    const long long nx = e + stride;
-    const size_t eb = (size_t)e * N3;
+  for (; have; parity ^= 1u) {
+    EopPos nxp;
+    const bool more = seq.advance(pos, nxp);
+    const int mi = seq.mesh_of(pos);
+    const EopMesh &M = seq.mesh(mi);
+    const size_t eb = (size_t)seq.elem(pos) * N3;
     // this element's admissible exponent fields of u (guard.cuh, u_range)
-    const uint2 ur_e = __ldg(reinterpret_cast<const uint2 *>(gkeys) + e);
+    const uint2 ur_e = __ldg(M.urange + seq.elem(pos));
+    if (mi != cmesh) {  // group-uniform: the staged coefficients of this mesh
+      load_coef(M);
+      cmesh = mi;
+    }
     // ---- phase 1: this element's u (or the direction formed here), split,
     // lines of the three directions; the next element's inputs start loading
     double ucur[2][2];
@@ -264,9 +312,9 @@ ax_eop_kernel(double *__restrict__ w, const double *__restrict__ u,
         double x = uv[b][a];
         if constexpr (PUPD) {
           double z = __dmul_rn(mv[b][a], x);
-          if (use_corr) z = __dadd_rn(z, qv[b][a]);
-          x = __fma_rn(beta, pv[b][a], z);
-          if (real) pw[eb + pidx(b, a)] = x;
+          if (up.use_corr) z = __dadd_rn(z, qv[b][a]);
+          x = __fma_rn(up.beta, pv[b][a], z);
+          if (real) up.pw[eb + pidx(b, a)] = x;
         }
         ucur[b][a] = x;
         uk = max(uk, guard::key(x));
@@ -276,11 +324,11 @@ ax_eop_kernel(double *__restrict__ w, const double *__restrict__ u,
     for (int b = 0; b < 2; ++b)
 #pragma unroll
       for (int a = 0; a < 2; ++a) v[b][a] = split(ucur[b][a]);
-    if (real && nx < nelv) load_in(nx);
+    if (real && more) load_in(nxp);
     uk = __reduce_max_sync(0xffffffffu, real ? uk : 0u);
     if ((tid & 31) == 0) kslot[tid >> 5] = uk;
     publish(Lb, v, v, v);
-    __syncthreads();
+    sync();
 
     // ---- phase 2: reference gradient
     df2 gr[2][2], gs[2][2], gt[2][2];
@@ -321,8 +369,8 @@ ax_eop_kernel(double *__restrict__ w, const double *__restrict__ u,
       }
     }
     // every thread is done with the geometry and the gradient lines
-    if (!__syncthreads_and(got)) {
-      // a staged copy never completed: record it and stop (CTA-uniform);
+    if (!sync_and(got)) {
+      // a staged copy never completed: record it and stop (group-uniform);
       // the copy may still be in flight, so wait once more, bounded
       if (tid == 0) {
         if (err) atomicExch(err, 1);
@@ -330,9 +378,10 @@ ax_eop_kernel(double *__restrict__ w, const double *__restrict__ u,
       }
       break;
     }
-    if (tid == 0 && nx < nelv) {
+    if (tid == 0 && more) {
       fence_async_smem();
-      bulk_load(smem_u32(Gs), gp + (size_t)nx * C::GE, C::GBYTES, bar);
+      const EopMesh &Mn = seq.mesh(seq.mesh_of(nxp));
+      bulk_load(smem_u32(Gs), Mn.gp + (size_t)seq.elem(nxp) * C::GE, C::GBYTES, bar);
     }
     unsigned uke = 0u;
 #pragma unroll
@@ -341,7 +390,7 @@ ax_eop_kernel(double *__restrict__ w, const double *__restrict__ u,
 
     // ---- phase 4: lines of the weighted gradient
     publish(Lb, gr, gs, gt);
-    __syncthreads();
+    sync();
 
     // ---- phase 5: transposed contractions, summed, stored
     contract_all(Lb, tf, tn, gr, gs, gt);
@@ -353,32 +402,58 @@ ax_eop_kernel(double *__restrict__ w, const double *__restrict__ u,
         acc = dsum2(acc, dd2{pk(gt[b][0].hi, gt[b][1].hi), pk(gt[b][0].lo, gt[b][1].lo)});
         const df2 w0 = norm(lx_(acc.hi), lx_(acc.lo)), w1 = norm(ly_(acc.hi), ly_(acc.lo));
         const double wd0 = join(w0.hi, w0.lo), wd1 = join(w1.hi, w1.lo);
-        w[eb + pidx(b, 0)] = wd0;
-        w[eb + pidx(b, 1)] = wd1;
+        M.w[eb + pidx(b, 0)] = wd0;
+        M.w[eb + pidx(b, 1)] = wd1;
         if constexpr (DOT) {
           dsum = __fma_rn(ucur[b][0], wd0, dsum);
           dsum = __fma_rn(ucur[b][1], wd1, dsum);
         }
       }
     }
-    if (bad) {  // CTA-uniform: fp64 units for this element
-      __syncthreads();  // phase 5 has read the lines that serve as scratch
-      guard::element_f64<LX>(real, w, PUPD ? pw : u, dx, dx, dx, dxt, dxt, dxt, raw.h1, raw.g11,
-                             raw.g22, raw.g33, raw.g12, raw.g13, raw.g23, eb,
-                             reinterpret_cast<double *>(Lb), tid, NT, [] { __syncthreads(); },
-                             DOT ? &dsum : nullptr);
+    if (bad) {  // group-uniform: fp64 units for this element
+      sync();   // phase 5 has read the lines that serve as scratch
+      guard::element_f64<LX>(real, M.w, PUPD ? up.pw : M.u, M.dx, M.dx, M.dx, M.dxt, M.dxt,
+                             M.dxt, M.raw.h1, M.raw.g11, M.raw.g22, M.raw.g33, M.raw.g12,
+                             M.raw.g13, M.raw.g23, eb, reinterpret_cast<double *>(Lb), tid, NT,
+                             sync, DOT ? &dsum : nullptr);
     }
-    __syncthreads();  // the lines and key slots are free for the next element
+    sync();  // the lines and key slots are free for the next element
+    pos = nxp;
+    have = more;
   }
+  if (tid == 0) {  // no copy is pending here: the barrier may be reused as plain memory
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+  }
+}
 
+// The operator handle's kernel: one mesh, elements blockIdx.x + k gridDim.x.
+// DOT: one partial of u . w per CTA (fixed order) in dotp[blockIdx.x].
+template <int LX, bool DOT, bool PUPD>
+__global__ void __launch_bounds__(Cfg<LX>::NTB, Cfg<LX>::MINB)
+ax_eop_kernel(const __grid_constant__ EopMesh mesh, long long nelv, int *__restrict__ err,
+              double *__restrict__ dotp, const __grid_constant__ EopUpd up0,
+              const double *__restrict__ beta_p, const int *__restrict__ use_corr_p) {
+  using C = Cfg<LX>;
+  extern __shared__ __align__(128) unsigned char sm[];
+  EopUpd up = up0;
+  if constexpr (PUPD) {  // solver scalars live on the device
+    up.beta = *beta_p;
+    up.use_corr = up.corr != nullptr && *use_corr_p != 0;
+  }
+  const SeqOne seq{&mesh, nelv};
+  double dsum = 0.0;
+  eop_run<LX, DOT, PUPD>(
+      sm, (int)threadIdx.x, seq, [] { __syncthreads(); },
+      [](bool p) { return __syncthreads_and(p) != 0; }, err, up, dsum);
   if constexpr (DOT) {  // one partial per CTA: fixed shuffle tree, warps in order
+    double *red = reinterpret_cast<double *>(sm + C::OFF_MISC + 16 + C::NW * 8);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
-    if ((tid & 31) == 0) red[tid >> 5] = dsum;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dsum;
     __syncthreads();
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
       double s = 0.0;
-      for (int q = 0; q < NW; ++q) s += red[q];
+      for (int q = 0; q < C::NW; ++q) s += red[q];
       dotp[blockIdx.x] = s;
     }
   }

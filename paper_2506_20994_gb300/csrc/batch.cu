@@ -1,21 +1,20 @@
 // Batched element operator over many independent meshes of uneven size and
-// mixed polynomial order, launched as one persistent kernel per polynomial
-// order present (all recorded into one CUDA graph on first replay), and the
-// autotuner that picks elements per block for each lx.
+// mixed polynomial order in one persistent launch (optionally replayed from a
+// CUDA graph), and the autotuner tables the single-mesh kernels use.
 //
 // The paper's kernel (Listing 2) runs one mesh per launch, and Neko chooses
-// its kernel variant by timing at run time (Sec. "Methodology"); here a
-// host-built plan cuts every mesh into work items of `epb` elements (epb
-// tuned per lx), groups the items by lx, and assigns each group's items
-// longest-processing-time-first (cost ~ elements * lx^4) to a fixed set of
-// persistent blocks sized by the occupancy of that group's kernel.  Blocks
-// walk their own contiguous item list; there are no atomics and no
-// inter-block waits.  Each item runs the same device body as the
-// single-mesh kernel (ax_df64.cuh / ax_df64_eo.cuh / ax_kstep.cuh), so the
-// results are bit-identical to ax_helm / ax_helm_f32, or, for fp64 meshes
-// with lx in {8, 10, 12}, to the operator handle (geometry prepared here).  One kernel per lx
-// (rather than one kernel switching over lx) keeps each kernel's register
-// footprint, and so its occupancy, that of its single-mesh counterpart.
+// its kernel variant by timing at run time (Sec. "Methodology").  Here a
+// host-built plan cuts every mesh into work items, balances them over the
+// persistent CTAs of one kernel per dtype (longest processing time first,
+// cost ~ elements * lx^3 * measured time per point), and gives each CTA its
+// items sorted into groups of
+// one lx and thread layout (batch_kernels.cuh).  The layout of an fp64 mesh
+// is the variant table's (ax_tune_variant_*): the persistent even-odd body
+// for lx in {6, 8, 10} unless the table asks for the k-loop layout or the
+// mesh's matrices are not centro-antisymmetric, the double-float k-loop body
+// otherwise.  Each body is the single-mesh one, so results equal the
+// operator handle's (even-odd meshes) or ax_helm's / ax_helm_f32's bit for
+// bit.  No atomics and no waits between CTAs.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -25,57 +24,38 @@
 #include "batch_kernels.cuh"
 #include "dispatch.h"
 
-namespace ax {
-int batch_lx_launch_f64(int, int, int, size_t, const BatchMeshDev *, const BatchItem *,
-                        const int *, cudaStream_t);
-int batch_lx_launch_f32(int, int, size_t, const BatchMeshDev *, const BatchItem *, const int *,
-                        cudaStream_t);
-int batch_lx_setup_f64(int, int, size_t, int *);
-int batch_lx_setup_f32(int, size_t, int *);
-int batch_lx_launch(bool f64, int lx, int body, int nblocks, size_t smem, const BatchMeshDev *m,
-                    const BatchItem *it, const int *bs, cudaStream_t st) {
-  return f64 ? batch_lx_launch_f64(lx, body, nblocks, smem, m, it, bs, st)
-             : batch_lx_launch_f32(lx, nblocks, smem, m, it, bs, st);
-}
-int batch_lx_setup(bool f64, int lx, int body, size_t smem, int *bps) {
-  return f64 ? batch_lx_setup_f64(lx, body, smem, bps) : batch_lx_setup_f32(lx, smem, bps);
-}
-}  // namespace ax
-
 namespace {
 
+using ax::BatchGroup;
 using ax::BatchItem;
 using ax::BatchMeshDev;
 using ax::kBatchThreads;
 constexpr int kBatchLxMin = 2, kBatchLxMax = 12;
 
-size_t body_smem(bool f64, int lx, int body, int epb) {
-  const size_t n2 = (size_t)lx * lx, n3 = n2 * lx;
-  if (f64 && body == ax::kBodyEvenOdd) {
-    const size_t h = lx / 2;
-    return 2 * h * h * 24 + (size_t)epb * 3 * n2 * (h + 1) * 16;
-  }
-  return (2 * n2 + (size_t)epb * 3 * n3) * (f64 ? 8 : 4);
-}
-
-int default_epb(int lx) { return std::max(1, kBatchThreads / (lx * lx)); }
-
-// Thread layout of the fp64 kernel for lx: the variant the tuner recorded
-// (ax_tune_variant_run; either k-loop variant runs the double-float k-loop
-// body here), else ax_helm's built-in choice.
+// Layout of an fp64 mesh of order lx from the variant table (before the
+// symmetry check of its matrices).
 int choose_body(int lx) {
   int v = 0;
   if (ax_tune_variant_get(lx, &v) != AX_OK) v = 0;
-  if (v == AX_VARIANT_F64_DF_EO && ax::batch_eo_ok(lx)) return ax::kBodyEvenOdd;
   if (v == AX_VARIANT_F64_DF || v == AX_VARIANT_F64_NATIVE) return ax::kBodyKLoop;
-  return ax::batch_uses_eo(lx) ? ax::kBodyEvenOdd : ax::kBodyKLoop;
+  return ax::batch_eo_ok(lx) ? ax::kBodyEvenOdd : ax::kBodyKLoop;
 }
 
-struct Group {
-  int lx = 0, body = 0, nblocks = 0;
-  size_t smem = 0;
-  int item_off = 0, start_off = 0;  // into d_items / d_start
-};
+// Cost of one element in a batch CTA for balancing: lx^3 times the time per
+// point of its body, in ns (measured on GB300 on the uneven benchmark batch,
+// one order at a time; other orders take the nearest body's rate).  A model
+// proportional to the flops (lx^4) balanced the mixed batch 14 % worse: the
+// even-odd body is most efficient per point at lx = 8.
+double elem_cost(int lx, bool f64, bool eo) {
+  double ns;
+  if (f64 && eo)
+    ns = lx == 6 ? 10.8 : lx == 8 ? 7.2 : 8.6;
+  else if (f64)
+    ns = 13.0;
+  else
+    ns = lx <= 5 ? 5.5 : lx == 6 ? 4.7 : lx <= 9 ? 3.8 : 5.4;
+  return (double)lx * lx * lx * ns;
+}
 
 }  // namespace
 
@@ -91,13 +71,15 @@ int tuned_epb(int dtype, int lx) {
 
 struct ax_batch {
   int dtype = 0;
-  int nmesh = 0, nitems = 0, nblocks = 0;
+  int nmesh = 0, nitems = 0, nblocks = 0, ngroups = 0;
   size_t smem = 0;
-  std::vector<Group> groups;
   BatchMeshDev *d_mesh = nullptr;
-  std::vector<void *> prepared;  // owned prepared geometry of even-odd fp64 meshes
+  ax::eop::EopMesh *d_emesh = nullptr;
   BatchItem *d_items = nullptr;
+  BatchGroup *d_groups = nullptr;
   int *d_start = nullptr;
+  int *d_err = nullptr;
+  std::vector<void *> owned;  // prepared geometry and coefficients of even-odd meshes
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   double flops = 0, bytes = 0;
@@ -106,13 +88,20 @@ struct ax_batch {
 namespace {
 
 int batch_launch_raw(ax_batch *B, cudaStream_t st) {
-  const bool f64 = B->dtype == AX_BATCH_F64;
-  for (const Group &g : B->groups) {
-    int rc = ax::batch_lx_launch(f64, g.lx, g.body, g.nblocks, g.smem, B->d_mesh,
-                                 B->d_items + g.item_off, B->d_start + g.start_off, st);
-    if (rc) return rc;
-  }
-  return AX_OK;
+  if (B->nblocks == 0) return AX_OK;
+  if (B->dtype == AX_BATCH_F64)
+    return ax::batch_launch_f64(B->nblocks, B->smem, B->d_mesh, B->d_emesh, B->d_items,
+                                B->d_groups, B->d_start, B->d_err, st);
+  return ax::batch_launch_f32(B->nblocks, B->smem, B->d_mesh, B->d_items, B->d_groups,
+                              B->d_start, st);
+}
+
+template <typename T>
+bool upload(T **dst, const std::vector<T> &src, cudaStream_t st) {
+  if (cudaMalloc((void **)dst, std::max<size_t>(1, src.size()) * sizeof(T)) != cudaSuccess)
+    return false;
+  return src.empty() || cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T),
+                                        cudaMemcpyHostToDevice, st) == cudaSuccess;
 }
 
 }  // namespace
@@ -124,9 +113,12 @@ int ax_batch_destroy(ax_batch *B) {
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
   cudaFree(B->d_mesh);
+  cudaFree(B->d_emesh);
   cudaFree(B->d_items);
+  cudaFree(B->d_groups);
   cudaFree(B->d_start);
-  for (void *q : B->prepared) cudaFree(q);
+  cudaFree(B->d_err);
+  for (void *q : B->owned) cudaFree(q);
   delete B;
   return AX_OK;
 }
@@ -138,148 +130,165 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
     return AX_EINVAL;
   *out = nullptr;
   const bool f64 = dtype == AX_BATCH_F64;
-  std::vector<BatchMeshDev> mh(nmesh);
-  std::vector<int> mbody(nmesh, ax::kBodyKLoop);
-  // per (lx, layout): key = 2 lx + layout
-  const int nkey = 2 * (kBatchLxMax + 1);
-  std::vector<std::vector<BatchItem>> items(nkey);
-  std::vector<std::vector<double>> cost(nkey);
-  std::vector<size_t> smem(nkey, 0);
-  double flops = 0, bytes = 0;
   for (int m = 0; m < nmesh; ++m) {
     const ax_batch_mesh &s = meshes[m];
     if (s.lx < kBatchLxMin || s.lx > kBatchLxMax || s.nelv < 0) return AX_EINVAL;
     if (s.nelv > 0 && !ax::all_nonnull(s.w, s.u, s.dx, s.dxt, s.h1, s.g11, s.g22, s.g33, s.g12,
                                        s.g13, s.g23))
       return AX_EINVAL;
-    int epb;
-    const int body = f64 ? choose_body(s.lx) : ax::kBodyKLoop;
-    mbody[m] = body;
-    const int key = 2 * s.lx + body;
-    if (body == ax::kBodyEvenOdd) {
-      // even-odd body: (lx/2)^3 threads per element
-      const int h = s.lx / 2;
-      epb = std::max(1, kBatchThreads / (h * h * h));
-    } else {
-      epb = ax::tuned_epb(dtype, s.lx);
-      if (epb <= 0) epb = default_epb(s.lx);
-      epb = std::min(epb, kBatchThreads / (s.lx * s.lx));
-    }
-    mh[m] = BatchMeshDev{s.lx, epb, s.w, s.u, s.dx, s.dxt, s.h1,
-                         {s.g11, s.g22, s.g33, s.g12, s.g13, s.g23}, nullptr};
-    smem[key] = std::max(smem[key], body_smem(f64, s.lx, body, epb));
-    const double l = s.lx, l3 = l * l * l;
-    for (long long e = 0; e < s.nelv; e += epb) {
-      const int nel = (int)std::min<long long>(epb, s.nelv - e);
-      items[key].push_back(BatchItem{m, nel, e});
-      cost[key].push_back(nel * (l3 * l + 2.0 * l3));
-    }
-    flops += (double)s.nelv * (12.0 * l3 * l + 18.0 * l3);
-    bytes += (double)s.nelv * 9.0 * l3 * (f64 ? 8 : 4);
-  }
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  std::vector<Group> groups;
-  std::vector<BatchItem> flat;
-  std::vector<int> start;
-  size_t smem_max = 0;
-  for (int key = 2 * kBatchLxMin; key < nkey; ++key) {
-    if (items[key].empty()) continue;
-    const int lx = key / 2, body = key % 2;
-    int bps = 0;
-    int rc = ax::batch_lx_setup(f64, lx, body, smem[key], &bps);
-    if (rc) return rc;
-    if (bps < 1) return AX_EINVAL;
-    if (blocks_per_sm > 0) bps = std::min(bps, blocks_per_sm);
-    const int nb = std::max(1, std::min<int>(nsm * bps, (int)items[key].size()));
-    // longest processing time first onto the least-loaded block
-    std::vector<int> order(items[key].size());
-    for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return cost[key][a] > cost[key][b]; });
-    using Load = std::pair<double, int>;
-    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-    for (int b = 0; b < nb; ++b) heap.push({0.0, b});
-    std::vector<std::vector<int>> per(nb);
-    for (int q : order) {
-      Load ld = heap.top();
-      heap.pop();
-      per[ld.second].push_back(q);
-      heap.push({ld.first + cost[key][q], ld.second});
-    }
-    Group g;
-    g.lx = lx;
-    g.body = body;
-    g.nblocks = nb;
-    g.smem = smem[key];
-    g.item_off = (int)flat.size();
-    g.start_off = (int)start.size();
-    int cnt = 0;
-    for (int b = 0; b < nb; ++b) {
-      std::sort(per[b].begin(), per[b].end());  // memory order inside a block
-      start.push_back(cnt);
-      for (int q : per[b]) flat.push_back(items[key][q]), ++cnt;
-    }
-    start.push_back(cnt);
-    groups.push_back(g);
-    smem_max = std::max(smem_max, g.smem);
   }
   ax_batch *B = new (std::nothrow) ax_batch();
   if (!B) return AX_ENOMEM;
   cudaStream_t st = (cudaStream_t)stream;
-  // fp64 meshes of the even-odd orders: prepare their geometry once
-  for (int m = 0; f64 && m < nmesh; ++m) {
+  auto fail = [&](int rc) {
+    (void)cudaGetLastError();
+    ax_batch_destroy(B);
+    return rc;
+  };
+  std::vector<BatchMeshDev> mh(nmesh);
+  std::vector<ax::eop::EopMesh> em(nmesh);
+  std::vector<int> mbody(nmesh, ax::kBodyKLoop);
+  double flops = 0, bytes = 0, total_cost = 0;
+  for (int m = 0; m < nmesh; ++m) {
     const ax_batch_mesh &s = meshes[m];
-    if (mbody[m] != ax::kBodyEvenOdd || s.nelv == 0) continue;
-    void *gp = nullptr;
-    if (cudaMalloc(&gp, ax::eo_prep_bytes(s.lx, s.nelv)) != cudaSuccess) {
-      (void)cudaGetLastError();
-      ax_batch_destroy(B);
-      return AX_ENOMEM;
-    }
-    B->prepared.push_back(gp);
+    mh[m] = BatchMeshDev{s.lx, s.w, s.u, s.dx, s.dxt, s.h1,
+                         {s.g11, s.g22, s.g33, s.g12, s.g13, s.g23}};
+    em[m] = ax::eop::EopMesh{};
+    const double l3 = (double)s.lx * s.lx * s.lx;
+    flops += (double)s.nelv * (12.0 * l3 * s.lx + 18.0 * l3);
+    bytes += (double)s.nelv * 9.0 * l3 * (f64 ? 8 : 4);
+    if (!f64 || s.nelv == 0 || choose_body(s.lx) != ax::kBodyEvenOdd) continue;
+    // even-odd layout: the matrices must be centro-antisymmetric; geometry and
+    // coefficients are prepared here, once, as the operator handle does
+    const int lx = s.lx;
+    std::vector<double> dh((size_t)lx * lx), dth((size_t)lx * lx);
+    std::vector<unsigned char> cb(ax::eop_coef_bytes(lx));
+    if (cudaMemcpyAsync(dh.data(), s.dx, dh.size() * 8, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(dth.data(), s.dxt, dth.size() * 8, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return fail(AX_ELAUNCH);
+    int dfield = 0;
+    if (!ax::eop_coefficients(lx, dh.data(), dth.data(), cb.data(), &dfield)) continue;
+    void *gp = nullptr, *cf = nullptr;
+    if (cudaMalloc(&gp, ax::eo_prep_bytes(lx, s.nelv)) != cudaSuccess) return fail(AX_ENOMEM);
+    B->owned.push_back(gp);
+    if (cudaMalloc(&cf, cb.size()) != cudaSuccess) return fail(AX_ENOMEM);
+    B->owned.push_back(cf);
+    if (cudaMemcpyAsync(cf, cb.data(), cb.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return fail(AX_ELAUNCH);
     auto d = [](const void *q) { return static_cast<const double *>(q); };
-    int rc = ax::dispatch_eo_prepare(s.lx, static_cast<ax::df::dd2 *>(gp), d(s.h1), d(s.g11),
-                                     d(s.g22), d(s.g33), d(s.g12), d(s.g13), d(s.g23), s.nelv,
-                                     0x7F, st);
-    if (rc) {
-      ax_batch_destroy(B);
-      return rc;
-    }
-    mh[m].gp = static_cast<const ax::df::dd2 *>(gp);
-    mh[m].gstat = reinterpret_cast<const unsigned *>(static_cast<const char *>(gp) +
-                                                     (size_t)s.nelv * 56 * s.lx * s.lx * s.lx);
+    const ax::guard::RawGeo raw{d(s.h1), d(s.g11), d(s.g22), d(s.g33), d(s.g12), d(s.g13),
+                                d(s.g23)};
+    int rc = ax::eop_prepare(lx, static_cast<ax::df::dd2 *>(gp), raw, s.nelv, 0x7F, dfield, st);
+    if (rc) return fail(rc);
+    ax::eop::EopMesh &e = em[m];
+    e.w = static_cast<double *>(s.w);
+    e.u = d(s.u);
+    e.coef = static_cast<const ax::df::dd2 *>(cf);
+    e.gp = static_cast<const ax::df::dd2 *>(gp);
+    e.urange = reinterpret_cast<const uint2 *>(static_cast<const char *>(gp) +
+                                               (size_t)s.nelv * 56 * lx * lx * lx);
+    e.raw = raw;
+    e.dx = d(s.dx);
+    e.dxt = d(s.dxt);
+    mbody[m] = ax::kBodyEvenOdd;
   }
+  for (int m = 0; m < nmesh; ++m)
+    total_cost += meshes[m].nelv * elem_cost(meshes[m].lx, f64, mbody[m] == ax::kBodyEvenOdd);
+  // shared memory of the kernel: the largest group layout present
+  size_t smem = 0;
+  for (int m = 0; m < nmesh; ++m) {
+    if (meshes[m].nelv == 0) continue;
+    const int key = 2 * meshes[m].lx + mbody[m];
+    smem = std::max(smem, f64 ? ax::batch_key_smem_f64(key) : ax::batch_key_smem_f32(key));
+  }
+  int dev = 0, nsm = 0, bps = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(AX_ELAUNCH);
+  if (smem > 0) {
+    int rc = f64 ? ax::batch_setup_f64(smem, &bps) : ax::batch_setup_f32(smem, &bps);
+    if (rc) return fail(rc);
+    if (bps < 1) return fail(AX_EINVAL);
+    if (blocks_per_sm > 0) bps = std::min(bps, blocks_per_sm);
+  }
+  const int ncta = smem > 0 ? nsm * bps : 0;
+  // work items: about 8 per CTA of equal cost, k-loop items whole chunks
+  std::vector<BatchItem> items;
+  std::vector<double> cost;
+  const double target = ncta > 0 ? total_cost / (8.0 * ncta) : 1.0;
+  for (int m = 0; m < nmesh; ++m) {
+    const ax_batch_mesh &s = meshes[m];
+    if (s.nelv == 0) continue;
+    const double c = elem_cost(s.lx, f64, mbody[m] == ax::kBodyEvenOdd);
+    long long chunk = std::max<long long>(1, (long long)(target / c));
+    if (mbody[m] == ax::kBodyKLoop) {
+      const int epb = ax::batch_kloop_epb(s.lx);
+      chunk = (chunk + epb - 1) / epb * epb;
+    }
+    for (long long e = 0; e < s.nelv; e += chunk) {
+      const int nel = (int)std::min<long long>(chunk, s.nelv - e);
+      items.push_back(BatchItem{m, nel, e});
+      cost.push_back(nel * c);
+    }
+  }
+  // longest processing time first onto the least-loaded CTA
+  std::vector<std::vector<int>> per(std::max(ncta, 1));
+  {
+    std::vector<int> order(items.size());
+    for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    using Load = std::pair<double, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int b = 0; b < ncta; ++b) heap.push({0.0, b});
+    for (int q : order) {
+      Load ld = heap.top();
+      heap.pop();
+      per[ld.second].push_back(q);
+      heap.push({ld.first + cost[q], ld.second});
+    }
+  }
+  // per CTA: items sorted by (layout key, mesh, first element), then groups
+  std::vector<BatchItem> flat;
+  std::vector<BatchGroup> groups;
+  std::vector<int> start;
+  auto key_of = [&](const BatchItem &it) { return 2 * meshes[it.mesh].lx + mbody[it.mesh]; };
+  for (int b = 0; b < ncta; ++b) {
+    std::vector<BatchItem> mine;
+    for (int q : per[b]) mine.push_back(items[q]);
+    std::sort(mine.begin(), mine.end(), [&](const BatchItem &x, const BatchItem &y) {
+      const int kx = key_of(x), ky = key_of(y);
+      if (kx != ky) return kx > ky;
+      if (x.mesh != y.mesh) return x.mesh < y.mesh;
+      return x.e0 < y.e0;
+    });
+    start.push_back((int)groups.size());
+    for (const BatchItem &it : mine) {
+      const int k = key_of(it);
+      if (groups.empty() || (int)groups.size() == start.back() || groups.back().key != k)
+        groups.push_back(BatchGroup{k, (int)flat.size(), (int)flat.size()});
+      flat.push_back(it);
+      groups.back().ie = (int)flat.size();
+    }
+  }
+  start.push_back((int)groups.size());
   B->dtype = dtype;
   B->nmesh = nmesh;
   B->nitems = (int)flat.size();
-  B->groups = groups;
-  for (const Group &g : groups) B->nblocks += g.nblocks;
-  B->smem = smem_max;
+  B->nblocks = ncta;
+  B->ngroups = (int)groups.size();
+  B->smem = smem;
   B->flops = flops;
   B->bytes = bytes;
-  bool ok = cudaMalloc(&B->d_mesh, std::max<size_t>(1, mh.size()) * sizeof(BatchMeshDev)) ==
-                cudaSuccess &&
-            cudaMalloc(&B->d_items, std::max<size_t>(1, flat.size()) * sizeof(BatchItem)) ==
-                cudaSuccess &&
-            cudaMalloc(&B->d_start, std::max<size_t>(1, start.size()) * sizeof(int)) ==
-                cudaSuccess;
-  if (ok && !mh.empty())
-    ok = cudaMemcpyAsync(B->d_mesh, mh.data(), mh.size() * sizeof(BatchMeshDev),
-                         cudaMemcpyHostToDevice, st) == cudaSuccess;
-  if (ok && !flat.empty())
-    ok = cudaMemcpyAsync(B->d_items, flat.data(), flat.size() * sizeof(BatchItem),
-                         cudaMemcpyHostToDevice, st) == cudaSuccess;
-  if (ok && !start.empty())
-    ok = cudaMemcpyAsync(B->d_start, start.data(), start.size() * sizeof(int),
-                         cudaMemcpyHostToDevice, st) == cudaSuccess;
-  if (ok) ok = cudaStreamSynchronize(st) == cudaSuccess;
-  if (!ok) {
-    (void)cudaGetLastError();
-    ax_batch_destroy(B);
-    return AX_ENOMEM;
-  }
+  bool ok = upload(&B->d_mesh, mh, st) && upload(&B->d_emesh, em, st) &&
+            upload(&B->d_items, flat, st) && upload(&B->d_groups, groups, st) &&
+            upload(&B->d_start, start, st) &&
+            cudaMalloc((void **)&B->d_err, sizeof(int)) == cudaSuccess &&
+            cudaMemsetAsync(B->d_err, 0, sizeof(int), st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess;
+  if (!ok) return fail(AX_ENOMEM);
   *out = B;
   return AX_OK;
 }
@@ -327,6 +336,17 @@ int ax_batch_info(const ax_batch *B, int *nitems, int *nblocks, int64_t *smem_by
   if (smem_bytes) *smem_bytes = (int64_t)B->smem;
   if (flops) *flops = B->flops;
   if (bytes) *bytes = B->bytes;
+  return AX_OK;
+}
+
+int ax_batch_error(const ax_batch *B, int *flag) {
+  if (!B || !flag) return AX_EINVAL;
+  *flag = 0;
+  if (!B->d_err) return AX_OK;
+  if (cudaMemcpy(flag, B->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return AX_ELAUNCH;
+  }
   return AX_OK;
 }
 

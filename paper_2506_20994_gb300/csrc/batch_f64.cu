@@ -1,69 +1,82 @@
-// Persistent batched kernels for the f64 dtype, one per lx in [2, 12].
+// The batched operator's persistent kernel for fp64 meshes (batch_kernels.cuh):
+// the even-odd body for lx 6, 8, 10, the double-float k-loop body for every
+// lx in [2, 12].
 #include "batch_kernels.cuh"
 
 namespace ax {
 
-namespace {
-template <int LX, int BODY>
-int launch_one(int nblocks, size_t smem, const BatchMeshDev *meshes, const BatchItem *items,
-               const int *block_start, cudaStream_t st) {
-  batch_lx_kernel<true, LX, BODY><<<nblocks, kBatchThreads, smem, st>>>(meshes, items,
-                                                                        block_start);
+#define AX_BATCH_LX(M) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12)
+#define AX_BATCH_EO(M) M(6) M(8) M(10)
+
+__global__ void __launch_bounds__(kBatchThreads, 2)
+batch_f64_kernel(const BatchMeshDev *__restrict__ meshes, const eop::EopMesh *__restrict__ emesh,
+                 const BatchItem *__restrict__ items, const BatchGroup *__restrict__ groups,
+                 const int *__restrict__ cta_start, int *__restrict__ err) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int g1 = cta_start[blockIdx.x + 1];
+  for (int g = cta_start[blockIdx.x]; g < g1; ++g) {
+    const BatchGroup G = groups[g];
+    switch (G.key) {
+#define AX_CASE(L)                                      \
+  case 2 * L + kBodyKLoop:                              \
+    batch_run_kloop<true, L>(G, items, meshes, sm);     \
+    break;
+      AX_BATCH_LX(AX_CASE)
+#undef AX_CASE
+#define AX_CASE(L)                                      \
+  case 2 * L + kBodyEvenOdd:                            \
+    batch_run_eo<L>(G, items, emesh, sm, err);          \
+    break;
+      AX_BATCH_EO(AX_CASE)
+#undef AX_CASE
+      default:
+        break;
+    }
+    __syncthreads();  // the next group gives the shared memory another layout
+  }
+}
+
+size_t batch_key_smem_f64(int key) {
+  const int lx = key / 2;
+  if (key % 2 == kBodyEvenOdd) {
+    switch (lx) {
+#define AX_CASE(L) \
+  case L:          \
+    return (size_t)batch_eo_slots<L>() * batch_eo_slot_bytes<L>();
+      AX_BATCH_EO(AX_CASE)
+#undef AX_CASE
+      default:
+        return 0;
+    }
+  }
+  switch (lx) {
+#define AX_CASE(L) \
+  case L:          \
+    return df64_smem<L>(batch_kloop_epb(L));
+    AX_BATCH_LX(AX_CASE)
+#undef AX_CASE
+    default:
+      return 0;
+  }
+}
+
+int batch_launch_f64(int nblocks, size_t smem, const BatchMeshDev *meshes,
+                     const eop::EopMesh *emesh, const BatchItem *items, const BatchGroup *groups,
+                     const int *cta_start, int *err, cudaStream_t st) {
+  batch_f64_kernel<<<nblocks, kBatchThreads, smem, st>>>(meshes, emesh, items, groups, cta_start,
+                                                         err);
   return launch_status();
 }
-template <int LX, int BODY>
-int setup_one(size_t smem, int *bps) {
-  auto k = batch_lx_kernel<true, LX, BODY>;
-  if (smem + kStaticSmemMargin > 48 * 1024 &&
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess) {
-    (void)cudaGetLastError();
-    return AX_EINVAL;
-  }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, kBatchThreads, smem) != cudaSuccess) {
+
+int batch_setup_f64(size_t smem, int *bps) {
+  static std::atomic<size_t> granted[kMaxDevices];
+  if (!grant_smem(batch_f64_kernel, smem, granted)) return AX_EINVAL;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, batch_f64_kernel, kBatchThreads, smem) !=
+      cudaSuccess) {
     (void)cudaGetLastError();
     return AX_ELAUNCH;
   }
   return AX_OK;
-}
-}  // namespace
-
-#define AX_BATCH_LX(M) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12)
-#define AX_BATCH_EO(M) M(4) M(6) M(8) M(10) M(12)
-
-int batch_lx_launch_f64(int lx, int body, int nblocks, size_t smem, const BatchMeshDev *meshes,
-                        const BatchItem *items, const int *block_start, cudaStream_t st) {
-  switch (lx * 2 + (body == kBodyEvenOdd)) {
-#define AX_CASE(L)                                                                   \
-  case 2 * L:                                                                        \
-    return launch_one<L, kBodyKLoop>(nblocks, smem, meshes, items, block_start, st);
-    AX_BATCH_LX(AX_CASE)
-#undef AX_CASE
-#define AX_CASE(L)                                                                     \
-  case 2 * L + 1:                                                                      \
-    return launch_one<L, kBodyEvenOdd>(nblocks, smem, meshes, items, block_start, st);
-    AX_BATCH_EO(AX_CASE)
-#undef AX_CASE
-    default:
-      return AX_EINVAL;
-  }
-}
-
-int batch_lx_setup_f64(int lx, int body, size_t smem, int *bps) {
-  switch (lx * 2 + (body == kBodyEvenOdd)) {
-#define AX_CASE(L) \
-  case 2 * L:      \
-    return setup_one<L, kBodyKLoop>(smem, bps);
-    AX_BATCH_LX(AX_CASE)
-#undef AX_CASE
-#define AX_CASE(L) \
-  case 2 * L + 1:  \
-    return setup_one<L, kBodyEvenOdd>(smem, bps);
-    AX_BATCH_EO(AX_CASE)
-#undef AX_CASE
-    default:
-      return AX_EINVAL;
-  }
 }
 
 }  // namespace ax

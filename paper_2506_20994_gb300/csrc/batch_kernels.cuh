@@ -1,23 +1,39 @@
-// Persistent multi-mesh kernels of the batched operator (batch.cu): one
-// kernel per (dtype, lx), each block walking its own statically assigned
-// list of work items and running the single-mesh device body on each, so
-// that every kernel keeps the register footprint and occupancy of its
-// single-mesh counterpart.  fp64 meshes of the even-odd orders run on
-// geometry the plan prepared once (as the operator handle does).
+// The batched operator's kernels (batch.cu): one persistent kernel per dtype
+// for the whole batch, whatever the polynomial orders in it.
+//
+// Each CTA (kBatchThreads threads) walks its own list of groups; a group is
+// a run of work items (element ranges of meshes) that share one lx and one
+// thread layout, and the CTA runs the matching device body over it:
+//  * fp64, lx in {6, 8, 10} with centro-antisymmetric matrices: the
+//    persistent even-odd body of the operator handle (ax_eo_persist.cuh).
+//    The CTA splits into kBatchThreads / NTB independent slots of NTB
+//    threads, each with its own shared memory, bulk-copy barrier and named
+//    barrier; slot q takes elements q, q + S, ... of the group's
+//    concatenated items and streams the next one's geometry in while it
+//    computes the current one.  The arithmetic is the handle's, so results
+//    equal ax_op_apply's bit for bit.
+//  * every other case: the k-loop body of the single-mesh kernels
+//    (double-float for fp64, fp32 for fp32) in chunks of
+//    kBatchThreads / lx^2 elements, bit for bit ax_helm's / ax_helm_f32's.
+// Groups are separated by a block barrier (the shared memory changes role).
+// No atomics and no waits between CTAs.  CTAs of 256 threads, several per SM,
+// so that one CTA's block barriers (k-loop bodies) leave the others running
+// (measured: one 512-thread CTA per SM was 14-22 % slower on the uneven
+// benchmark batch).
 #pragma once
 
 #include "ax_df64.cuh"
-#include "ax_df64_eo.cuh"
+#include "ax_eo_persist.cuh"
 #include "ax_kstep.cuh"
 
 namespace ax {
 
+constexpr int kBatchThreads = 256;
+
 struct BatchMeshDev {
-  int lx, epb;
+  int lx;
   void *w;
   const void *u, *dx, *dxt, *h1, *g[6];
-  const df::dd2 *gp;  // geometry prepared for the even-odd kernel, or null
-  const unsigned *gstat;  // its per-element exponent keys (guard.cuh)
 };
 
 struct BatchItem {
@@ -25,57 +41,125 @@ struct BatchItem {
   long long e0;
 };
 
-constexpr int kBatchThreads = 256;
+// A group: items [ib, ie) of one body key (2 lx + layout).
+struct BatchGroup {
+  int key, ib, ie;
+};
 
-// Thread layout of a group's kernel: the k-loop body (lx^2 threads per
-// element walking k) or the even-odd body on prepared geometry ((lx/2)^3
-// threads per element, fp64 and even lx only).
+// Thread layout of a group.
 enum BatchBody : int { kBodyKLoop = 0, kBodyEvenOdd = 1 };
 
-// The default fp64 layout (ax_helm's built-in choice) for lx.
-__host__ __device__ constexpr bool batch_uses_eo(int lx) {
-  return lx == 8 || lx == 10 || lx == 12;
-}
-__host__ __device__ constexpr bool batch_eo_ok(int lx) { return lx >= 4 && lx <= 12 && lx % 2 == 0; }
+// Orders whose even-odd body fits a batch CTA (lx 12 needs 432 threads).
+__host__ __device__ constexpr bool batch_eo_ok(int lx) { return lx == 6 || lx == 8 || lx == 10; }
 
-template <bool F64, int LX, int BODY = kBodyKLoop>
-__global__ void __launch_bounds__(kBatchThreads, 2)
-batch_lx_kernel(const BatchMeshDev *__restrict__ meshes, const BatchItem *__restrict__ items,
-                const int *__restrict__ block_start) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int b0 = block_start[blockIdx.x], b1 = block_start[blockIdx.x + 1];
-  for (int it = b0; it < b1; ++it) {
+// Elements per chunk of the k-loop body in a batch CTA.
+__host__ __device__ constexpr int batch_kloop_epb(int lx) {
+  return kBatchThreads / (lx * lx) < 1 ? 1 : kBatchThreads / (lx * lx);
+}
+
+// The even-odd slots' sequence: elements slot, slot + S, ... of the
+// concatenation of items [ib, ie).
+struct SeqItems {
+  const BatchItem *items;
+  int ib, ie, slot, S;
+  const eop::EopMesh *meshes;
+  AX_D bool norm(eop::EopPos &p) const {
+    while (p.it < ie && p.off >= items[p.it].nel) {
+      p.off -= items[p.it].nel;
+      ++p.it;
+    }
+    return p.it < ie;
+  }
+  AX_D bool first(eop::EopPos &p) const {
+    p = eop::EopPos{ib, (long long)slot};
+    return norm(p);
+  }
+  AX_D bool advance(const eop::EopPos &p, eop::EopPos &q) const {
+    q = eop::EopPos{p.it, p.off + S};
+    return norm(q);
+  }
+  AX_D int mesh_of(const eop::EopPos &p) const { return items[p.it].mesh; }
+  AX_D long long elem(const eop::EopPos &p) const { return items[p.it].e0 + p.off; }
+  AX_D const eop::EopMesh &mesh(int m) const { return meshes[m]; }
+};
+
+// Bytes of one even-odd slot's shared memory (128-byte aligned).
+template <int LX>
+constexpr size_t batch_eo_slot_bytes() {
+  return (eop::Cfg<LX>::SMEM + 127) / 128 * 128;
+}
+template <int LX>
+constexpr int batch_eo_slots() {
+  return kBatchThreads / eop::Cfg<LX>::NTB;
+}
+
+template <int LX>
+__device__ __noinline__ void batch_run_eo(const BatchGroup &G, const BatchItem *items,
+                                             const eop::EopMesh *emesh, unsigned char *sm,
+                                             int *err) {
+  using C = eop::Cfg<LX>;
+  constexpr int S = batch_eo_slots<LX>();
+  const int slot = (int)threadIdx.x / C::NTB;
+  if (slot >= S) return;  // threads beyond the last whole slot sit the group out
+  const int tid = (int)threadIdx.x - slot * C::NTB;
+  const unsigned bid = 1u + (unsigned)slot;
+  const SeqItems seq{items, G.ib, G.ie, slot, S, emesh};
+  auto sync = [bid] { asm volatile("bar.sync %0, %1;" ::"r"(bid), "r"(C::NTB) : "memory"); };
+  auto sync_and = [bid](bool p) {
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred a, b;\n\tsetp.ne.u32 a, %1, 0;\n\t"
+        "bar.red.and.pred b, %2, %3, a;\n\tselp.u32 %0, 1, 0, b;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)p), "r"(bid), "r"(C::NTB)
+        : "memory");
+    return r != 0u;
+  };
+  double dsum = 0.0;
+  const eop::EopUpd up{nullptr, nullptr, nullptr, nullptr, 0.0, false};
+  eop::eop_run<LX, false, false>(sm + (size_t)slot * batch_eo_slot_bytes<LX>(), tid, seq, sync,
+                                 sync_and, err, up, dsum);
+}
+
+template <bool F64, int LX>
+__device__ __noinline__ void batch_run_kloop(const BatchGroup &G, const BatchItem *items,
+                                                const BatchMeshDev *meshes, unsigned char *sm) {
+  constexpr int EPB = batch_kloop_epb(LX);
+  for (int it = G.ib; it < G.ie; ++it) {
     const BatchItem itm = items[it];
     const BatchMeshDev m = meshes[itm.mesh];
-    if constexpr (F64 && BODY == kBodyEvenOdd) {
-      // every mesh of this group has prepared geometry (the plan made it)
-      df64eo_body<LX, true>((double *)m.w, (const double *)m.u, (const double *)m.dx,
-                            (const double *)m.dxt, (const double *)m.h1, (const double *)m.g[0],
-                            (const double *)m.g[1], (const double *)m.g[2], (const double *)m.g[3],
-                            (const double *)m.g[4], (const double *)m.g[5], m.gp, m.gstat,
-                            itm.e0, itm.nel, m.epb, smem_raw);
-    } else if constexpr (F64) {
-      df64_body<LX>((double *)m.w, (const double *)m.u, (const double *)m.dx,
-                    (const double *)m.dxt, (const double *)m.h1, (const double *)m.g[0],
-                    (const double *)m.g[1], (const double *)m.g[2], (const double *)m.g[3],
-                    (const double *)m.g[4], (const double *)m.g[5], itm.e0, itm.nel, m.epb,
-                    smem_raw);
-    } else {
-      kstep_body<LX, float, float, float, float>(
-          (float *)m.w, (const float *)m.u, (const float *)m.dx, (const float *)m.dxt,
-          (const float *)m.h1, (const float *)m.g[0], (const float *)m.g[1],
-          (const float *)m.g[2], (const float *)m.g[3], (const float *)m.g[4],
-          (const float *)m.g[5], itm.e0, itm.nel, m.epb, smem_raw);
+    for (int q = 0; q < itm.nel; q += EPB) {
+      const int nel = itm.nel - q < EPB ? itm.nel - q : EPB;
+      if constexpr (F64) {
+        df64_body<LX>((double *)m.w, (const double *)m.u, (const double *)m.dx,
+                      (const double *)m.dxt, (const double *)m.h1, (const double *)m.g[0],
+                      (const double *)m.g[1], (const double *)m.g[2], (const double *)m.g[3],
+                      (const double *)m.g[4], (const double *)m.g[5], itm.e0 + q, nel, EPB, sm);
+      } else {
+        kstep_body<LX, float, float, float, float, true, false, kstep_vec<LX, float>()>(
+            (float *)m.w, (const float *)m.u, (const float *)m.dx, (const float *)m.dxt,
+            (const float *)m.h1, (const float *)m.g[0], (const float *)m.g[1],
+            (const float *)m.g[2], (const float *)m.g[3], (const float *)m.g[4],
+            (const float *)m.g[5], itm.e0 + q, nel, EPB, sm);
+      }
+      __syncthreads();  // the next chunk reuses the shared memory
     }
-    __syncthreads();  // the next item reuses shared memory
   }
 }
 
-// Per-(dtype, lx) host helpers, defined in batch_f64.cu / batch_f32.cu.
-// launch: one persistent launch; setup: sets the shared-memory limit and
-// returns the resident blocks per SM for smem bytes (0 if it does not fit).
-int batch_lx_launch(bool f64, int lx, int nblocks, size_t smem, const BatchMeshDev *meshes,
-                    const BatchItem *items, const int *block_start, cudaStream_t st);
-int batch_lx_setup(bool f64, int lx, size_t smem, int *blocks_per_sm);
+// Per-dtype host helpers, defined in batch_f64.cu / batch_f32.cu: one
+// persistent launch of the dtype's kernel; the shared-memory bytes a group
+// of key (2 lx + layout) needs; the resident CTAs per SM at `smem` bytes
+// (raising the kernel's shared-memory limit first).
+int batch_launch_f64(int nblocks, size_t smem, const BatchMeshDev *meshes,
+                     const eop::EopMesh *emesh, const BatchItem *items, const BatchGroup *groups,
+                     const int *cta_start, int *err, cudaStream_t st);
+int batch_launch_f32(int nblocks, size_t smem, const BatchMeshDev *meshes,
+                     const BatchItem *items, const BatchGroup *groups, const int *cta_start,
+                     cudaStream_t st);
+size_t batch_key_smem_f64(int key);
+size_t batch_key_smem_f32(int key);
+int batch_setup_f64(size_t smem, int *blocks_per_sm);
+int batch_setup_f32(size_t smem, int *blocks_per_sm);
 
 }  // namespace ax

@@ -2,8 +2,11 @@
 
 Uneven meshes of mixed lx in one persistent launch (and its CUDA-graph
 replay) must give, for every mesh, exactly the bits of the single-mesh
-kernel with the same elements per block, and match the oracle within the
-fp64 (1e-12) or fp32 (1e-6) relative L2 tolerance.
+entry point with the same thread layout (the operator handle for fp64 lx 6,
+8, 10; ax_helm / ax_helm_f32 otherwise, lx 12 included), and match the oracle within the
+fp64 (1e-12) or fp32 (1e-6) relative L2 tolerance; at the benchmark's size
+(64 meshes, E log-uniform in [64, 8192], lx in {5, 6, 8, 10}) sampled
+elements of every mesh are checked against the oracle.
 """
 import numpy as np
 import pytest
@@ -62,18 +65,20 @@ def test_batch_matches_oracle_and_single_launch(dtype, graph):
     if graph:  # replay twice more: same bits
         B.launch(graph=True)
     torch.cuda.synchronize()
+    assert B.error() == 0
     tol = 1e-12 if dtype == ax.AX_BATCH_F64 else 1e-6
     for m in meshes:
         w = m["w"].double().cpu().numpy()
         assert rel_l2(w, m["ref"]) <= tol, m["lx"]
-        # the single-mesh kernel with default elements per block (fp64 even-odd
-        # orders: the operator handle on prepared geometry): same bits
+        # the single-mesh entry point of the same layout (fp64 even-odd orders:
+        # the operator handle on prepared geometry): same bits
         w1 = torch.empty_like(m["u"])
-        if dtype == ax.AX_BATCH_F64 and m["lx"] in (8, 10, 12):
+        if dtype == ax.AX_BATCH_F64 and m["lx"] in (6, 8, 10):
             op = ax.Operator(m["lx"], m["dx"], m["dxt"], m["h1"], *[m[k] for k in GKEYS])
             op.apply(w1, m["u"])
-        elif dtype == ax.AX_BATCH_F64:
-            ax.ax_helm(w1, m["u"], m["dx"], m["dxt"], m["h1"], *[m[k] for k in GKEYS], m["lx"])
+        elif dtype == ax.AX_BATCH_F64:  # the double-float k-loop layout
+            ax.ax_helm(w1, m["u"], m["dx"], m["dxt"], m["h1"], *[m[k] for k in GKEYS], m["lx"],
+                       variant=ax.AX_VARIANT_F64_DF)
         else:
             ax.ax_helm_f32(w1, m["u"], m["dx"], m["dxt"], m["h1"], *[m[k] for k in GKEYS],
                            m["lx"])
@@ -175,3 +180,45 @@ def test_batch_follows_the_tuned_thread_layout():
     finally:
         ax.tune_variant_set(8, 0)
         ax.tune_variant_set(6, 0)
+
+
+@pytest.mark.parametrize("dtype", [ax.AX_BATCH_F64, ax.AX_BATCH_F32])
+def test_benchmark_size_batch_sampled(dtype):
+    """The benchmark's batch: 64 meshes from synth.batch_meshes (E log-uniform
+    in [64, 8192], lx in {5, 6, 8, 10}; ~1e5 elements), one launch through the
+    graph.  Inputs are seeded device-random fields (the operator is defined
+    for any G; positive G and h1 keep it an SPD-like form); for every mesh
+    four elements, its first and last among them, are checked against the
+    oracle one by one."""
+    tdt = torch.float64 if dtype == ax.AX_BATCH_F64 else torch.float32
+    tol = 1e-12 if dtype == ax.AX_BATCH_F64 else 1e-6
+    specs = synth.batch_meshes(seed=0)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1234)
+    meshes = []
+    for nx, ny, nz, lx in specs:
+        ne = nx * ny * nz
+        f = lambda lo, hi: (lo + (hi - lo) * torch.rand(ne * lx ** 3, device="cuda",
+                                                        generator=gen, dtype=torch.float64)).to(tdt)
+        dx, dxt = oracle.d_buffers(lx)
+        m = {"lx": lx, "u": f(-1.0, 1.0), "h1": f(0.5, 2.0),
+             "dx": torch.as_tensor(dx, device="cuda", dtype=tdt),
+             "dxt": torch.as_tensor(dxt, device="cuda", dtype=tdt)}
+        for k in GKEYS:
+            m[k] = f(0.5, 1.0) if k in ("g11", "g22", "g33") else f(-0.1, 0.1)
+        m["w"] = torch.full_like(m["u"], float("nan"))
+        meshes.append(m)
+    B = ax.Batch(meshes, dtype=dtype)
+    B.launch(graph=True)
+    torch.cuda.synchronize()
+    assert B.error() == 0
+    g = synth.rng(77)
+    for m in meshes:
+        lx, n3 = m["lx"], m["lx"] ** 3
+        ne = m["u"].numel() // n3
+        pick = sorted({0, ne - 1, int(g.integers(0, ne)), int(g.integers(0, ne))})
+        sl = lambda t: t.view(ne, lx, lx, lx)[pick].double().cpu().numpy()
+        ref = oracle.ax_helm(sl(m["u"]), m["dx"].double().cpu().numpy(),
+                             m["dxt"].double().cpu().numpy(), sl(m["h1"]),
+                             *[sl(m[k]) for k in GKEYS], lx)
+        assert rel_l2(sl(m["w"]), ref) <= tol, (lx, ne)
