@@ -17,16 +17,22 @@ CUDA events (kernels) or wall time around a synchronising solve (solvers):
            residual/error pairs of 20 plain-CG iterates on an 8^3 mesh: 10,240
            element pairs), in fp64 and inside mixed refinement
   rates    multiply-add throughput per SM and clock (fp64, fp32, packed
-           f32x2), the rates that decide the fp64 design
+           f32x2), the rates that decide the fp64 design (bench_probe.cu,
+           built here apart from the library)
   batch    64 meshes, E log-uniform in [64, 8192], lx in {5, 6, 8, 10}: one
            persistent launch (and its CUDA-graph replay) against one launch
            per mesh, fp64 and fp32
 """
 from __future__ import annotations
 
+import os
 import time
 
 import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
 
 GKEYS = ("g11", "g22", "g33", "g12", "g13", "g23")
 
@@ -284,11 +290,38 @@ def batch(ax, synth, dev, hbm_peak):
     return out
 
 
+def probe_rates() -> dict:
+    """Multiply-add throughput per SM and clock of the current device (fp64,
+    fp32, packed f32x2): bench_probe.cu, built here with nvcc into _build/
+    and loaded on its own (it is not part of the library)."""
+    import ctypes
+    import shutil
+    import subprocess
+    import torch
+    src = os.path.join(ROOT, "bench_probe.cu")
+    out_dir = os.path.join(ROOT, "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    so = os.path.join(out_dir, "libaxprobe.so")
+    if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+        tmp = so + f".tmp{os.getpid()}"
+        subprocess.run([nvcc, "-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+                        "-gencode", "arch=compute_103a,code=sm_103a", "-I", ROOT,
+                        "-I", os.path.join(ROOT, "include"), src, "-o", tmp], check=True)
+        os.replace(tmp, so)
+    lib = ctypes.CDLL(so)
+    rates = (ctypes.c_double * 3)()
+    rc = lib.bench_probe_rates(rates, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise RuntimeError(f"bench_probe_rates failed: {rc}")
+    return {"fp64_fma": rates[0], "fp32_fma": rates[1], "fp32x2_fma": rates[2]}
+
+
 def rates(ax):
     """Multiply-add throughput per SM and clock (fp64, fp32, packed f32x2)
     and what the fp64 one implies for an fp64-unit operator at lx = 8."""
     import torch
-    r = ax.probe_rates()
+    r = probe_rates()
     props = torch.cuda.get_device_properties(0)
     r["sms"] = props.multi_processor_count
     # Listing 2's flops per fp64 byte at lx = 8: (12 lx^4 + 18 lx^3) / (72 lx^3)

@@ -1,8 +1,10 @@
-// Arithmetic throughput probe: the per-SM, per-clock rates of the three
-// multiply-add forms the operator kernels are built from (fp64 on the fp64
-// pipe, fp32, and the packed f32x2 form of the double-float kernels).  These
-// rates decide the design: an fp64-unit operator is bound by the first, the
-// double-float kernels by the other two.
+// Benchmark tooling, not part of libaxhelm.so: bench_extras.py compiles this
+// file on its own (nvcc -shared) and loads it to report, beside the operator
+// timings, the per-SM, per-clock rates of the three multiply-add forms the
+// operator kernels are built from (fp64 on the fp64 pipe, fp32, and the
+// packed f32x2 form of the double-float kernels).  These rates decide the
+// design: an fp64-unit operator is bound by the first, the double-float
+// kernels by the other two.
 //
 // Each thread runs kChains independent multiply-add chains of `iters` steps
 // (independent so the pipe, not the latency, limits); every block records
@@ -15,8 +17,8 @@
 #include <algorithm>
 #include <vector>
 
-#include "common.cuh"
-#include "df64.cuh"
+#include "paper_2506_20994_gb300/csrc/common.cuh"
+#include "paper_2506_20994_gb300/csrc/df64.cuh"
 
 namespace {
 
@@ -110,7 +112,10 @@ int run_probe(int sms, int blocks_per_sm, int iters, long long *d_stamps, double
 
 }  // namespace
 
-extern "C" int ax_probe_rates(double *rates, void *stream) {
+// rates[0] fp64, rates[1] fp32, rates[2] packed f32x2 multiply-adds per SM
+// and clock on the current device (4 x 256 threads per SM, median over SMs);
+// allocates a small scratch buffer, synchronises `stream`.
+extern "C" int bench_probe_rates(double *rates, void *stream) {
   if (!rates) return AX_EINVAL;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||

@@ -540,15 +540,6 @@ int ax_mpfcg_solve(ax_poisson *P, const ax_mlp *M, int mode, double *x, const do
                    double tol, double inner_tol, int max_outer, int max_inner, int *outer_iters,
                    int *inner_iters, double *relres, int *fallbacks, void *stream);
 
-/* Arithmetic throughput of the current device, per SM and clock:
- * rates[0] fp64 multiply-adds (fp64 pipe), rates[1] fp32 multiply-adds,
- * rates[2] fp32 multiply-adds issued as packed fma.rn.f32x2 (two per lane).
- * A microbenchmark of the pipes the operator kernels use (independent chains
- * on 4 x 256 threads per SM, clocks read on the SM).  Allocates and frees a
- * small scratch buffer and synchronises `stream`.  AX_EINVAL for a NULL
- * rates, AX_ENOMEM, AX_ELAUNCH. */
-int ax_probe_rates(double *rates, void *stream);
-
 /* ------------------------------------------------------------------------
  * Host-side discretisation set-up (no GPU needed; plain host memory).
  * ------------------------------------------------------------------------ */

@@ -28,7 +28,7 @@ __all__ = [
     "AX_PREC_F32", "AX_PREC_BF16", "Batch", "tune", "tune_set", "tune_get", "AX_BATCH_F64",
     "AX_BATCH_F32", "fourier_coefficient", "Mlp", "mlp_init_params", "training_pairs", "train_mlp", "axpby", "iterate_pairs",
     "train_energy", "AX_MLP_TANH", "AX_MLP_SYM", "Operator", "ax_helm_h2", "ax_helm_xyz", "ax_helm_trilinear_f32", "box_corners", "ax_helm_host", "tune_variant",
-    "tune_variant_set", "tune_variant_get", "tune_save", "tune_load", "probe_rates",
+    "tune_variant_set", "tune_variant_get", "tune_save", "tune_load",
 ]
 
 
@@ -563,15 +563,6 @@ def tune_get(dtype: int, lx: int) -> int:
     e = ctypes.c_int()
     check("ax_tune_get", lib().ax_tune_get(dtype, lx, ctypes.addressof(e)))
     return e.value
-
-
-def probe_rates() -> dict:
-    """Multiply-add throughput per SM and clock of the current device:
-    fp64, fp32 and packed f32x2 (ax_probe_rates)."""
-    out = np.zeros(3)
-    check("ax_probe_rates", lib().ax_probe_rates(_addr(out), _stream()))
-    return {"fp64_fma": float(out[0]), "fp32_fma": float(out[1]),
-            "fp32x2_fma": float(out[2])}
 
 
 def tune_save(path: str) -> None:

@@ -29,7 +29,6 @@ PROTOTYPES = {
     "ax_dmat": (c_int, [c_int, P, P]),
     "ax_box_geometry": (c_int, [c_int, c_int, c_int, c_int, P] + [P] * 8),
     "ax_box_corners": (c_int, [c_int, c_int, c_int, P, P]),
-    "ax_probe_rates": (c_int, [P, P]),
     "ax_tune_save": (c_int, [ctypes.c_char_p]),
     "ax_tune_load": (c_int, [ctypes.c_char_p]),
     "ax_box_numbering": (c_int, [c_int, c_int, c_int, c_int, P]),
