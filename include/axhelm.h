@@ -512,6 +512,58 @@ int ax_gather(double *out, const double *v, const int64_t *idx, int64_t n, void 
 int ax_scatter_add(double *v, const double *vals, const int64_t *idx, const int64_t *pos,
                    int64_t n, void *stream);
 
+/* Right-hand side of the weak form: b = mask .* gs(B .* f) for the nodal
+ * source f and mass B = jac * w_i w_j w_k (device arrays of the handle's
+ * local points; b may alias f).  Asynchronous on stream. */
+int ax_poisson_rhs(ax_poisson *P, const double *B, const double *f, double *b, void *stream);
+
+/* Partitioned Jacobi-PCG (one rank's part of an SPMD solve).  The element
+ * set is split across ranks; they are coupled only by the gather-scatter sum
+ * at nodes shared between ranks and by the global dot products.  The driver
+ * runs the scalar recurrences (textbook PCG from x0 = 0, stopping at
+ * ||r|| <= tol ||r0||, norms over unique global nodes) and does everything
+ * else through two caller tables:
+ *   ops:  the rank-local vector work on this rank's vectors (all of one
+ *         length): w = mask .* gs(A p) with the rank-local gather-scatter,
+ *         z = M^-1 r, the rank-local weighted dot (weights 1 / global
+ *         multiplicity) returned as a host double, y = a x + b y, copy, zero;
+ *   comm: halo(v) adds the other ranks' partial sums at the shared nodes of
+ *         a rank-locally summed vector; allsum(vals, count) sums host doubles
+ *         over the ranks in place (every rank must get the same bits).
+ * Each callback returns 0 on success; any other value ends the solve and is
+ * returned.  Two all-sums per iteration.  x, b, r, z, p, w: this rank's
+ * vectors (device or host memory, as the ops expect); b is the rank's part of
+ * the assembled, masked right-hand side.  Returns AX_OK, AX_ENOTCONV (maxit
+ * reached), AX_EBREAKDOWN (p.Ap <= 0 or a non-finite value), AX_EINVAL, or a
+ * callback's code.  The driver itself makes no CUDA call. */
+typedef struct {
+  void *ctx;
+  int (*apply)(void *ctx, double *w, const double *p, void *stream);
+  int (*precond)(void *ctx, double *z, const double *r, void *stream);
+  int (*dot)(void *ctx, const double *a, const double *b, double *out, void *stream);
+  int (*axpby)(void *ctx, double *y, double a, const double *x, double b, void *stream);
+  int (*copy)(void *ctx, double *dst, const double *src, void *stream);
+  int (*zero)(void *ctx, double *v, void *stream);
+} ax_part_ops;
+typedef struct {
+  void *ctx;
+  int (*halo)(void *ctx, double *v, void *stream);
+  int (*allsum)(void *ctx, double *vals, int count);
+} ax_part_comm;
+int ax_cg_solve_part(const ax_part_ops *ops, const ax_part_comm *comm, double *x,
+                     const double *b, double *r, double *z, double *p, double *w, double tol,
+                     int maxit, int *iters, double *relres, void *stream);
+/* The same solve on a GPU rank with this library's kernels as the ops: the
+ * rank's Poisson handle P (its operator, rank-local gather-scatter, mask and
+ * Jacobi diagonal, set by ax_poisson_set_diag to the diagonal assembled
+ * across ranks), wgt = 1 / global multiplicity per local point (device).
+ * x, b: device vectors of the rank.  Uses the handle's work vectors plus one
+ * vector and the dot scratch it allocates for the call; synchronises stream
+ * at every dot.  AX_ENOMEM if that allocation fails. */
+int ax_cg_solve_part_poisson(ax_poisson *P, const double *wgt, const ax_part_comm *comm,
+                             double *x, const double *b, double tol, int maxit, int *iters,
+                             double *relres, void *stream);
+
 /* Preconditioner application z = minv .* r (+ learned correction if M is
  * not NULL; M's n_in must be lx^3) for fp64 local vectors; synchronises. */
 int ax_precondition(ax_poisson *P, const ax_mlp *M, double *z, const double *r, void *stream);
@@ -571,6 +623,12 @@ int ax_box_corners(int nx, int ny, int nz, const double *vertices, double *corne
 /* Global node id of every local point of the structured box (x fastest):
  * glob = X + NX*(Y + NY*Z), X = ex*(lx-1)+i, NX = nx*(lx-1)+1, ... */
 int ax_box_numbering(int nx, int ny, int nz, int lx, int64_t *glob);
+
+/* Dirichlet mask of the structured box (host array of nelv lx^3 doubles):
+ * 0 at every local point on a face marked in dirichlet[6] (faces x = 0,
+ * x = 1, y = 0, y = 1, z = 0, z = 1; nonzero = homogeneous Dirichlet), 1
+ * elsewhere.  A face left open is an interface to another partition. */
+int ax_box_mask(int nx, int ny, int nz, int lx, const int *dirichlet, double *mask);
 
 /* Host diagnostic of the fp64 <-> fp32-pair conversions that the
  * AX_VARIANT_F64_DF kernels use on the device (same source): splits each

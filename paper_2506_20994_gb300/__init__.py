@@ -96,6 +96,15 @@ def box_numbering(nx: int, ny: int, nz: int, lx: int) -> np.ndarray:
     return g
 
 
+def box_mask(nx: int, ny: int, nz: int, lx: int, dirichlet=(True,) * 6) -> np.ndarray:
+    """Dirichlet mask of the box (ax_box_mask): 0 on the marked faces
+    (x0, x1, y0, y1, z0, z1), 1 elsewhere."""
+    d = np.asarray([1 if f else 0 for f in dirichlet], dtype=np.int32)
+    m = np.empty((nx * ny * nz, lx, lx, lx))
+    check("ax_box_mask", lib().ax_box_mask(nx, ny, nz, lx, _addr(d), _addr(m)))
+    return m
+
+
 def df64_roundtrip(x: np.ndarray):
     """Host twin of the device fp64 <-> fp32-pair conversion (diagnostic)."""
     x = np.ascontiguousarray(x, dtype=np.float64).ravel()
@@ -371,13 +380,7 @@ class Poisson:
         self.mass_host = geo["mass"]
         glob = box_numbering(nx, ny, nz, lx)
         self.glob = glob
-        n = lx - 1
-        NX, NY, NZ = nx * n + 1, ny * n + 1, nz * n + 1
-        X, Y, Z = glob % NX, (glob // NX) % NY, glob // (NX * NY)
-        fx0, fx1, fy0, fy1, fz0, fz1 = dirichlet
-        on = ((fx0 & (X == 0)) | (fx1 & (X == NX - 1)) | (fy0 & (Y == 0)) | (fy1 & (Y == NY - 1))
-              | (fz0 & (Z == 0)) | (fz1 & (Z == NZ - 1)))
-        mask = np.where(on, 0.0, 1.0)
+        mask = box_mask(nx, ny, nz, lx, dirichlet)
         if callable(h1):
             h1 = h1(self.xyz[..., 0], self.xyz[..., 1], self.xyz[..., 2])
         if h1 is not None and np.size(h1) == mask.size:
@@ -412,13 +415,15 @@ class Poisson:
                 self._h, self.d["h2"].data_ptr(), self.mass.data_ptr(), _stream()))
 
     def rhs(self, f) -> "torch.Tensor":
-        """b = mask .* gs(B f) for a callable f(x, y, z) (evaluated on host)."""
+        """b = mask .* gs(B f) (ax_poisson_rhs) for a callable source f(x, y, z),
+        sampled at the nodes on the host."""
         import torch
         x = self.xyz
         fv = f(x[..., 0], x[..., 1], x[..., 2])
-        b = self.mass * torch.as_tensor(np.ascontiguousarray(fv), device=self.device)
-        self.gs.sum(b)
-        return b * self.d["mask"]
+        b = torch.as_tensor(np.ascontiguousarray(fv, dtype=np.float64), device=self.device)
+        check("ax_poisson_rhs", lib().ax_poisson_rhs(self._h, self.mass.data_ptr(),
+                                                     b.data_ptr(), b.data_ptr(), _stream()))
+        return b
 
     def apply(self, w, u) -> None:
         check("ax_poisson_apply", lib().ax_poisson_apply(self._h, w.data_ptr(), u.data_ptr(),

@@ -32,6 +32,11 @@ PROTOTYPES = {
     "ax_tune_save": (c_int, [ctypes.c_char_p]),
     "ax_tune_load": (c_int, [ctypes.c_char_p]),
     "ax_box_numbering": (c_int, [c_int, c_int, c_int, c_int, P]),
+    "ax_box_mask": (c_int, [c_int, c_int, c_int, c_int, P, P]),
+    "ax_poisson_rhs": (c_int, [c_void_p, P, P, P, c_void_p]),
+    "ax_cg_solve_part": (c_int, [P] * 8 + [c_double, c_int, P, P, c_void_p]),
+    "ax_cg_solve_part_poisson": (c_int, [c_void_p, P, P, P, P, c_double, c_int, P, P,
+                                         c_void_p]),
     "ax_df64_roundtrip": (c_int, [P, P, P, P, c_int64]),
     "ax_gs_setup": (c_int, [P, P, c_int64, c_void_p]),
     "ax_gs_sum": (c_int, [c_void_p, P, c_void_p]),
@@ -105,6 +110,27 @@ class BatchMesh(ctypes.Structure):
     _fields_ = [("lx", c_int), ("nelv", c_int)] + [
         (n, c_void_p) for n in ("w", "u", "dx", "dxt", "h1", "g11", "g22", "g33", "g12", "g13",
                                 "g23")]
+
+# the callback tables of the partitioned solve (ax_part_ops, ax_part_comm)
+APPLY_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_void_p, c_void_p, c_void_p)
+DOT_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double),
+                          c_void_p)
+AXPBY_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_void_p, c_double, c_void_p, c_double, c_void_p)
+ZERO_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_void_p, c_void_p)
+HALO_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_void_p, c_void_p)
+ALLSUM_FN = ctypes.CFUNCTYPE(c_int, c_void_p, ctypes.POINTER(c_double), c_int)
+
+
+class PartOps(ctypes.Structure):
+    """Mirror of ax_part_ops."""
+    _fields_ = [("ctx", c_void_p), ("apply", APPLY_FN), ("precond", APPLY_FN),
+                ("dot", DOT_FN), ("axpby", AXPBY_FN), ("copy", APPLY_FN), ("zero", ZERO_FN)]
+
+
+class PartComm(ctypes.Structure):
+    """Mirror of ax_part_comm."""
+    _fields_ = [("ctx", c_void_p), ("halo", HALO_FN), ("allsum", ALLSUM_FN)]
+
 
 AX_OK = 0
 AX_EINVAL = -1

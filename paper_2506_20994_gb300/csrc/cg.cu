@@ -296,6 +296,12 @@ __global__ void mul_kernel(double *__restrict__ out, const double *__restrict__ 
        q += (int64_t)gridDim.x * blockDim.x)
     out[q] = a[q] * b[q];
 }
+// out = a .* b where out may alias a or b
+__global__ void mul_alias_kernel(double *out, const double *a, const double *b, int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    out[q] = a[q] * b[q];
+}
 __global__ void add_kernel(double *__restrict__ out, const double *__restrict__ a, int64_t n) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x)
@@ -1505,5 +1511,90 @@ extern "C" int ax_mlp_train_energy(ax_poisson *P, ax_mlp *M, const double *r_set
     *final_loss = m / K;  // mean relative energy error of the last epoch
   }
   cleanup();
+  return rc;
+}
+
+extern "C" int ax_poisson_rhs(ax_poisson *P, const double *B, const double *f, double *b,
+                              void *stream) {
+  if (!P || !B || !f || !b) return AX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  mul_alias_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(b, B, f, P->n);  // B .* f
+  int rc = ax::launch_status();
+  if (rc) return rc;
+  if ((rc = ax_gs_sum(P->gs, b, st))) return rc;
+  mul_alias_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(b, P->mask, b, P->n);  // mask .* gs(B f)
+  return ax::launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// The partitioned solve's rank-local vector work on a GPU rank: this
+// library's kernels on the rank's Poisson handle (the driver is part.cpp).
+namespace {
+
+struct PartNative {
+  ax_poisson *P;
+  const double *wgt;
+  double *work;  // AX_DOT_WORK partials + the dot result
+};
+
+int pn_apply(void *c, double *w, const double *p, void *st) {
+  return ax_poisson_apply(static_cast<PartNative *>(c)->P, w, p, st);
+}
+int pn_precond(void *c, double *z, const double *r, void *st) {
+  return ax_precondition(static_cast<PartNative *>(c)->P, nullptr, z, r, st);
+}
+int pn_dot(void *c, const double *a, const double *b, double *out, void *st) {
+  auto *n = static_cast<PartNative *>(c);
+  int rc = ax_dot_weighted(a, b, n->wgt, n->P->n, n->work, n->work + AX_DOT_WORK, st);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(out, n->work + AX_DOT_WORK, sizeof(double), cudaMemcpyDeviceToHost,
+                      (cudaStream_t)st) != cudaSuccess ||
+      cudaStreamSynchronize((cudaStream_t)st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return AX_ELAUNCH;
+  }
+  return AX_OK;
+}
+int pn_axpby(void *c, double *y, double a, const double *x, double b, void *st) {
+  return ax_axpby(y, a, x, b, static_cast<PartNative *>(c)->P->n, st);
+}
+int pn_copy(void *c, double *dst, const double *src, void *st) {
+  const int64_t n = static_cast<PartNative *>(c)->P->n;
+  if (cudaMemcpyAsync(dst, src, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice,
+                      (cudaStream_t)st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return AX_ELAUNCH;
+  }
+  return AX_OK;
+}
+int pn_zero(void *c, double *v, void *st) {
+  const int64_t n = static_cast<PartNative *>(c)->P->n;
+  if (cudaMemsetAsync(v, 0, (size_t)n * sizeof(double), (cudaStream_t)st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return AX_ELAUNCH;
+  }
+  return AX_OK;
+}
+
+}  // namespace
+
+extern "C" int ax_cg_solve_part_poisson(ax_poisson *P, const double *wgt,
+                                        const ax_part_comm *comm, double *x, const double *b,
+                                        double tol, int maxit, int *iters, double *relres,
+                                        void *stream) {
+  if (!P || !wgt || !comm || !x || !b) return AX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  double *z = nullptr, *work = nullptr;
+  if (alloc(&z, P->n) || alloc(&work, AX_DOT_WORK + 1)) {
+    cudaFree(z);
+    return AX_ENOMEM;
+  }
+  PartNative ctx{P, wgt, work};
+  const ax_part_ops ops{&ctx, pn_apply, pn_precond, pn_dot, pn_axpby, pn_copy, pn_zero};
+  int rc = ax_cg_solve_part(&ops, comm, x, b, P->r, z, P->p, P->w, tol, maxit, iters, relres,
+                            stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess && rc == AX_OK) rc = AX_ELAUNCH;
+  cudaFree(z);
+  cudaFree(work);
   return rc;
 }

@@ -242,6 +242,31 @@ int ax_box_numbering(int nx, int ny, int nz, int lx, int64_t *glob) {
   return AX_OK;
 }
 
+int ax_box_mask(int nx, int ny, int nz, int lx, const int *dirichlet, double *mask) {
+  if (lx < AX_LX_MIN || lx > AX_LX_MAX || nx < 1 || ny < 1 || nz < 1 || !dirichlet || !mask)
+    return AX_EINVAL;
+  const int64_t n = lx - 1, NX = (int64_t)nx * n + 1, NY = (int64_t)ny * n + 1;
+  const int64_t NZ = (int64_t)nz * n + 1;
+  const int64_t nel = (int64_t)nx * ny * nz;
+  const bool fx0 = dirichlet[0], fx1 = dirichlet[1], fy0 = dirichlet[2], fy1 = dirichlet[3];
+  const bool fz0 = dirichlet[4], fz1 = dirichlet[5];
+  parallel_for(nel, [&](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1; ++e) {
+      const int64_t ex = e % nx, ey = (e / nx) % ny, ez = e / ((int64_t)nx * ny);
+      int64_t q = e * lx * lx * lx;
+      for (int k = 0; k < lx; ++k)
+        for (int j = 0; j < lx; ++j)
+          for (int i = 0; i < lx; ++i) {
+            const int64_t X = ex * n + i, Y = ey * n + j, Z = ez * n + k;
+            const bool on = (fx0 && X == 0) || (fx1 && X == NX - 1) || (fy0 && Y == 0) ||
+                            (fy1 && Y == NY - 1) || (fz0 && Z == 0) || (fz1 && Z == NZ - 1);
+            mask[q++] = on ? 0.0 : 1.0;
+          }
+    }
+  });
+  return AX_OK;
+}
+
 int ax_box_corners(int nx, int ny, int nz, const double *vertices, double *corners) {
   if (nx < 1 || ny < 1 || nz < 1 || !vertices || !corners) return AX_EINVAL;
   const int64_t nel = (int64_t)nx * ny * nz;

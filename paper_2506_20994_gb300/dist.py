@@ -17,15 +17,18 @@ logic of that split:
   holds this rank's partial sum; one exchange per neighbour adds the other
   side's.  Both sides compute own + other with IEEE addition, which is
   commutative, so the two copies agree bit for bit.
-* ``pcg``: Jacobi-PCG from x0 = 0 in SPMD form, stopping at
-  ||r|| <= tol ||r0||, with the dots over unique global nodes (weights
-  1/global multiplicity) summed across ranks.
+* ``pcg``: Jacobi-PCG from x0 = 0 in SPMD form, run by the library's driver
+  (``ax_cg_solve_part``: the scalar recurrences, stopping at
+  ||r|| <= tol ||r0||, dots over unique global nodes with weights
+  1/global multiplicity).  This module only hands the driver its callback
+  tables: the halo exchange and the scalar all-sum (moving bytes between
+  ranks) and, for rank-local work other than the library's own, the ops.
 
 The vector work is done by an ``ops`` object (``LibSlabOps``: the library's
-kernels on this rank's GPU) and the communication by a ``comm`` object
-(``TorchComm``: torch.distributed; ``ThreadComm``: ranks as threads of one
-process, which lets several partitions share one GPU without any kernel
-waiting on another).
+kernels on this rank's GPU, which the driver then calls directly) and the
+communication by a ``comm`` object (``TorchComm``: torch.distributed;
+``ThreadComm``: ranks as threads of one process, which lets several
+partitions share one GPU without any kernel waiting on another).
 """
 from __future__ import annotations
 
@@ -96,10 +99,13 @@ class TorchComm:
         self.rank, self.world = dist.get_rank(), dist.get_world_size()
 
     def allsum(self, x: float) -> float:
+        return self.allsum_many([x])[0]
+
+    def allsum_many(self, xs) -> list:
         import torch
-        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        t = torch.tensor(list(xs), dtype=torch.float64, device=self.device)
         self.dist.all_reduce(t)
-        return float(t.item())
+        return [float(v) for v in t.cpu()]
 
     def exchange(self, sends: dict) -> dict:
         """sends: {neighbour rank: 1-D float64 tensor}; returns the tensors
@@ -137,13 +143,19 @@ class ThreadComm:
         return [cls(sh, r) for r in range(world)]
 
     def allsum(self, x: float) -> float:
-        self.s.vals[self.rank] = float(x)
+        return self.allsum_many([x])[0]
+
+    def allsum_many(self, xs) -> list:
+        self.s.vals[self.rank] = [float(x) for x in xs]
         self.s.barrier.wait()
-        total = 0.0
-        for v in self.s.vals:                 # rank order: the same bits everywhere
-            total += v
+        out = []
+        for q in range(len(xs)):
+            total = 0.0
+            for v in self.s.vals:             # rank order: the same bits everywhere
+                total += v[q]
+            out.append(total)
         self.s.barrier.wait()
-        return total
+        return out
 
     def exchange(self, sends: dict) -> dict:
         # messages go through host memory: .cpu() waits for the sender's
@@ -182,34 +194,73 @@ def setup(ops, plan: SlabPlan, comm) -> None:
 
 
 def pcg(ops, plan: SlabPlan, comm, b, tol: float = 1e-8, maxit: int = 10000):
-    """Jacobi-PCG on the partitioned problem.  b: this rank's part of the
+    """Jacobi-PCG on the partitioned problem by the library's driver
+    (ax_cg_solve_part_poisson for ``LibSlabOps``, ax_cg_solve_part with
+    ``ops``' methods as callbacks otherwise).  b: this rank's part of the
     assembled, masked right-hand side.  Returns (x, iterations, relres)."""
+    import ctypes
     x = ops.zeros()
-    r = ops.clone(b)
-    z = ops.zeros()
-    ops.precond(z, r)
-    p = ops.clone(z)
-    w = ops.zeros()
-    rz = comm.allsum(ops.dot(r, z))
-    r0 = np.sqrt(comm.allsum(ops.dot(r, r)))
-    if r0 == 0.0:
-        return x, 0, 0.0
-    it, rel = 0, 1.0
-    while it < maxit:
-        ops.apply(w, p)
-        halo_sum(ops, plan, comm, w)
-        alpha = rz / comm.allsum(ops.dot(p, w))
-        ops.axpby(x, alpha, p, 1.0)
-        ops.axpby(r, -alpha, w, 1.0)
-        it += 1
-        rel = np.sqrt(comm.allsum(ops.dot(r, r))) / r0
-        if rel <= tol:
-            break
-        ops.precond(z, r)
-        rz_new = comm.allsum(ops.dot(r, z))
-        ops.axpby(p, 1.0, z, rz_new / rz)
-        rz = rz_new
-    return x, it, rel
+    vecs = {}            # address -> vector, for the callbacks
+    errors = []
+
+    def reg(t):
+        vecs[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def at(addr):
+        t = vecs.get(addr)
+        return t if t is not None else ops.wrap(addr)
+
+    def guarded(fn):
+        def run(*a):
+            try:
+                fn(*a)
+                return 0
+            except Exception as exc:  # reported after the driver returns
+                errors.append(exc)
+                return 1
+        return run
+
+    def allsum(ctx, vals, n):
+        out = comm.allsum_many([vals[q] for q in range(n)])
+        for q in range(n):
+            vals[q] = out[q]
+
+    ctab = _lib.PartComm(None,
+                         _lib.HALO_FN(guarded(lambda c, v, st: halo_sum(ops, plan, comm, at(v)))),
+                         _lib.ALLSUM_FN(guarded(allsum)))
+    it, rel = ctypes.c_int(), ctypes.c_double()
+    reg(x)
+    reg(b)
+    if isinstance(ops, LibSlabOps):
+        rc = _lib.lib().ax_cg_solve_part_poisson(
+            ops.P._h, ops.wgt.data_ptr(), ctypes.addressof(ctab), x.data_ptr(), b.data_ptr(),
+            float(tol), int(maxit), ctypes.addressof(it), ctypes.addressof(rel), ops._s())
+    else:
+        work = [ops.zeros() for _ in range(4)]
+        for t in work:
+            reg(t)
+
+        def dot(c, a, bb, out, st):
+            out[0] = ops.dot(at(a), at(bb))
+
+        otab = _lib.PartOps(
+            None,
+            _lib.APPLY_FN(guarded(lambda c, w, p, st: ops.apply(at(w), at(p)))),
+            _lib.APPLY_FN(guarded(lambda c, z, r, st: ops.precond(at(z), at(r)))),
+            _lib.DOT_FN(guarded(dot)),
+            _lib.AXPBY_FN(guarded(lambda c, y, a, xx, bb, st: ops.axpby(at(y), a, at(xx), bb))),
+            _lib.APPLY_FN(guarded(lambda c, d, s_, st: at(d).copy_(at(s_)))),
+            _lib.ZERO_FN(guarded(lambda c, v, st: at(v).zero_())))
+        rc = _lib.lib().ax_cg_solve_part(
+            ctypes.addressof(otab), ctypes.addressof(ctab), x.data_ptr(), b.data_ptr(),
+            *[t.data_ptr() for t in work], float(tol), int(maxit), ctypes.addressof(it),
+            ctypes.addressof(rel), None)
+    if errors:
+        raise errors[0]
+    if rc not in (_lib.AX_OK, _lib.AX_ENOTCONV):
+        _lib.check("ax_cg_solve_part", rc)
+    return x, it.value, rel.value
 
 
 # ---------------------------------------------------------------------------
@@ -243,6 +294,13 @@ class LibSlabOps:
         import torch
         return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).reshape(self.shape),
                                device=self.device).clone()
+
+    def wrap(self, addr):
+        """A view of a local vector the library owns (the solver's work)."""
+        import torch
+        from . import _DeviceArray
+        n = int(np.prod(self.shape))
+        return torch.as_tensor(_DeviceArray(addr, n, "<f8", self), device=self.device)
 
     def zeros(self):
         import torch

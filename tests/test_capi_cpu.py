@@ -79,6 +79,22 @@ def _ulp64(x):
     return np.spacing(np.abs(x))
 
 
+def test_host_mask_matches_oracle():
+    """ax_box_mask with every face Dirichlet is the oracle's boundary mask;
+    with faces left open (partition interfaces) exactly the marked faces
+    are zero."""
+    nx, ny, nz, lx = 3, 2, 4, 4
+    np.testing.assert_array_equal(ax.box_mask(nx, ny, nz, lx),
+                                  oracle.boundary_mask(nx, ny, nz, lx))
+    n = lx - 1
+    g = oracle.numbering(nx, ny, nz, lx)
+    NX, NY = nx * n + 1, ny * n + 1
+    Z = g // (NX * NY)
+    X = g % NX
+    m = ax.box_mask(nx, ny, nz, lx, (True, False, False, False, False, True))
+    np.testing.assert_array_equal(m, np.where((X == 0) | (Z == nz * n), 0.0, 1.0))
+
+
 def test_df64_split_is_exact_truncation():
     g = synth.rng(5)
     mags = 10.0 ** g.uniform(-20, 30, size=20000)

@@ -1,6 +1,7 @@
 """The partitioned Poisson solve on CPU ranks: the slab plan's bookkeeping,
-and Jacobi-PCG over 2 and 3 gloo ranks (oracle-backed rank-local work)
-against the single-domain oracle PCG."""
+and Jacobi-PCG over 2, 3 and 4 gloo ranks - the library's partitioned driver
+(ax_cg_solve_part, host code) with oracle-backed rank-local work as its ops
+table - against the single-domain oracle PCG."""
 import os
 import socket
 
@@ -82,6 +83,8 @@ def _rank_main(rank, world, port, dims, lx, outdir):
 
 @pytest.mark.parametrize("world,dims,lx", [(2, (2, 2, 4), 4), (3, (2, 3, 3), 3), (4, (2, 2, 4), 3)])
 def test_partitioned_pcg_matches_single_domain(world, dims, lx, tmp_path):
+    import paper_2506_20994_gb300 as ax
+    ax.build()  # the driver is library code; its ranks load libaxhelm.so
     mp.spawn(_rank_main, args=(world, _free_port(), dims, lx, str(tmp_path)), nprocs=world,
              join=True)
     nx, ny, nz = dims
