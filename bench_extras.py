@@ -32,8 +32,6 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 
-ROOT = os.path.dirname(os.path.abspath(__file__))
-
 GKEYS = ("g11", "g22", "g33", "g12", "g13", "g23")
 
 
@@ -73,6 +71,50 @@ def _mesh_tensors(ax, synth, n, lx, dev, seed=0):
     return d, sh[0]
 
 
+def sample_elements(nel, count=64):
+    """Elements on which the CPU-baseline leg checks every mode against the
+    oracle: spread over the mesh, the first and the last included."""
+    return np.unique(np.linspace(0, nel - 1, count).round().astype(np.int64))
+
+
+def mode_outputs(ax, lx, u, h1, dx, dxt, G, corners, xi, wq):
+    """Every operator mode of the modes section applied to the same small
+    set of elements (fp64 host inputs; G a dict of the six factors): the
+    fp64 variants and the operator handle, fp32 and bf16 storage, fp32 with
+    G formed from the corners.  Returns {mode: fp64 host output}."""
+    import torch
+    dev = torch.device("cuda")
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), device=dev).to(dt)
+    a64 = [t(u), t(dx), t(dxt), t(h1)] + [t(G[k]) for k in GKEYS]
+    out = {}
+    w = torch.empty_like(a64[0])
+    for name, var in (("f64_native", ax.AX_VARIANT_F64_NATIVE), ("f64_df", ax.AX_VARIANT_F64_DF),
+                      ("f64_df_eo", ax.AX_VARIANT_F64_DF_EO)):
+        try:
+            ax.ax_helm(w, *a64, lx, variant=var)
+        except ax.AxError:
+            continue
+        out[name] = w.cpu().numpy().copy()
+    ax.ax_helm(w, *a64, lx)
+    out["f64_ax_helm_unprepared"] = w.cpu().numpy().copy()
+    op = ax.Operator(lx, a64[1], a64[2], a64[3], *a64[4:])
+    op.apply(w, a64[0])
+    out["f64_op_prepared"] = w.cpu().numpy().copy()
+    for mode, dt, fn in (("f32", torch.float32, ax.ax_helm_f32),
+                         ("bf16", torch.bfloat16, ax.ax_helm_bf16)):
+        f = [t(u, dt), t(h1, dt)] + [t(G[k], dt) for k in GKEYS]
+        w32 = torch.empty(f[0].shape, dtype=torch.float32, device=dev)
+        fn(w32, f[0], t(dx, torch.float32), t(dxt, torch.float32), f[1], *f[2:], lx)
+        out[mode] = w32.double().cpu().numpy()
+    w32 = torch.empty(u.shape, dtype=torch.float32, device=dev)
+    ax.ax_helm_trilinear_f32(w32, t(u, torch.float32), t(dx, torch.float32),
+                             t(dxt, torch.float32), None, t(corners).reshape(-1), t(xi), t(wq),
+                             lx)
+    out["f32_trilinear"] = w32.double().cpu().numpy()
+    torch.cuda.synchronize()
+    return out
+
+
 def modes(ax, d, lx, nel, hbm_peak):
     import torch
     out = {}
@@ -88,6 +130,11 @@ def modes(ax, d, lx, nel, hbm_peak):
             continue
         out[name] = {"gdofs": round(npts / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 4),
                      "hbm_frac": round(72.0 * npts / (ms * 1e-3) / 1e9 / hbm_peak, 4)}
+    # ax_helm's own choice on the caller's fp64 arrays (no prepared geometry)
+    ms = _events_ms(lambda: ax.ax_helm(w64, d["u"], d["dx"], d["dxt"], d["h1"], *G, lx), 10)
+    out["f64_ax_helm_unprepared"] = {
+        "gdofs": round(npts / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 4),
+        "hbm_frac": round(72.0 * npts / (ms * 1e-3) / 1e9 / hbm_peak, 4)}
     op = ax.Operator(lx, d["dx"], d["dxt"], d["h1"], *G)
     if op.info()["prepared"]:
         ms = _events_ms(lambda: op.apply(w64, d["u"]), 10)
@@ -227,17 +274,31 @@ def learned(ax, synth, oracle_f, dev):
     t_pairs, (R, E) = _wall(lambda: ax.iterate_pairs(Ps, bs, iterates=iterates))
     t_train, loss = _wall(lambda: ax.train_energy(Ps, M, R, E, epochs=100, lr=2e-3))
     out["training"] = {"arch": "symmetric linear, n_hid 48", "iterates": int(R.shape[0]),
-                       "element_pairs": int(R.shape[0]) * Ps.nelv, "params": M.nparams,
+                       "element_pairs": int(R.shape[0]) * Ps.nelv,
+                       "params": lx ** 3 * n_hid,
+                       "params_note": "free parameters of the tied form (one lx^3 x 48 basis "
+                                      "W used as W and W^T); %d stored in the flat layout"
+                                      % M.nparams,
                        "pair_s": round(t_pairs, 3), "train_s": round(t_train, 3),
                        "final_rel_energy_err": loss}
+    t_setup = t_pairs + t_train
     del Ps, R, E
     P = ax.Poisson(synth.box_vertices(32, seed=0), lx, h1=coef, device=dev)
     P.set_check_every(8)
     b = P.rhs(oracle_f)
+    P.cg(b, tol=1e-8, maxit=3)  # warm-up
+    # the baseline: plain fp64 Jacobi-preconditioned CG on the same problem
+    tc, (x, ic, rc_, sc) = _wall(lambda: P.cg(b, tol=1e-8))
+    out["f64_jacobi_cg"] = {"s": round(tc, 4), "iters": ic, "relres": rc_, "status": sc}
+
+    def vs_cg(t):
+        return {"speedup_vs_f64_jacobi_cg": round(tc / t, 3),
+                "speedup_vs_f64_jacobi_cg_with_training": round(tc / (t + t_setup), 3)}
     t0, (x, i0, r0, f0, s0) = _wall(lambda: P.fcg(b, None, tol=1e-8))
     out["f64_jacobi_fcg"] = {"s": round(t0, 4), "iters": i0, "status": s0}
     t1, (x, i1, r1, f1, s1) = _wall(lambda: P.fcg(b, M, tol=1e-8))
-    out["f64_learned_fcg"] = {"s": round(t1, 4), "iters": i1, "fallbacks": f1, "status": s1}
+    out["f64_learned_fcg"] = {"s": round(t1, 4), "iters": i1, "fallbacks": f1, "status": s1,
+                              **vs_cg(t1)}
     P.mpfcg(b, None, tol=1e-8)  # converts the fp32 operator data once
     t2, (x, no, ni, r2, f2, s2) = _wall(lambda: P.mpfcg(b, None, tol=1e-8, inner_tol=1e-4))
     out["f32_ir_jacobi"] = {"s": round(t2, 4), "outer": no, "inner_iters": ni, "status": s2,
@@ -245,7 +306,9 @@ def learned(ax, synth, oracle_f, dev):
     t3, (x, no, ni, r3, f3, s3) = _wall(lambda: P.mpfcg(b, M, tol=1e-8, inner_tol=1e-4))
     out["f32_ir_learned"] = {"s": round(t3, 4), "outer": no, "inner_iters": ni,
                              "fallbacks": f3, "status": s3,
-                             "speedup_vs_f64_jacobi": round(t0 / t3, 3)}
+                             "speedup_vs_f64_jacobi": round(t0 / t3, 3), **vs_cg(t3)}
+    out["f32_ir_jacobi"].update(vs_cg(t2))
+    out["training_s"] = round(t_setup, 3)
     return out
 
 

@@ -22,17 +22,9 @@
 // the geometry-weighted gradient before the transposed contractions.  No
 // fp64 instruction is issued.
 //
-// The geometry of the pointwise step comes either from the fp64 arrays
-// (split on the fly, one point at a time) or from a prepared copy in this
-// kernel's own order (eo_prepare_kernel), which the pointwise step consumes
-// two points at a time (a = 0, 1: i' and N-i') as the two lanes of packed
-// double-float arithmetic.  The prepared order is, per element, per
-// corner pair (c, b), per field (g11, g22, g33, g12, g13, g23, h1), per
-// thread, one 16-byte entry {hi(a=0), hi(a=1), lo(a=0), lo(a=1)}: the same
-// 8 bytes per value and the same split, but no conversion instructions and
-// coalesced 16-byte loads.  (The packed pointwise step rounds its tail sums
-// in another order than the scalar one, so the two paths agree to ~1e-16
-// relative, not bit for bit.)
+// The geometry of the pointwise step comes from the fp64 arrays, split one
+// point at a time (the operator handle's persistent kernel,
+// ax_eo_persist.cuh, reads a copy prepared in its own order instead).
 #pragma once
 
 #include <algorithm>
@@ -54,23 +46,9 @@ constexpr int dir_entries() {
   return LX * LX * line_stride<LX>();
 }
 
-// 16-byte entries of one element's prepared geometry
-template <int LX>
-constexpr int prep_entries() {
-  return 4 * 7 * (LX / 2) * (LX / 2) * (LX / 2);
-}
-
-// geometry in flight: 7 fields of one corner (fp64 arrays) or of one corner
-// pair (prepared)
-template <bool PREP>
-struct GeoStage;
-template <>
-struct GeoStage<false> {
+// geometry in flight: the 7 fields of one corner point
+struct GeoStage {
   double v[7];
-};
-template <>
-struct GeoStage<true> {
-  df::dd2 v[7];
 };
 
 }  // namespace eo
@@ -83,11 +61,7 @@ constexpr size_t df64eo_smem(int epb) {
   return 2 * H2 * (16 + 8) + (size_t)epb * 3 * eo::dir_entries<LX>() * 16;
 }
 
-// PUPD (prepared geometry only): u is not an input; instead the kernel first
-// forms the solver's next search direction in place, pw = z + (*beta) pw
-// with z = minv .* r (+ corr when *use_corr, the flexible CG's learned
-// step), in fp64 with explicit roundings, and applies the operator to it.
-template <int LX, bool PREP = false, bool PUPD = false, bool NBAR = true>
+template <int LX, bool NBAR = true>
 __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double *__restrict__ u,
                                             const double *__restrict__ dx,
                                             const double *__restrict__ dxt,
@@ -97,17 +71,8 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
                                             const double *__restrict__ g33,
                                             const double *__restrict__ g12,
                                             const double *__restrict__ g13,
-                                            const double *__restrict__ g23,
-                                            const df::dd2 *__restrict__ gp,
-                                            const unsigned *__restrict__ gstat, long long e0,
-                                            int nel, int epb, unsigned char *smem_raw,
-                                            double *__restrict__ dotp = nullptr,
-                                            double *__restrict__ pw = nullptr,
-                                            const double *__restrict__ r_in = nullptr,
-                                            const double *__restrict__ minv_in = nullptr,
-                                            const double *__restrict__ beta_p = nullptr,
-                                            const double *__restrict__ corr_in = nullptr,
-                                            const int *__restrict__ use_corr_p = nullptr) {
+                                            const double *__restrict__ g23, long long e0,
+                                            int nel, int epb, unsigned char *smem_raw) {
   static_assert(LX % 2 == 0, "even-odd kernel needs an even lx");
   using namespace df;
   constexpr int H = LX / 2, N = LX - 1;
@@ -171,16 +136,10 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
   const bool active = own && le < nel;
   const size_t eb = (size_t)(active ? e0 + le : 0) * N3;
   // the geometry of this element is read only in phase 3: start it towards L2 now
-  const size_t ep = (size_t)(active ? e0 + le : 0) * eo::prep_entries<LX>();
   if (active && t < 7) {
-    if constexpr (PREP) {  // the element's prepared block, in 7 equal pieces
-      prefetch_l2(gp + ep + (size_t)t * (eo::prep_entries<LX>() / 7),
-                  (unsigned)(N3 * sizeof(double)));
-    } else {
-      const double *f = t == 0 ? g11 : t == 1 ? g22 : t == 2 ? g33 : t == 3 ? g12
-                      : t == 4 ? g13 : t == 5 ? g23 : h1;
-      prefetch_l2(f + eb, (unsigned)(N3 * sizeof(double)));
-    }
+    const double *f = t == 0 ? g11 : t == 1 ? g22 : t == 2 ? g33 : t == 3 ? g12
+                    : t == 4 ? g13 : t == 5 ? g23 : h1;
+    prefetch_l2(f + eb, (unsigned)(N3 * sizeof(double)));
   }
   auto gidx = [&](int c, int b, int a) {
     const int k = c ? N - kp : kp, j = b ? N - jp : jp, i = a ? N - ip : ip;
@@ -225,28 +184,7 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
   unsigned ukey = 0u, gkey = 0u, hkey = 0u;  // exponent keys of u, G, h1 (guard.cuh)
   // ---- phase 1: own values of u, (e, o) along each direction
   if (own) {
-    if constexpr (PUPD) {
-      const double beta = *beta_p;
-      // flexible CG: z = minv r + corr when its step took the correction
-      const bool uc = corr_in != nullptr && *use_corr_p != 0;
-#pragma unroll
-      for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-          for (int a = 0; a < 2; ++a) {
-            gr[c][b][a] = df2{0.f, 0.f};
-            if (active) {
-              const size_t q = gidx(c, b, a);
-              double z = __dmul_rn(__ldg(minv_in + q), __ldg(r_in + q));
-              if (uc) z = __dadd_rn(z, __ldg(corr_in + q));
-              const double pn = __fma_rn(beta, pw[q], z);
-              pw[q] = pn;
-              ukey = max(ukey, guard::key(pn));
-              gr[c][b][a] = split(pn);
-            }
-          }
-    } else {
+    {
 #pragma unroll
       for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -263,24 +201,14 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
   }
   phase_sync();
 
-  // geometry of corner pair q = (c, b) (prepared) or of corner q = (c, b, a)
-  // (fp64 arrays); two in flight
-  auto load_geo = [&](int q, eo::GeoStage<PREP> &g) {
-    if constexpr (PREP) {
-      const dd2 *src = gp + ep + (size_t)q * 7 * H3 + t;
+  // geometry of corner q = (c, b, a); two in flight
+  auto load_geo = [&](int q, eo::GeoStage &g) {
+    const size_t x = gidx((q >> 2) & 1, (q >> 1) & 1, q & 1);
+    const double *fld[7] = {g11, g22, g33, g12, g13, g23, h1};
 #pragma unroll
-      for (int f = 0; f < 7; ++f) {
-        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(src + (size_t)f * H3));
-        g.v[f] = dd2{v.x, v.y};
-      }
-    } else {
-      const size_t x = gidx((q >> 2) & 1, (q >> 1) & 1, q & 1);
-      const double *fld[7] = {g11, g22, g33, g12, g13, g23, h1};
-#pragma unroll
-      for (int f = 0; f < 7; ++f) g.v[f] = __ldg(fld[f] + x);
-    }
+    for (int f = 0; f < 7; ++f) g.v[f] = __ldg(fld[f] + x);
   };
-  eo::GeoStage<PREP> geo[2];
+  eo::GeoStage geo[2];
   if (active) load_geo(0, geo[0]);
 
   // ---- phase 2: reference gradient at the eight points
@@ -301,53 +229,7 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
   }
 
   // ---- phase 3: pointwise h1 G, the next geometry loading meanwhile
-  if constexpr (PREP) {  // point pairs a = 0, 1 as packed lanes
-    if (active && t == 0) {  // the geometry's exponent keys, recorded when it was prepared
-      atomicMax(&rec.ex[le][1], __ldg(gstat + 2 * (e0 + le)));
-      atomicMax(&rec.ex[le][2], __ldg(gstat + 2 * (e0 + le) + 1));
-    }
-    if (own) {
-      const u64 zero = pk(0.f, 0.f);
-#pragma unroll
-      for (int cp = 0; cp < 4; ++cp) {
-        const int c = cp >> 1, b = cp & 1;
-        if (active && cp + 1 < 4) load_geo(cp + 1, geo[(cp + 1) & 1]);
-        dd2 WR{zero, zero}, WS{zero, zero}, WT{zero, zero};
-        if (active) {
-          const eo::GeoStage<PREP> &g = geo[cp & 1];
-          const dd2 UR{pk(gr[c][b][0].hi, gr[c][b][1].hi), pk(gr[c][b][0].lo, gr[c][b][1].lo)};
-          const dd2 US{pk(gs_[c][b][0].hi, gs_[c][b][1].hi),
-                       pk(gs_[c][b][0].lo, gs_[c][b][1].lo)};
-          const dd2 UT{pk(gt[c][b][0].hi, gt[c][b][1].hi), pk(gt[c][b][0].lo, gt[c][b][1].lo)};
-          const u64 nR = neg2(UR.hi), nS = neg2(US.hi), nT = neg2(UT.hi);
-          const dd2 &G11 = g.v[0], &G22 = g.v[1], &G33 = g.v[2];
-          const dd2 &G12 = g.v[3], &G13 = g.v[4], &G23 = g.v[5], &HH = g.v[6];
-          const u64 nH = neg2(HH.hi);
-          acc2 a = prod2(UR, nR, G11);
-          mac2(a, US, nS, G12);
-          mac2(a, UT, nT, G13);
-          acc2 m = prod2(HH, nH, dd2{a.s, a.c});
-          WR = dd2{m.s, m.c};
-          a = prod2(UR, nR, G12);
-          mac2(a, US, nS, G22);
-          mac2(a, UT, nT, G23);
-          m = prod2(HH, nH, dd2{a.s, a.c});
-          WS = dd2{m.s, m.c};
-          a = prod2(UR, nR, G13);
-          mac2(a, US, nS, G23);
-          mac2(a, UT, nT, G33);
-          m = prod2(HH, nH, dd2{a.s, a.c});
-          WT = dd2{m.s, m.c};
-        }
-        gr[c][b][0] = df2{lx_(WR.hi), lx_(WR.lo)};
-        gr[c][b][1] = df2{ly_(WR.hi), ly_(WR.lo)};
-        gs_[c][b][0] = df2{lx_(WS.hi), lx_(WS.lo)};
-        gs_[c][b][1] = df2{ly_(WS.hi), ly_(WS.lo)};
-        gt[c][b][0] = df2{lx_(WT.hi), lx_(WT.lo)};
-        gt[c][b][1] = df2{ly_(WT.hi), ly_(WT.lo)};
-      }
-    }
-  } else {  // one point at a time, geometry split on the fly
+  {  // one point at a time, geometry split on the fly
     if (own) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -423,7 +305,6 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
     any_bad = __syncthreads_or(bad) != 0;
   }
 
-  double dsum = 0.0;
   // ---- phase 5: transposed half-size contractions, summed, stored
   if (own) {
 #pragma unroll
@@ -455,47 +336,24 @@ __device__ __forceinline__ void df64eo_body(double *__restrict__ w, const double
           const double wd0 = join(w0.hi, w0.lo), wd1 = join(w1.hi, w1.lo);
           w[gidx(c, b, 0)] = wd0;
           w[gidx(c, b, 1)] = wd1;
-          if (dotp) {  // u . Au of this element (u re-read from L2)
-            if constexpr (PUPD) {  // written above by this thread: coherent loads
-              dsum = __fma_rn(__ldcg(pw + gidx(c, b, 0)), wd0, dsum);
-              dsum = __fma_rn(__ldcg(pw + gidx(c, b, 1)), wd1, dsum);
-            } else {
-              dsum = __fma_rn(__ldg(u + gidx(c, b, 0)), wd0, dsum);
-              dsum = __fma_rn(__ldg(u + gidx(c, b, 1)), wd1, dsum);
-            }
-          }
         }
     }
   }
   if (any_bad) {  // fp64 units for the flagged elements (element- or block-uniform branch)
-    const double *uu = PUPD ? pw : u;
+    const double *uu = u;
     const int rank = (int)threadIdx.x - le * H3;
     if (elem_bar) {
       auto sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(1 + le), "r"(H3) : "memory"); };
       sync();  // phase 5 has read the lines that serve as scratch
       guard::element_f64<LX>(true, w, uu, dx, dx, dx, dxt, dxt, dxt, h1, g11, g22, g33, g12, g13, g23,
-                             eb, reinterpret_cast<double *>(Ar), rank, H3, sync,
-                             dotp ? &dsum : nullptr);
+                             eb, reinterpret_cast<double *>(Ar), rank, H3, sync, nullptr);
     } else {
       auto sync = [&]() { __syncthreads(); };
       sync();
       // every thread takes part in the barriers; only flagged elements compute
       guard::element_f64<LX>(bad, w, uu, dx, dx, dx, dxt, dxt, dxt, h1, g11, g22, g33, g12,
                                 g13, g23, eb, reinterpret_cast<double *>(Ar), own ? rank : 0,
-                                H3, sync, dotp ? &dsum : nullptr);
-    }
-  }
-  if (dotp) {  // one partial per block, fixed order (block-uniform branch)
-    __shared__ double red[32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) red[wid] = dsum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int k = 0; k < (int)((blockDim.x + 31) / 32); ++k) s += red[k];
-      dotp[blockIdx.x] = s;
+                                H3, sync, nullptr);
     }
   }
 }
@@ -512,65 +370,7 @@ ax_df64eo_kernel(double *__restrict__ w, const double *__restrict__ u,
   const long long e0 = (long long)blockIdx.x * epb;
   const long long left = nelv - e0;
   const int nel = left < epb ? (int)left : epb;
-  df64eo_body<LX, false>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nullptr, nullptr, e0,
-                         nel, epb, smem_raw);
-}
-
-// Same operator on geometry prepared by eo_prepare_kernel; DOT adds the
-// per-block partials of u . w; PUPD forms u = pw = minv .* r + beta pw first
-// (see df64eo_body).
-template <int LX, bool DOT, bool PUPD = false>
-__global__ void __launch_bounds__(256, 2)
-ax_df64eo_prep_kernel(double *__restrict__ w, const double *__restrict__ u,
-                      const double *__restrict__ dx, const double *__restrict__ dxt,
-                      const df::dd2 *__restrict__ gp, const unsigned *__restrict__ gstat,
-                      guard::RawGeo raw, int nelv, int epb,
-                      double *__restrict__ dotp, double *__restrict__ pw,
-                      const double *__restrict__ r_in, const double *__restrict__ minv_in,
-                      const double *__restrict__ beta_p, const double *__restrict__ corr_in,
-                      const int *__restrict__ use_corr_p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const long long e0 = (long long)blockIdx.x * epb;
-  const long long left = nelv - e0;
-  const int nel = left < epb ? (int)left : epb;
-  df64eo_body<LX, true, PUPD, false>(w, u, dx, dxt, raw.h1, raw.g11, raw.g22, raw.g33, raw.g12,
-                                     raw.g13, raw.g23, gp, gstat, e0, nel, epb, smem_raw,
-                                     DOT ? dotp : nullptr, pw, r_in, minv_in, beta_p, corr_in,
-                                     use_corr_p);
-}
-
-// Prepared geometry: entry ((e*4 + cp)*7 + f)*H3 + t holds field f at the
-// two points a = 0, 1 of corner pair cp = (c, b) of thread t, split into
-// double-float pairs exactly as the kernel above splits them.  fmask selects
-// the fields to (re)write (bit f; bit 6 = h1).  The buffer ends with two
-// exponent keys per element (largest of the six G fields, of h1; guard.cuh),
-// written by geo_keys_kernel.
-template <int LX>
-__global__ void eo_prepare_kernel(df::dd2 *__restrict__ gp, const double *__restrict__ h1,
-                                  const double *__restrict__ g11,
-                                  const double *__restrict__ g22,
-                                  const double *__restrict__ g33,
-                                  const double *__restrict__ g12,
-                                  const double *__restrict__ g13,
-                                  const double *__restrict__ g23, int nelv, int fmask) {
-  using namespace df;
-  constexpr int H = LX / 2, N = LX - 1, H3 = H * H * H, N3 = LX * LX * LX;
-  const int64_t total = (int64_t)nelv * eo::prep_entries<LX>();
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int t = (int)(q % H3);
-    const int f = (int)((q / H3) % 7);
-    if (!((fmask >> f) & 1)) continue;
-    const int cp = (int)((q / (7 * H3)) % 4);
-    const int64_t e = q / eo::prep_entries<LX>();
-    const int ip = t % H, jp = (t / H) % H, kp = t / (H * H);
-    const int k = (cp >> 1) ? N - kp : kp, j = (cp & 1) ? N - jp : jp;
-    const double *fld = f == 0 ? g11 : f == 1 ? g22 : f == 2 ? g33 : f == 3 ? g12 : f == 4 ? g13
-                      : f == 5 ? g23 : h1;
-    const size_t row = (size_t)e * N3 + (size_t)(k * LX + j) * LX;
-    const df2 a0 = split(fld[row + ip]), a1 = split(fld[row + N - ip]);
-    gp[q] = dd2{pk(a0.hi, a1.hi), pk(a0.lo, a1.lo)};
-  }
+  df64eo_body<LX>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, e0, nel, epb, smem_raw);
 }
 
 template <int LX>
@@ -588,61 +388,6 @@ int launch_df64eo(double *w, const double *u, const double *dx, const double *dx
   const unsigned grid = (unsigned)((nelv + epb - 1) / epb);
   kern<<<grid, epb * H3, smem, stream>>>(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nelv,
                                          epb);
-  return launch_status();
-}
-
-// dotp (optional): one partial of sum u . w per block, gridDim = ceil(nelv /
-// epb) of them (prep_blocks).
-template <int LX>
-int prep_blocks(int nelv, int epb) {
-  constexpr int H3 = (LX / 2) * (LX / 2) * (LX / 2);
-  if (epb <= 0) epb = 128 / H3 < 1 ? 1 : 128 / H3;
-  return (nelv + epb - 1) / epb;
-}
-
-// pw (with dotp, r_in, minv_in, beta_p): the fused direction update.
-template <int LX>
-int launch_df64eo_prep(double *w, const double *u, const double *dx, const double *dxt,
-                       const df::dd2 *gp, const guard::RawGeo &raw, int nelv, int epb,
-                       cudaStream_t stream,
-                       double *dotp = nullptr, double *pw = nullptr,
-                       const double *r_in = nullptr, const double *minv_in = nullptr,
-                       const double *beta_p = nullptr, const double *corr_in = nullptr,
-                       const int *use_corr_p = nullptr) {
-  if (pw && !(dotp && r_in && minv_in && beta_p)) return AX_EINVAL;
-  if (corr_in && !use_corr_p) return AX_EINVAL;
-  constexpr int H3 = (LX / 2) * (LX / 2) * (LX / 2);
-  // measured on GB300 (E = 32768 at lx = 8, 13824 at lx = 10): blocks of
-  // about 128 threads (4 per SM) beat 256-thread blocks by 8-9 %
-  if (epb <= 0) epb = 128 / H3 < 1 ? 1 : 128 / H3;
-  if (epb * H3 > 256) return AX_EINVAL;
-  const size_t smem = df64eo_smem<LX>(epb);
-  const int kind = pw ? 2 : dotp ? 1 : 0;
-  auto kern = kind == 2   ? ax_df64eo_prep_kernel<LX, true, true>
-              : kind == 1 ? ax_df64eo_prep_kernel<LX, true>
-                          : ax_df64eo_prep_kernel<LX, false>;
-  static std::atomic<size_t> granted[3][kMaxDevices];
-  if (!grant_smem(kern, smem, granted[kind])) return AX_EINVAL;
-  const unsigned grid = (unsigned)((nelv + epb - 1) / epb);
-  const unsigned *gstat = reinterpret_cast<const unsigned *>(gp + (size_t)nelv * eo::prep_entries<LX>());
-  kern<<<grid, epb * H3, smem, stream>>>(w, u, dx, dxt, gp, gstat, raw, nelv, epb, dotp, pw, r_in,
-                                         minv_in, beta_p, corr_in, use_corr_p);
-  return launch_status();
-}
-
-template <int LX>
-int launch_eo_prepare(df::dd2 *gp, const double *h1, const double *g11, const double *g22,
-                      const double *g33, const double *g12, const double *g13,
-                      const double *g23, int nelv, int fmask, cudaStream_t stream) {
-  const int64_t total = (int64_t)nelv * eo::prep_entries<LX>();
-  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
-  eo_prepare_kernel<LX><<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, stream>>>(
-      gp, h1, g11, g22, g33, g12, g13, g23, nelv, fmask);
-  int rc = launch_status();
-  if (rc) return rc;
-  unsigned *keys = reinterpret_cast<unsigned *>(gp + (size_t)nelv * eo::prep_entries<LX>());
-  geo_keys_kernel<<<(unsigned)std::max<int64_t>(((int64_t)nelv + 7) / 8, 1), 256, 0, stream>>>(
-      keys, h1, g11, g22, g33, g12, g13, g23, nelv, LX * LX * LX);
   return launch_status();
 }
 

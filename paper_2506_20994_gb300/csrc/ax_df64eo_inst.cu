@@ -19,23 +19,6 @@ int dispatch_df64eo(int lx, double *w, const double *u, const double *dx, const 
   }
 }
 
-int dispatch_df64eo_prep(int lx, double *w, const double *u, const double *dx,
-                         const double *dxt, const df::dd2 *gp, const guard::RawGeo &raw,
-                         int nelv, int epb, cudaStream_t st, double *dotp, double *pw, const double *r_in,
-                         const double *minv_in, const double *beta_p, const double *corr_in,
-                         const int *use_corr_p) {
-  switch (lx) {
-#define AX_CASE(L)                                                                             \
-  case L:                                                                                      \
-    return launch_df64eo_prep<L>(w, u, dx, dxt, gp, raw, nelv, epb, st, dotp, pw, r_in,      \
-                                 minv_in, beta_p, corr_in, use_corr_p);
-    AX_CASE(4) AX_CASE(6) AX_CASE(8) AX_CASE(10) AX_CASE(12)
-#undef AX_CASE
-    default:
-      return AX_EINVAL;
-  }
-}
-
 __global__ void geo_keys_kernel(unsigned *__restrict__ keys, const double *__restrict__ h1,
                                 const double *__restrict__ g11, const double *__restrict__ g22,
                                 const double *__restrict__ g33, const double *__restrict__ g12,
@@ -58,32 +41,6 @@ __global__ void geo_keys_kernel(unsigned *__restrict__ keys, const double *__res
   if (lane == 0) {
     keys[2 * e] = kg;
     keys[2 * e + 1] = kh;
-  }
-}
-
-int df64eo_prep_blocks(int lx, int nelv) {
-  switch (lx) {
-    case 4: return prep_blocks<4>(nelv, 0);
-    case 6: return prep_blocks<6>(nelv, 0);
-    case 8: return prep_blocks<8>(nelv, 0);
-    case 10: return prep_blocks<10>(nelv, 0);
-    case 12: return prep_blocks<12>(nelv, 0);
-    default: return 0;
-  }
-}
-
-int dispatch_eo_prepare(int lx, df::dd2 *gp, const double *h1, const double *g11,
-                        const double *g22, const double *g33, const double *g12,
-                        const double *g13, const double *g23, int nelv, int fmask,
-                        cudaStream_t st) {
-  switch (lx) {
-#define AX_CASE(L)                                                                             \
-  case L:                                                                                      \
-    return launch_eo_prepare<L>(gp, h1, g11, g22, g33, g12, g13, g23, nelv, fmask, st);
-    AX_CASE(4) AX_CASE(6) AX_CASE(8) AX_CASE(10) AX_CASE(12)
-#undef AX_CASE
-    default:
-      return AX_EINVAL;
   }
 }
 

@@ -145,9 +145,11 @@ struct EopPos {
 };
 
 // The operator handle's sequence: elements blockIdx.x, + gridDim.x, ... of
-// one mesh.
+// one mesh.  The mesh operands are held by value (copies of kernel
+// parameters), so the compiler reads them from the constant bank; through a
+// pointer every per-element access would be a load.
 struct SeqOne {
-  const EopMesh *m;
+  EopMesh m;
   long long nelv;
   AX_D bool first(EopPos &p) const {
     p = EopPos{0, (long long)blockIdx.x};
@@ -159,7 +161,7 @@ struct SeqOne {
   }
   AX_D int mesh_of(const EopPos &) const { return 0; }
   AX_D long long elem(const EopPos &p) const { return p.off; }
-  AX_D const EopMesh &mesh(int) const { return *m; }
+  AX_D const EopMesh &mesh(int) const { return m; }
 };
 
 // Persistent even-odd body over the element sequence `seq` of one group of
@@ -260,7 +262,7 @@ AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
   EopPos pos;
   bool have = seq.first(pos);
   int cmesh = -1;  // mesh whose coefficients are staged
-  sync();
+  sync();  // the barrier is initialised before anyone waits on it
   if (tid == 0 && have) {
     const EopMesh &M = seq.mesh(seq.mesh_of(pos));
     bulk_load(smem_u32(Gs), M.gp + (size_t)seq.elem(pos) * C::GE, C::GBYTES, bar);
@@ -289,18 +291,19 @@ AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
   if (real && have) load_in(pos);
 
   uint32_t parity = 0;
-  for (; have; parity ^= 1u) {
+  // outer loop: runs of elements of one mesh, whose coefficients are staged
+  // before the run (measured: staging them inside the element loop, even
+  // behind a test that is false after the first element, cost 6 %)
+  while (have) {
+    cmesh = seq.mesh_of(pos);
+    load_coef(seq.mesh(cmesh));  // the previous element's last barrier freed them
+  for (; have && seq.mesh_of(pos) == cmesh; parity ^= 1u) {
     EopPos nxp;
     const bool more = seq.advance(pos, nxp);
-    const int mi = seq.mesh_of(pos);
-    const EopMesh &M = seq.mesh(mi);
+    const EopMesh &M = seq.mesh(cmesh);
     const size_t eb = (size_t)seq.elem(pos) * N3;
     // this element's admissible exponent fields of u (guard.cuh, u_range)
     const uint2 ur_e = __ldg(M.urange + seq.elem(pos));
-    if (mi != cmesh) {  // group-uniform: the staged coefficients of this mesh
-      load_coef(M);
-      cmesh = mi;
-    }
     // ---- phase 1: this element's u (or the direction formed here), split,
     // lines of the three directions; the next element's inputs start loading
     double ucur[2][2];
@@ -376,6 +379,7 @@ AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
         if (err) atomicExch(err, 1);
         (void)mbar_wait(bar, parity, kWaitLimit);
       }
+      have = false;
       break;
     }
     if (tid == 0 && more) {
@@ -421,6 +425,7 @@ AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
     pos = nxp;
     have = more;
   }
+  }
   if (tid == 0) {  // no copy is pending here: the barrier may be reused as plain memory
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
   }
@@ -430,8 +435,8 @@ AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
 // DOT: one partial of u . w per CTA (fixed order) in dotp[blockIdx.x].
 template <int LX, bool DOT, bool PUPD>
 __global__ void __launch_bounds__(Cfg<LX>::NTB, Cfg<LX>::MINB)
-ax_eop_kernel(const __grid_constant__ EopMesh mesh, long long nelv, int *__restrict__ err,
-              double *__restrict__ dotp, const __grid_constant__ EopUpd up0,
+ax_eop_kernel(const EopMesh mesh, long long nelv, int *__restrict__ err,
+              double *__restrict__ dotp, const EopUpd up0,
               const double *__restrict__ beta_p, const int *__restrict__ use_corr_p) {
   using C = Cfg<LX>;
   extern __shared__ __align__(128) unsigned char sm[];
@@ -440,7 +445,7 @@ ax_eop_kernel(const __grid_constant__ EopMesh mesh, long long nelv, int *__restr
     up.beta = *beta_p;
     up.use_corr = up.corr != nullptr && *use_corr_p != 0;
   }
-  const SeqOne seq{&mesh, nelv};
+  const SeqOne seq{mesh, nelv};
   double dsum = 0.0;
   eop_run<LX, DOT, PUPD>(
       sm, (int)threadIdx.x, seq, [] { __syncthreads(); },

@@ -53,29 +53,13 @@ int dispatch_df64eo(int lx, double *w, const double *u, const double *dx, const 
                     const double *g12, const double *g13, const double *g23, int nelv, int epb,
                     cudaStream_t st);
 inline bool df64eo_supported(int lx) { return lx >= 4 && lx <= 12 && lx % 2 == 0; }
-// The same kernel on geometry prepared by dispatch_eo_prepare (df::dd2
-// entries, 56 lx^3 bytes per element); fmask picks the fields to write
-// (bits 0-5 g11, g22, g33, g12, g13, g23; bit 6 h1).
-// dotp (optional): per-block partial sums of u . w, df64eo_prep_blocks(lx,
-// nelv) of them (default elements per block).
-// pw, r_in, minv_in, beta_p (optional, with dotp): u is replaced by the
-// search direction formed in place, pw = minv_in .* r_in + (*beta_p) pw.
-// raw: the fp64 geometry the prepared copy came from (elements outside the
-// double-float range are recomputed from it with fp64 units).
-int dispatch_df64eo_prep(int lx, double *w, const double *u, const double *dx,
-                         const double *dxt, const df::dd2 *gp, const guard::RawGeo &raw,
-                         int nelv, int epb, cudaStream_t st, double *dotp = nullptr, double *pw = nullptr,
-                         const double *r_in = nullptr, const double *minv_in = nullptr,
-                         const double *beta_p = nullptr, const double *corr_in = nullptr,
-                         const int *use_corr_p = nullptr);
-int df64eo_prep_blocks(int lx, int nelv);
 // Persistent even-odd operator of the operator handle (ax_eo_persist.cuh),
 // lx in {6, 8, 10, 12}.  gp: geometry prepared by eop_prepare (eo_prep_bytes
 // bytes, the keys at its end); coef: the block eop_coefficients writes
 // (eop_coef_bytes, device); dfield: its matrices' exponent field.  dotp:
 // one partial of u . w per CTA, eop_blocks(lx, nelv, true) of them; pw, r,
-// minv, beta (+ corr, use_corr): the fused direction update (as
-// dispatch_df64eo_prep).  err: device word set to 1 if a staged copy never
+// minv, beta (+ corr, use_corr): the fused direction update, pw = minv .* r
+// (+ corr when *use_corr) + (*beta) pw formed in place before the apply.  err: device word set to 1 if a staged copy never
 // arrived (may be null).
 struct EopArgs {
   double *w = nullptr;
@@ -104,10 +88,7 @@ bool eop_coefficients(int lx, const double *dx_host, const double *dxt_host, voi
 inline size_t eo_prep_bytes(int lx, int nelv) {
   return (size_t)nelv * 56 * lx * lx * lx + (size_t)nelv * 8;
 }
-int dispatch_eo_prepare(int lx, df::dd2 *gp, const double *h1, const double *g11,
-                        const double *g22, const double *g33, const double *g12,
-                        const double *g13, const double *g23, int nelv, int fmask,
-                        cudaStream_t st);
+
 
 // fp64-accurate double-float kernel, lx in 2..7 (a), 8..10 (b), 11..12 (c),
 // 13..14 (d), 15..16 (e); AX_EINVAL above AX_DF64_LX_MAX.
