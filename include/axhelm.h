@@ -311,10 +311,11 @@ int ax_poisson_set_check_every(ax_poisson *P, int every);
  * a fixed device array inside the library of AX_NOALLOC_MAX_POINTS doubles
  * (4 MiB, reserved on every GPU that loads the library until exit); larger
  * problems return AX_EINVAL, as does a gs handle of another size.  Calls no
- * cudaMalloc/cudaFree.  The first call on a device resolves the array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * race and must be serialised by the caller.  Asynchronous on stream. */
+ * cudaMalloc/cudaFree.  The first call on a device, and the first after
+ * the device's context changed (cudaDeviceReset), resolves the array's
+ * device address (cudaGetSymbolAddress); make that call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race
+ * and must be serialised by the caller.  Asynchronous on stream. */
 #define AX_NOALLOC_MAX_POINTS (1 << 19)
 int ax_jacobi_noalloc(double *minv, const double *dx, const double *h1, const double *g11,
                       const double *g22, const double *g33, const double *g12,

@@ -843,6 +843,8 @@ int ax_mpcg_solve(ax_poisson *P, int mode, double *x, const double *b, double to
 // ---------------------------------------------------------------------------
 #include <mutex>
 
+#include <cuda.h>
+
 static __device__ __align__(256) double g_noalloc_diag[AX_NOALLOC_MAX_POINTS];
 
 namespace {
@@ -856,10 +858,47 @@ __global__ void noalloc_minv_kernel(double *__restrict__ minv, const double *__r
 
 constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mu;
-double *g_noalloc_ptr[kNoallocMaxDevices];  // device address of the array, per device
+// Device address of the array per device, and the context it was resolved
+// in: a context created after cudaDeviceReset may hold the module at another
+// address, so the address is resolved again when the context changes.
+double *g_noalloc_ptr[kNoallocMaxDevices];
+unsigned long long g_noalloc_ctx[kNoallocMaxDevices];
 
-// Device address of the scratch array on the current device; resolved once
-// per device (host code cannot use the symbol itself as an address).
+// Id of the current context through the driver's entry points (cuCtxGetCurrent,
+// cuCtxGetId; no link against the driver library); 0 when unavailable, in
+// which case the address is resolved on every call.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext *);
+  using GetId = CUresult (*)(CUcontext, unsigned long long *);
+  static GetCurrent get_current = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    (void)cudaGetLastError();
+    return reinterpret_cast<GetCurrent>(f);
+  }();
+  static GetId get_id = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    (void)cudaGetLastError();
+    return reinterpret_cast<GetId>(f);
+  }();
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c ||
+      get_id(c, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device (host code
+// cannot use the symbol itself as an address): resolved once per device and
+// context.
 int noalloc_scratch(double **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -867,14 +906,21 @@ int noalloc_scratch(double **out) {
     return AX_ELAUNCH;
   }
   if (dev < 0 || dev >= kNoallocMaxDevices) return AX_EINVAL;
+  // a runtime call makes sure the device's primary context is current
+  if (cudaFree(nullptr) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return AX_ELAUNCH;
+  }
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  if (!g_noalloc_ptr[dev] || ctx == 0 || g_noalloc_ctx[dev] != ctx) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_diag) != cudaSuccess || !p) {
       (void)cudaGetLastError();
       return AX_ELAUNCH;
     }
     g_noalloc_ptr[dev] = static_cast<double *>(p);
+    g_noalloc_ctx[dev] = ctx;
   }
   *out = g_noalloc_ptr[dev];
   return AX_OK;

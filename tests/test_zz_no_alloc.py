@@ -7,9 +7,12 @@ test calls it through the C ABI twice in a row, with two different
 coefficients h1, and checks each result against the array that the
 allocating path (ax_poisson_create / ax_poisson_jacobi) computes: same
 kernels and summation order, so the bits must agree (the relative 1e-12
-tolerance of the other fp64 tests is also asserted).  It also checks that a
-problem larger than the fixed scratch is rejected.  This file is named to
-be collected last.
+tolerance of the other fp64 tests is also asserted).  Each result is also
+compared with the oracle's masked inverse of the assembled diagonal
+(jacobi_diagonal, then gs_sum), and the device's free memory is checked to be
+the same before and after a warmed-up call.  It also checks that a problem
+larger than the fixed scratch is rejected.  This file is named to be
+collected last.
 """
 import numpy as np
 import pytest
@@ -19,6 +22,8 @@ pytestmark = pytest.mark.gpu
 
 import paper_2506_20994_gb300 as ax  # noqa: E402
 from paper_2506_20994_gb300 import _lib, synth  # noqa: E402
+
+import oracle  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -52,6 +57,29 @@ def test_noalloc_jacobi_matches_allocating_path_twice():
         a, b = out.cpu().numpy(), ref.cpu().numpy()
         assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
         assert torch.equal(out, ref)
+        # the oracle's masked inverse of the assembled diagonal
+        c = {k: P.d[k].cpu().numpy() for k in ("dx", "h1", "mask", *ax.Poisson.GKEYS)}
+        dg = oracle.gs_sum(oracle.jacobi_diagonal(c["dx"], c["h1"],
+                                                  *[c[k] for k in ax.Poisson.GKEYS], lx),
+                           P.glob).reshape(-1)
+        m = c["mask"].reshape(-1)
+        want = np.where(m > 0, 1.0 / np.where(dg != 0, dg, 1.0), 0.0)
+        assert np.linalg.norm(a - want) <= 1e-12 * np.linalg.norm(want)
+
+
+def test_noalloc_jacobi_leaves_free_memory_unchanged():
+    lx = 8
+    P = ax.Poisson(synth.box_vertices(4, 4, 4, seed=21), lx)
+    out = torch.empty(P.nelv * lx ** 3, dtype=torch.float64, device="cuda")
+    assert _call(P, P.d["h1"], out) == _lib.AX_OK  # loads the kernels, resolves the scratch
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert _call(P, P.d["h1"], out) == _lib.AX_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.equal(out, P.jacobi())
 
 
 def test_noalloc_rejects_oversize_and_bad_handle():
