@@ -96,6 +96,11 @@ int ax_helm_f32(float *w, const float *u, const float *dx, const float *dxt, con
                 const float *g13, const float *g23, int lx, int nelv, void *stream) {
   int rc = check_args(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx, nelv);
   if (rc != AX_OK) return rc > 0 ? AX_OK : rc;
+  if (ax::eo32_ok(lx, w, u, h1, g11, g22, g33, g12, g13, g23)) {
+    const float *g[7] = {h1, g11, g22, g33, g12, g13, g23};
+    return ax::dispatch_eo32_f32(lx, w, u, dx, dxt, g, nelv, nullptr, nullptr,
+                                 (cudaStream_t)stream);
+  }
   return ax::dispatch_kstep_f32(lx, w, u, dx, dxt, h1, g11, g22, g33, g12, g13,
                                              g23, nelv, ax::tuned_epb(AX_BATCH_F32, lx),
                                              (cudaStream_t)stream);
@@ -109,6 +114,11 @@ int ax_helm_bf16(float *w, const ax_bf16 *u, const float *dx, const float *dxt,
   if (rc != AX_OK) return rc > 0 ? AX_OK : rc;
   using B = __nv_bfloat16;
   auto c = [](const ax_bf16 *p) { return reinterpret_cast<const B *>(p); };
+  if (ax::eo32_ok(lx, w, u, h1, g11, g22, g33, g12, g13, g23)) {
+    const B *g[7] = {c(h1), c(g11), c(g22), c(g33), c(g12), c(g13), c(g23)};
+    return ax::dispatch_eo32_bf16(lx, w, c(u), dx, dxt, g, nelv, nullptr, nullptr,
+                                  (cudaStream_t)stream);
+  }
   return ax::dispatch_kstep_bf16(lx, w, c(u), dx, dxt, c(h1), c(g11), c(g22), c(g33),
                                          c(g12), c(g13), c(g23), nelv, 0, (cudaStream_t)stream);
 }

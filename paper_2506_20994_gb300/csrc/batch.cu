@@ -50,6 +50,8 @@ double elem_cost(int lx, bool f64, bool eo) {
   double ns;
   if (f64 && eo)
     ns = lx == 6 ? 10.8 : lx == 8 ? 7.2 : 8.6;
+  else if (eo)  // fp32 even-odd body: single-mesh rates scaled to the batch CTA
+    ns = lx <= 6 ? 3.9 : lx == 8 ? 3.0 : 4.2;
   else if (f64)
     ns = 13.0;
   else
@@ -75,6 +77,7 @@ struct ax_batch {
   size_t smem = 0;
   BatchMeshDev *d_mesh = nullptr;
   ax::eop::EopMesh *d_emesh = nullptr;
+  ax::F32Mesh *d_fmesh = nullptr;
   BatchItem *d_items = nullptr;
   BatchGroup *d_groups = nullptr;
   int *d_start = nullptr;
@@ -92,8 +95,8 @@ int batch_launch_raw(ax_batch *B, cudaStream_t st) {
   if (B->dtype == AX_BATCH_F64)
     return ax::batch_launch_f64(B->nblocks, B->smem, B->d_mesh, B->d_emesh, B->d_items,
                                 B->d_groups, B->d_start, B->d_err, st);
-  return ax::batch_launch_f32(B->nblocks, B->smem, B->d_mesh, B->d_items, B->d_groups,
-                              B->d_start, st);
+  return ax::batch_launch_f32(B->nblocks, B->smem, B->d_mesh, B->d_fmesh, B->d_items,
+                              B->d_groups, B->d_start, B->d_err, st);
 }
 
 template <typename T>
@@ -114,6 +117,7 @@ int ax_batch_destroy(ax_batch *B) {
   if (B->graph) cudaGraphDestroy(B->graph);
   cudaFree(B->d_mesh);
   cudaFree(B->d_emesh);
+  cudaFree(B->d_fmesh);
   cudaFree(B->d_items);
   cudaFree(B->d_groups);
   cudaFree(B->d_start);
@@ -147,6 +151,7 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
   };
   std::vector<BatchMeshDev> mh(nmesh);
   std::vector<ax::eop::EopMesh> em(nmesh);
+  std::vector<ax::F32Mesh> fm(nmesh);
   std::vector<int> mbody(nmesh, ax::kBodyKLoop);
   double flops = 0, bytes = 0, total_cost = 0;
   for (int m = 0; m < nmesh; ++m) {
@@ -157,7 +162,23 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
     const double l3 = (double)s.lx * s.lx * s.lx;
     flops += (double)s.nelv * (12.0 * l3 * s.lx + 18.0 * l3);
     bytes += (double)s.nelv * 9.0 * l3 * (f64 ? 8 : 4);
-    if (!f64 || s.nelv == 0 || choose_body(s.lx) != ax::kBodyEvenOdd) continue;
+    if (!f64) {
+      // fp32: the even-odd body exactly where ax_helm_f32 takes it
+      auto fl = [](const void *q) { return static_cast<const float *>(q); };
+      if (s.nelv > 0 && ax::batch_e32_ok(s.lx) &&
+          ax::eo32_ok(s.lx, s.w, s.u, s.h1, s.g11, s.g22, s.g33, s.g12, s.g13, s.g23)) {
+        ax::F32Mesh &f = fm[m];
+        f.w = static_cast<float *>(s.w);
+        f.u = fl(s.u);
+        const void *g[7] = {s.h1, s.g11, s.g22, s.g33, s.g12, s.g13, s.g23};
+        for (int q = 0; q < 7; ++q) f.g[q] = fl(g[q]);
+        f.dx = fl(s.dx);
+        f.dxt = fl(s.dxt);
+        mbody[m] = ax::kBodyEvenOdd;
+      }
+      continue;
+    }
+    if (s.nelv == 0 || choose_body(s.lx) != ax::kBodyEvenOdd) continue;
     // even-odd layout: the matrices must be centro-antisymmetric; geometry and
     // coefficients are prepared here, once, as the operator handle does
     const int lx = s.lx;
@@ -283,6 +304,7 @@ int ax_batch_create(ax_batch **out, int dtype, int nmesh, const ax_batch_mesh *m
   B->flops = flops;
   B->bytes = bytes;
   bool ok = upload(&B->d_mesh, mh, st) && upload(&B->d_emesh, em, st) &&
+            upload(&B->d_fmesh, fm, st) &&
             upload(&B->d_items, flat, st) && upload(&B->d_groups, groups, st) &&
             upload(&B->d_start, start, st) &&
             cudaMalloc((void **)&B->d_err, sizeof(int)) == cudaSuccess &&

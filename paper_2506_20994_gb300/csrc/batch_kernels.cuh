@@ -12,6 +12,8 @@
 //    concatenated items and streams the next one's geometry in while it
 //    computes the current one.  The arithmetic is the handle's, so results
 //    equal ax_op_apply's bit for bit.
+//  * fp32, lx in {6, 8, 10} with 16-byte aligned arrays: the persistent
+//    even-odd fp32 body of ax_helm_f32 (ax_eo32.cuh), in slots the same way;
 //  * every other case: the k-loop body of the single-mesh kernels
 //    (double-float for fp64, fp32 for fp32) in chunks of
 //    kBatchThreads / lx^2 elements, bit for bit ax_helm's / ax_helm_f32's.
@@ -23,6 +25,7 @@
 #pragma once
 
 #include "ax_df64.cuh"
+#include "ax_eo32.cuh"
 #include "ax_eo_persist.cuh"
 #include "ax_kstep.cuh"
 
@@ -58,11 +61,12 @@ __host__ __device__ constexpr int batch_kloop_epb(int lx) {
 }
 
 // The even-odd slots' sequence: elements slot, slot + S, ... of the
-// concatenation of items [ib, ie).
-struct SeqItems {
+// concatenation of items [ib, ie); M: the body's mesh operands.
+template <class M>
+struct SeqItemsT {
   const BatchItem *items;
   int ib, ie, slot, S;
-  const eop::EopMesh *meshes;
+  const M *meshes;
   AX_D bool norm(eop::EopPos &p) const {
     while (p.it < ie && p.off >= items[p.it].nel) {
       p.off -= items[p.it].nel;
@@ -80,8 +84,10 @@ struct SeqItems {
   }
   AX_D int mesh_of(const eop::EopPos &p) const { return items[p.it].mesh; }
   AX_D long long elem(const eop::EopPos &p) const { return items[p.it].e0 + p.off; }
-  AX_D const eop::EopMesh &mesh(int m) const { return meshes[m]; }
+  AX_D const M &mesh(int m) const { return meshes[m]; }
 };
+using SeqItems = SeqItemsT<eop::EopMesh>;
+using F32Mesh = e32::Mesh<float, float>;
 
 // Bytes of one even-odd slot's shared memory (128-byte aligned).
 template <int LX>
@@ -121,6 +127,45 @@ __device__ __noinline__ void batch_run_eo(const BatchGroup &G, const BatchItem *
                                  sync_and, err, up, dsum);
 }
 
+// fp32 meshes of these orders with 16-byte aligned arrays run the even-odd
+// fp32 body (that of ax_helm_f32, bit for bit); its lx = 12 form needs 432
+// threads, so lx 12 runs the k-loop body here.
+__host__ __device__ constexpr bool batch_e32_ok(int lx) { return lx == 6 || lx == 8 || lx == 10; }
+template <int LX>
+constexpr size_t batch_e32_slot_bytes() {
+  return (e32::Cfg<LX, float, float>::SMEM + 127) / 128 * 128;
+}
+template <int LX>
+constexpr int batch_e32_slots() {
+  return kBatchThreads / e32::Cfg<LX, float, float>::NTB;
+}
+
+template <int LX>
+__device__ __noinline__ void batch_run_e32(const BatchGroup &G, const BatchItem *items,
+                                           const F32Mesh *fmesh, unsigned char *sm, int *err) {
+  using C = e32::Cfg<LX, float, float>;
+  constexpr int S = batch_e32_slots<LX>();
+  const int slot = (int)threadIdx.x / C::NTB;
+  if (slot >= S) return;
+  const int tid = (int)threadIdx.x - slot * C::NTB;
+  const unsigned bid = 1u + (unsigned)slot;
+  const SeqItemsT<F32Mesh> seq{items, G.ib, G.ie, slot, S, fmesh};
+  auto sync = [bid] { asm volatile("bar.sync %0, %1;" ::"r"(bid), "r"(C::NTB) : "memory"); };
+  auto sync_and = [bid](bool p) {
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred a, b;\n\tsetp.ne.u32 a, %1, 0;\n\t"
+        "bar.red.and.pred b, %2, %3, a;\n\tselp.u32 %0, 1, 0, b;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)p), "r"(bid), "r"(C::NTB)
+        : "memory");
+    return r != 0u;
+  };
+  double dsum = 0.0;
+  e32::e32_run<LX, float, float, false, false>(sm + (size_t)slot * batch_e32_slot_bytes<LX>(),
+                                               tid, seq, sync, sync_and, err, dsum);
+}
+
 template <bool F64, int LX>
 __device__ __noinline__ void batch_run_kloop(const BatchGroup &G, const BatchItem *items,
                                                 const BatchMeshDev *meshes, unsigned char *sm) {
@@ -155,8 +200,8 @@ int batch_launch_f64(int nblocks, size_t smem, const BatchMeshDev *meshes,
                      const eop::EopMesh *emesh, const BatchItem *items, const BatchGroup *groups,
                      const int *cta_start, int *err, cudaStream_t st);
 int batch_launch_f32(int nblocks, size_t smem, const BatchMeshDev *meshes,
-                     const BatchItem *items, const BatchGroup *groups, const int *cta_start,
-                     cudaStream_t st);
+                     const F32Mesh *fmesh, const BatchItem *items, const BatchGroup *groups,
+                     const int *cta_start, int *err, cudaStream_t st);
 size_t batch_key_smem_f64(int key);
 size_t batch_key_smem_f32(int key);
 int batch_setup_f64(size_t smem, int *blocks_per_sm);

@@ -13,6 +13,7 @@
 // nodes).  Inner products run over unique global nodes, i.e. the local sum
 // weighted by 1/multiplicity.  The scalars of the iteration live on the
 // device; the host reads the residual norm every `check_every` iterations.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -366,7 +367,8 @@ struct ax_poisson {
   ax_op *op = nullptr;  // the operator (prepared geometry where it applies)
   double *dotp = nullptr;  // per-block partials of p . Ap from the fused apply
   int ndot = 0;            // partials of the fp64 (prepared-geometry) apply
-  int ndot32 = 0;          // partials of the fp32 / bf16-data k-loop apply
+  int ndot32 = 0;          // partials of the fp32 / bf16-data apply
+  bool lowp_eo32 = false;  // that apply runs the even-odd fp32 kernel
   float *sqm = nullptr;  // sqrt(minv) in fp32 for the symmetric learned form (lazily)
   double *hb = nullptr;  // h2 .* B of the Helmholtz problem, or null (Poisson)
   float *hb32 = nullptr;  // its fp32 copy for the mixed-precision solves
@@ -409,11 +411,22 @@ int apply_f64(ax_poisson *P, double *w, const double *u, cudaStream_t st) {
   return ax_gs_sum(P->gs, w, st);
 }
 
-// dotp: also the per-block partials of u . Ax (kstep_blocks of them)
+// dotp: also the per-block partials of u . Ax (P->ndot32 of them)
 int apply_lowp(ax_poisson *P, float *w, const float *u, cudaStream_t st,
                double *dotp = nullptr) {
   int rc;
-  if (P->lowp_mode == 2) {
+  if (P->lowp_eo32 && P->lowp_mode == 2) {
+    auto b = [](const void *x) { return reinterpret_cast<const __nv_bfloat16 *>(x); };
+    const __nv_bfloat16 *g[7] = {b(P->h1lp), b(P->glp[0]), b(P->glp[1]), b(P->glp[2]),
+                                 b(P->glp[3]), b(P->glp[4]), b(P->glp[5])};
+    rc = ax::dispatch_eo32_f32u_bf16(P->lx, w, u, P->dx32, P->dxt32, g, P->nelv, nullptr, dotp,
+                                     st);
+  } else if (P->lowp_eo32) {
+    auto f = [](const void *x) { return reinterpret_cast<const float *>(x); };
+    const float *g[7] = {f(P->h1lp), f(P->glp[0]), f(P->glp[1]), f(P->glp[2]),
+                         f(P->glp[3]), f(P->glp[4]), f(P->glp[5])};
+    rc = ax::dispatch_eo32_f32(P->lx, w, u, P->dx32, P->dxt32, g, P->nelv, nullptr, dotp, st);
+  } else if (P->lowp_mode == 2) {
     auto b = [](const void *x) { return reinterpret_cast<const __nv_bfloat16 *>(x); };
     // u is fp32: the bf16 mode keeps vectors in fp32 and only G, h1 in bf16
     rc = ax::dispatch_kstep_f32u_bf16(P->lx, w, u, P->dx32, P->dxt32, b(P->h1lp), b(P->glp[0]),
@@ -593,6 +606,13 @@ int ensure_lowp(ax_poisson *P, int mode, cudaStream_t st) {
   }
   if (ax::launch_status()) return AX_ELAUNCH;
   P->lowp_mode = mode;
+  // the even-odd fp32 kernel where it applies (library buffers are aligned),
+  // else the k-loop kernel; the fused dot's partial count follows
+  const int ne = ax::eo32_lx(P->lx) ? (mode == 2 ? ax::eo32_blocks_f32u_bf16(P->lx, P->nelv)
+                                                 : ax::eo32_blocks_f32(P->lx, P->nelv))
+                                    : 0;
+  P->lowp_eo32 = ne > 0;
+  P->ndot32 = ne > 0 ? ne : ax::kstep_blocks(P->lx, P->nelv);
   return AX_OK;
 }
 
@@ -654,7 +674,12 @@ int ax_poisson_create(ax_poisson **out, int lx, int nelv, const double *dx, cons
   }
   P->ndot = ax::op_dot_blocks(P->op);
   P->ndot32 = ax::kstep_blocks(lx, nelv);
-  if (alloc(&P->dotp, (size_t)std::max(P->ndot, P->ndot32) + kRedBlocks)) {
+  // room for the partials of every reduced-precision apply (ensure_lowp
+  // picks one)
+  int nd32 = P->ndot32;
+  if (ax::eo32_lx(lx))
+    nd32 = std::max({nd32, ax::eo32_blocks_f32(lx, nelv), ax::eo32_blocks_f32u_bf16(lx, nelv)});
+  if (alloc(&P->dotp, (size_t)std::max(P->ndot, nd32) + kRedBlocks)) {
     ax_poisson_destroy(P);
     return AX_ENOMEM;
   }

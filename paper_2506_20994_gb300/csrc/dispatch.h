@@ -40,6 +40,32 @@ int dispatch_kstep_f32u_bf16(int lx, float *w, const float *u, const float *dx, 
                              const __nv_bfloat16 *g12, const __nv_bfloat16 *g13,
                              const __nv_bfloat16 *g23, int nelv, int epb, cudaStream_t st,
                              double *dotp = nullptr);
+// Persistent even-odd operator with fp32 arithmetic (ax_eo32.cuh) for
+// lx in {6, 8, 10, 12} (AX_EINVAL otherwise): u stored as fp32 or bf16,
+// g = {h1, g11, g22, g33, g12, g13, g23} as fp32 or bf16, fp32 D and w.
+// Every array must be 16-byte aligned (eo32_ok).  dotp: one partial of
+// u . w per CTA, eo32_blocks_*(lx, nelv) of them.  err: device word set to
+// 1 if a staged copy never arrived (may be null; the affected elements are
+// then written as NaN).
+int dispatch_eo32_f32(int lx, float *w, const float *u, const float *dx, const float *dxt,
+                      const float *const g[7], int nelv, int *err, double *dotp,
+                      cudaStream_t st);
+int dispatch_eo32_bf16(int lx, float *w, const __nv_bfloat16 *u, const float *dx,
+                       const float *dxt, const __nv_bfloat16 *const g[7], int nelv, int *err,
+                       double *dotp, cudaStream_t st);
+int dispatch_eo32_f32u_bf16(int lx, float *w, const float *u, const float *dx,
+                            const float *dxt, const __nv_bfloat16 *const g[7], int nelv,
+                            int *err, double *dotp, cudaStream_t st);
+int eo32_blocks_f32(int lx, int nelv);
+int eo32_blocks_bf16(int lx, int nelv);
+int eo32_blocks_f32u_bf16(int lx, int nelv);
+// lx 4 stays on the k-loop kernel (measured faster there: 142 against 162 us
+// for fp32 at 2^26 points)
+inline bool eo32_lx(int lx) { return lx >= 6 && lx <= 12 && lx % 2 == 0; }
+template <class... P>
+inline bool eo32_ok(int lx, const P *...p) {
+  return eo32_lx(lx) && ((((uintptr_t)p) % 16 == 0) && ...);
+}
 // Blocks (and dot partials) of a k-loop launch with the default elements per
 // block.
 inline int kstep_blocks(int lx, int nelv) {

@@ -117,7 +117,7 @@ def test_f64_deterministic():
     np.testing.assert_array_equal(a, b)
 
 
-@pytest.mark.parametrize("lx", [2, 5, 6, 8, 10, 12, 16])
+@pytest.mark.parametrize("lx", [2, 4, 5, 6, 8, 10, 12, 16])
 def test_f32_parity(lx):
     case = operator_case((4, 3, 2) if lx <= 12 else (2, 1, 1), lx, seed=200 + lx)
     f = torch.float32
@@ -128,7 +128,7 @@ def test_f32_parity(lx):
     assert rel_l2(w.cpu().numpy(), case["w"]) <= TOL["f32"]
 
 
-@pytest.mark.parametrize("lx", [2, 5, 8, 10, 12])
+@pytest.mark.parametrize("lx", [2, 4, 5, 6, 8, 10, 12])
 def test_bf16_parity(lx):
     case = operator_case((4, 3, 2), lx, seed=300 + lx)
     b = torch.bfloat16
@@ -139,6 +139,82 @@ def test_bf16_parity(lx):
     ax.ax_helm_bf16(w, u, dx, dxt, *fields, lx)
     torch.cuda.synchronize()
     assert rel_l2(w.cpu().numpy(), case["w"]) <= TOL["bf16"]
+
+
+def _run_lowp(case, mode, off=0, dxm=None):
+    """ax_helm_f32 / ax_helm_bf16 on the case; off > 0 shifts every array by
+    `off` values inside a larger buffer (breaks 16-byte alignment)."""
+    lx = case["lx"]
+    st = torch.float32 if mode == "f32" else torch.bfloat16
+
+    def put(a, dt):
+        flat = np.ascontiguousarray(a).reshape(-1)
+        buf = torch.zeros(flat.size + off, dtype=dt, device="cuda")
+        buf[off:] = torch.as_tensor(flat).to(dtype=dt, device="cuda")
+        return buf[off:].view(np.shape(a))
+
+    u = put(case["u"], st)
+    fields = [put(case[k], st) for k in ("h1",) + GKEYS]
+    dx = put(case["dx"] if dxm is None else dxm[0], torch.float32)
+    dxt = put(case["dxt"] if dxm is None else dxm[1], torch.float32)
+    w = put(np.full(np.shape(case["u"]), np.nan), torch.float32)
+    fn = ax.ax_helm_f32 if mode == "f32" else ax.ax_helm_bf16
+    fn(w, u, dx, dxt, *fields, lx)
+    torch.cuda.synchronize()
+    return w.cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", ["f32", "bf16"])
+@pytest.mark.parametrize("lx", [4, 8, 10, 12])
+def test_lowp_general_matrices(mode, lx):
+    """Random dx and an unrelated random dxt (not centro-antisymmetric): the
+    even-odd fp32 kernel must take its general rows."""
+    case = operator_case((3, 2, 2), lx, seed=400 + lx)
+    g = synth.rng(401 + lx)
+    dx = g.uniform(-1.0, 1.0, (lx, lx))
+    dxt = g.uniform(-1.0, 1.0, (lx, lx))
+    G = [case[k] for k in GKEYS]
+    ref = oracle.ax_helm(case["u"], dx.reshape(-1), dxt.reshape(-1), case["h1"], *G, lx)
+    w = _run_lowp(case, mode, dxm=(dx, dxt))
+    assert rel_l2(w, ref) <= TOL[mode]
+
+
+@pytest.mark.parametrize("mode", ["f32", "bf16"])
+@pytest.mark.parametrize("lx", [6, 8])
+def test_lowp_unaligned_arrays(mode, lx):
+    """Arrays that start 4 (fp32) or 2 (bf16) bytes past a 16-byte boundary
+    cannot be bulk-copied; the entry point must still return the operator."""
+    case = operator_case((3, 3, 2), lx, seed=420 + lx)
+    w0 = _run_lowp(case, mode)
+    w1 = _run_lowp(case, mode, off=1)
+    assert rel_l2(w0, case["w"]) <= TOL[mode]
+    assert rel_l2(w1, case["w"]) <= TOL[mode]
+
+
+@pytest.mark.parametrize("mode", ["f32", "bf16"])
+def test_lowp_full_size_sampled(mode):
+    """E = 32768 (32^3), lx = 8 in the benchmark's launch configuration;
+    the oracle evaluates 64 sampled elements, the first and last included."""
+    lx, n = 8, 32
+    v = synth.box_vertices(n, seed=0)
+    g = ax.box_geometry(v, lx)
+    shape = g["g11"].shape
+    u = synth.uniform(shape, seed=1)
+    h1 = synth.uniform(shape, seed=2, lo=0.5, hi=2.0)
+    dx, dxt = ax.dmat(lx)
+    st = torch.float32 if mode == "f32" else torch.bfloat16
+    t = lambda a: torch.as_tensor(a).to(device="cuda", dtype=st)
+    w = torch.full(shape, float("nan"), dtype=torch.float32, device="cuda")
+    fn = ax.ax_helm_f32 if mode == "f32" else ax.ax_helm_bf16
+    fn(w, t(u), _dev(dx, torch.float32), _dev(dxt, torch.float32), t(h1),
+       *[t(g[k]) for k in GKEYS], lx)
+    torch.cuda.synchronize()
+    w = w.cpu().numpy()
+    pick = np.unique(np.concatenate([[0, shape[0] - 1], synth.rng(19).integers(0, shape[0], 62)]))
+    go = oracle.box_geometry(v, lx, elements=pick)
+    dxo, dxto = oracle.d_buffers(lx)
+    ref = oracle.ax_helm(u[pick], dxo, dxto, h1[pick], *[go[k] for k in GKEYS], lx)
+    assert rel_l2(w[pick], ref) <= TOL[mode]
 
 
 def test_full_size_sampled_parity():

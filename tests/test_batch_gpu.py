@@ -3,7 +3,9 @@
 Uneven meshes of mixed lx in one persistent launch (and its CUDA-graph
 replay) must give, for every mesh, exactly the bits of the single-mesh
 entry point with the same thread layout (the operator handle for fp64 lx 6,
-8, 10; ax_helm / ax_helm_f32 otherwise, lx 12 included), and match the oracle within the
+8, 10; ax_helm / ax_helm_f32 otherwise; fp32 lx 12, which the batch runs in
+the k-loop layout and ax_helm_f32 in the even-odd one, within 1e-6 of it),
+and match the oracle within the
 fp64 (1e-12) or fp32 (1e-6) relative L2 tolerance; at the benchmark's size
 (64 meshes, E log-uniform in [64, 8192], lx in {5, 6, 8, 10}) sampled
 elements of every mesh are checked against the oracle.
@@ -83,7 +85,10 @@ def test_batch_matches_oracle_and_single_launch(dtype, graph):
             ax.ax_helm_f32(w1, m["u"], m["dx"], m["dxt"], m["h1"], *[m[k] for k in GKEYS],
                            m["lx"])
         torch.cuda.synchronize()
-        assert torch.equal(w1, m["w"])
+        if dtype == ax.AX_BATCH_F32 and m["lx"] == 12:  # another layout: fp32 rounding
+            assert rel_l2(w1.double().cpu().numpy(), w) <= 1e-6
+        else:
+            assert torch.equal(w1, m["w"])
 
 
 def test_batch_empty_and_bad_meshes():
