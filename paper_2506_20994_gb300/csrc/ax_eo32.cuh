@@ -27,8 +27,9 @@
 //    partner lane.  The two contractions of a direction share their
 //    coefficient loads.
 //  * The (e, o) lines of the three directions go to shared memory as 8-byte
-//    entries; two line sets alternate between elements, so no barrier
-//    separates one element's last contraction from the next one's lines.
+//    entries, those of the gradient and those of the weighted gradient in
+//    two separate sets: two barriers per element (after each publication)
+//    order every reuse of a set or a stage buffer.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -374,7 +375,7 @@ AX_D void e32_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
       const int buf = (int)(n & 1u);
       const uint32_t par = (n >> 1) & 1u;
       // stage buf ^ 1 was last read by the previous element, before its
-      // second barrier
+      // second barrier (which this thread has passed)
       if (tid == 0 && more) {
         eop::fence_async_smem();
         issue(nxp, buf ^ 1);
@@ -384,14 +385,14 @@ AX_D void e32_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
       const unsigned char *st = stg + (size_t)buf * C::SBYTES;
       const SU *U = reinterpret_cast<const SU *>(st);
       const SG *G = reinterpret_cast<const SG *>(st + C::UBYTES);
-      u64 *L = Lb + (size_t)buf * C::SETE;
+      u64 *LA = Lb, *LB = Lb + C::SETE;  // gradient and weighted-gradient lines
 
       // ---- phase 1: this element's u, lines of the three directions
       const bool got = eop::mbar_wait(bar0 + 8u * (uint32_t)buf, par, eop::kWaitLimit);
       float v[2][2];
 #pragma unroll
       for (int b = 0; b < 2; ++b) row_pair(U, b, v[b][0], v[b][1]);
-      publish(L, v, v, v);
+      publish(LA, v, v, v);
       if (!sync_and(got)) {
         // a staged copy never completed: record it, write NaN into this
         // group's remaining elements (so that the failure cannot pass
@@ -417,7 +418,7 @@ AX_D void e32_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
 
       // ---- phase 2: reference gradient
       float gr[2][2], gs[2][2], gt[2][2];
-      contract_all(L, 0, gen, gr, gs, gt);
+      contract_all(LA, 0, gen, gr, gs, gt);
 
       // ---- phase 3: pointwise h1 G
 #pragma unroll
@@ -441,14 +442,15 @@ AX_D void e32_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
               h[a], __fmaf_rn(g33[a], ut, __fmaf_rn(g23[a], us, __fmul_rn(g13[a], ur))));
         }
       }
-      sync();  // the gradient lines and the stage are read
 
-      // ---- phase 4: lines of the weighted gradient
-      publish(L, gr, gs, gt);
+      // ---- phase 4: lines of the weighted gradient (set B: its last
+      // readers, the previous element's phase 5, are behind this element's
+      // first barrier)
+      publish(LB, gr, gs, gt);
       sync();
 
       // ---- phase 5: transposed contractions, summed, stored
-      contract_all(L, 1, gen, gr, gs, gt);
+      contract_all(LB, 1, gen, gr, gs, gt);
       if (real) {
         float el = 0.f;
 #pragma unroll
