@@ -21,8 +21,7 @@
 //  * The (lx/2)^3 mirror octants get two threads each, thread 2t + c owning
 //    the points {i', N-i'} x {j} x {k', N-k'}, j = j' (c = 0) or N - j'
 //    (c = 1): a warp's reads of a staged field then cover the eight rows of
-//    one k-plane (no two threads in one bank), and at lx = 8 a bf16 row is
-//    one 16-byte load that serves both of a thread's points.  Pairs along i
+//    one k-plane.  Pairs along i
 //    and k stay inside a thread; pairs along j take one shuffle with the
 //    partner lane.  The two contractions of a direction share their
 //    coefficient loads.
@@ -290,19 +289,26 @@ AX_D void e32_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
     }
   };
   // this thread's two values (a = 0, 1) of row (k_b, j_c) of one staged
-  // field; bf16 rows at lx = 8 are one 16-byte load
+  // field.  bf16 at lx = 8: the two 32-bit words holding i' and N - i', each
+  // value moved into the high half of an fp32 word by one byte permute.
+  // Otherwise the thread with c = 1 reads N - i' first: rows j and j + 4 of
+  // a plane share banks at lx = 8, and this way the two halves of the warp
+  // read different column halves in each load.
+  const unsigned wsel0 = (ip & 1) ? 0x3244u : 0x1044u;  // value -> high half, zeros below
+  const unsigned wsel1 = (ip & 1) ? 0x1044u : 0x3244u;  // (N - i' has the other parity)
   auto row_pair = [&](const auto *F, int b, float &x0, float &x1) __attribute__((always_inline)) {
     using S = std::remove_cv_t<std::remove_pointer_t<decltype(F)>>;
     const int r = real ? (kb(b) * LX + jc) * LX : 0;
     if constexpr (std::is_same_v<S, __nv_bfloat16> && LX == 8) {
-      const uint4 q = *reinterpret_cast<const uint4 *>(F + r);
-      // i' in words 0-1, N - i' in words 2-3; bf16 -> fp32 bits: value << 16
-      const unsigned w0 = (ip & 2) ? q.y : q.x, w1 = (ip & 2) ? q.z : q.w;
-      x0 = __uint_as_float((ip & 1) ? (w0 & 0xffff0000u) : (w0 << 16));
-      x1 = __uint_as_float((ip & 1) ? (w1 << 16) : (w1 & 0xffff0000u));
+      const unsigned *wr = reinterpret_cast<const unsigned *>(F + r);
+      const unsigned w0 = wr[ip >> 1], w1 = wr[3 - (ip >> 1)];
+      x0 = __uint_as_float(__byte_perm(w0, 0u, wsel0));
+      x1 = __uint_as_float(__byte_perm(w1, 0u, wsel1));
     } else {
-      x0 = ldf(F + r + (real ? ip : 0));
-      x1 = ldf(F + r + (real ? N - ip : 0));
+      const int i0 = real ? (c ? N - ip : ip) : 0, i1 = real ? (c ? ip : N - ip) : 0;
+      const float f0 = ldf(F + r + i0), f1 = ldf(F + r + i1);
+      x0 = c ? f1 : f0;
+      x1 = c ? f0 : f1;
     }
   };
   // the even-odd coefficients of one mesh's matrices; returns true when a
