@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--n", type=int, default=32, help="elements per box edge")
     p.add_argument("--lx", type=int, default=8)
     p.add_argument("--no-extras", action="store_true")
-    p.add_argument("--extras", default="modes,sweep,cg,cg_sweep,learned,batch,rates",
+    p.add_argument("--extras", default="modes,sweep,cg,cg_sweep,learned,batch,rates,tri_df",
                    help="comma list of extra sections to run")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()

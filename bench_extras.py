@@ -22,6 +22,10 @@ CUDA events (kernels) or wall time around a synchronising solve (solvers):
   batch    64 meshes, E log-uniform in [64, 8192], lx in {5, 6, 8, 10}: one
            persistent launch (and its CUDA-graph replay) against one launch
            per mesh, fp64 and fp32
+  tri_df   prototype of the fp64-accurate on-the-fly trilinear geometry:
+           the time to form G per point from the corners in double-float,
+           alone (bench_probe.cu), against the HBM time of the 56 bytes of
+           stored geometry it would replace
 """
 from __future__ import annotations
 
@@ -353,14 +357,12 @@ def batch(ax, synth, dev, hbm_peak):
     return out
 
 
-def probe_rates() -> dict:
-    """Multiply-add throughput per SM and clock of the current device (fp64,
-    fp32, packed f32x2): bench_probe.cu, built here with nvcc into _build/
-    and loaded on its own (it is not part of the library)."""
+def _probe_lib():
+    """bench_probe.cu, built here with nvcc into _build/ and loaded on its own
+    (it is not part of the library)."""
     import ctypes
     import shutil
     import subprocess
-    import torch
     src = os.path.join(ROOT, "bench_probe.cu")
     out_dir = os.path.join(ROOT, "_build")
     os.makedirs(out_dir, exist_ok=True)
@@ -372,7 +374,49 @@ def probe_rates() -> dict:
                         "-gencode", "arch=compute_103a,code=sm_103a", "-I", ROOT,
                         "-I", os.path.join(ROOT, "include"), src, "-o", tmp], check=True)
         os.replace(tmp, so)
-    lib = ctypes.CDLL(so)
+    return ctypes.CDLL(so)
+
+
+def tri_df_probe(ax, synth, dev, n=32, lx=8):
+    """The fp64-accurate on-the-fly trilinear geometry prototype (bench_probe.cu):
+    time to compute G per point from the corners in double-float at E = n^3,
+    and its element-0 G against ax_box_geometry's fp64 G."""
+    import ctypes
+    import numpy as np
+    import torch
+    lib = _probe_lib()
+    v = synth.box_vertices(n, seed=0)
+    cor = torch.as_tensor(ax.box_corners(v), device=dev).reshape(-1).contiguous()
+    xi, wq = (torch.as_tensor(a, device=dev) for a in ax.gll(lx))
+    g0 = torch.zeros(6 * lx ** 3, dtype=torch.float64, device=dev)
+    ms = ctypes.c_float()
+    rc = lib.bench_probe_tri_df(ctypes.c_void_p(cor.data_ptr()), ctypes.c_void_p(xi.data_ptr()),
+                                ctypes.c_void_p(wq.data_ptr()), ctypes.c_int(n ** 3),
+                                ctypes.c_int(20), ctypes.c_void_p(g0.data_ptr()),
+                                ctypes.byref(ms),
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise RuntimeError(f"bench_probe_tri_df failed: {rc}")
+    geo = ax.box_geometry(v[:2, :2, :2], lx)  # element 0 of the same mesh
+    ref = np.stack([geo[k][0].reshape(-1) for k in ("g11", "g22", "g33", "g12", "g13", "g23")])
+    got = g0.cpu().numpy().reshape(6, -1)
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    npts = n ** 3 * lx ** 3
+    return {"what": "G from the 8 corners per point in double-float (k-loop schedule), alone",
+            "E": n ** 3, "lx": lx, "ms": round(ms.value, 4),
+            "ns_per_point_all_sms": round(ms.value * 1e6 / npts, 4),
+            "rel_err_g_element0_vs_fp64": err,
+            "stored_geometry_bytes_saved_per_point": 56,
+            "hbm_time_of_those_bytes_ms": round(56 * npts / 6785.9e9 * 1e3, 4)}
+
+
+def probe_rates() -> dict:
+    """Multiply-add throughput per SM and clock of the current device (fp64,
+    fp32, packed f32x2): bench_probe.cu, built here with nvcc into _build/
+    and loaded on its own (it is not part of the library)."""
+    import ctypes
+    import torch
+    lib = _probe_lib()
     rates = (ctypes.c_double * 3)()
     rc = lib.bench_probe_rates(rates, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     if rc != 0:
@@ -406,6 +450,7 @@ def run_extras(ax, host, d, lx, nel, stream, hbm_peak, which):
         "learned": lambda: learned(ax, synth, synth.poisson_source, dev),
         "batch": lambda: batch(ax, synth, dev, hbm_peak),
         "rates": lambda: rates(ax),
+        "tri_df": lambda: tri_df_probe(ax, synth, dev),
     }
     for name, fn in sections.items():
         if name not in which:

@@ -143,3 +143,186 @@ extern "C" int bench_probe_rates(double *rates, void *stream) {
   cudaFree(d_sink);
   return rc;
 }
+
+// ---------------------------------------------------------------------------
+// Prototype for the fp64-accurate on-the-fly trilinear geometry (not a
+// library path): the cost of computing G = (w_i w_j w_k / det J) adj(J)
+// adj(J)^T per point from an element's 8 corners in double-float arithmetic,
+// in the k-loop schedule of the fp32 trilinear kernel (the t-column of J
+// fixed along a thread's k-walk, the r- and s-columns linear in k).  Timing
+// this kernel alone gives the work the fp64 operator would add per point in
+// exchange for the 56 bytes of stored geometry it would stop reading.  Each
+// thread folds its G values into a checksum (so nothing is optimised away);
+// the G of element 0 is written out in fp64 for a parity check.
+namespace {
+
+using ax::df::df2;
+
+__device__ __forceinline__ df2 dsplit(double x) {
+  df2 o;
+  o.hi = (float)x;
+  o.lo = (float)(x - (double)o.hi);
+  return o;
+}
+__device__ __forceinline__ df2 dnorm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return df2{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+// TwoProduct of the heads, cross terms in the tail
+__device__ __forceinline__ df2 dmul(df2 a, df2 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return dnorm(p, e);
+}
+// TwoSum of the heads, tails added
+__device__ __forceinline__ df2 dadd(df2 a, df2 b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bp = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(b.hi, bp));
+  return dnorm(s, __fadd_rn(err, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df2 dneg(df2 a) { return df2{-a.hi, -a.lo}; }
+__device__ __forceinline__ df2 dfms(df2 a, df2 b, df2 c, df2 d) {  // a b - c d
+  return dadd(dmul(a, b), dneg(dmul(c, d)));
+}
+// a / b: reciprocal of the head, one correction step on the pair residual
+__device__ __forceinline__ df2 ddiv(df2 a, df2 b) {
+  const float r = __frcp_rn(b.hi);
+  const float q1 = __fmul_rn(a.hi, r);
+  const df2 res = dadd(a, dneg(dmul(b, df2{q1, 0.f})));
+  const float q2 = __fmul_rn(res.hi, r);
+  return dnorm(q1, q2);
+}
+
+template <int LX>
+__global__ void __launch_bounds__(LX * LX) probe_tri_df_kernel(const double *__restrict__ corners,
+                                                               const double *__restrict__ xi,
+                                                               const double *__restrict__ wq,
+                                                               int nelv, double *__restrict__ sink,
+                                                               double *__restrict__ g0) {
+  constexpr int N2 = LX * LX;
+  __shared__ df2 cf[36], phi0[LX], phi1[LX], sw[LX];
+  const int p = (int)threadIdx.x, i = p % LX, j = p / LX;
+  if (p < LX) {
+    phi0[p] = dsplit(0.5 * (1.0 - xi[p]));
+    phi1[p] = dsplit(0.5 * (1.0 + xi[p]));
+    sw[p] = dsplit(wq[p]);
+  }
+  float check = 0.f;
+  for (long long e = blockIdx.x; e < nelv; e += gridDim.x) {
+    __syncthreads();
+    for (int t = p; t < 36; t += N2) {  // half edge vectors, as the fp32 kernel's
+      const int dir = t / 12, d = (t / 4) % 3, q = t % 4, hi = q >> 1, lo = q & 1;
+      int c0, c1;
+      if (dir == 0) {
+        c0 = (hi * 2 + lo) * 2;
+        c1 = c0 + 1;
+      } else if (dir == 1) {
+        c0 = (hi * 2) * 2 + lo;
+        c1 = c0 + 2;
+      } else {
+        c0 = hi * 2 + lo;
+        c1 = c0 + 4;
+      }
+      const double *x = corners + (size_t)e * 24;
+      cf[t] = dsplit(0.5 * (x[c1 * 3 + d] - x[c0 * 3 + d]));
+    }
+    __syncthreads();
+    const df2 pj0 = phi0[j], pj1 = phi1[j], pi0 = phi0[i], pi1 = phi1[i];
+    df2 P[3][2], Q[3][2], Jt[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        P[d][c] = dadd(dmul(cf[d * 4 + c * 2 + 1], pj1), dmul(cf[d * 4 + c * 2], pj0));
+        Q[d][c] = dadd(dmul(cf[12 + d * 4 + c * 2 + 1], pi1), dmul(cf[12 + d * 4 + c * 2], pi0));
+      }
+      const df2 b0 = dadd(dmul(cf[24 + d * 4 + 1], pi1), dmul(cf[24 + d * 4], pi0));
+      const df2 b1 = dadd(dmul(cf[24 + d * 4 + 3], pi1), dmul(cf[24 + d * 4 + 2], pi0));
+      Jt[d] = dadd(dmul(b1, pj1), dmul(b0, pj0));
+    }
+    const df2 wij = dmul(sw[i], sw[j]);
+#pragma unroll 2
+    for (int k = 0; k < LX; ++k) {
+      const df2 z0 = phi0[k], z1 = phi1[k];
+      const df2 a = dadd(dmul(P[0][1], z1), dmul(P[0][0], z0));
+      const df2 b = dadd(dmul(Q[0][1], z1), dmul(Q[0][0], z0));
+      const df2 c = Jt[0];
+      const df2 d = dadd(dmul(P[1][1], z1), dmul(P[1][0], z0));
+      const df2 f = dadd(dmul(Q[1][1], z1), dmul(Q[1][0], z0));
+      const df2 g = Jt[1];
+      const df2 h = dadd(dmul(P[2][1], z1), dmul(P[2][0], z0));
+      const df2 m = dadd(dmul(Q[2][1], z1), dmul(Q[2][0], z0));
+      const df2 n = Jt[2];
+      const df2 A00 = dfms(f, n, g, m), A01 = dfms(c, m, b, n), A02 = dfms(b, g, c, f);
+      const df2 A10 = dfms(g, h, d, n), A11 = dfms(a, n, c, h), A12 = dfms(c, d, a, g);
+      const df2 A20 = dfms(d, m, f, h), A21 = dfms(b, h, a, m), A22 = dfms(a, f, b, d);
+      const df2 det = dadd(dmul(a, A00), dadd(dmul(b, A10), dmul(c, A20)));
+      const df2 s = ddiv(dmul(wij, sw[k]), det);
+      auto dot3 = [](df2 x0, df2 x1, df2 x2, df2 y0, df2 y1, df2 y2) {
+        return dadd(dmul(x0, y0), dadd(dmul(x1, y1), dmul(x2, y2)));
+      };
+      const df2 G[6] = {dmul(s, dot3(A00, A01, A02, A00, A01, A02)),
+                        dmul(s, dot3(A10, A11, A12, A10, A11, A12)),
+                        dmul(s, dot3(A20, A21, A22, A20, A21, A22)),
+                        dmul(s, dot3(A00, A01, A02, A10, A11, A12)),
+                        dmul(s, dot3(A00, A01, A02, A20, A21, A22)),
+                        dmul(s, dot3(A10, A11, A12, A20, A21, A22))};
+#pragma unroll
+      for (int q = 0; q < 6; ++q) check += G[q].hi;
+      if (e == 0 && g0) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+          g0[(size_t)q * LX * N2 + (size_t)k * N2 + p] = (double)G[q].hi + (double)G[q].lo;
+      }
+    }
+  }
+  sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = (double)check;
+}
+
+}  // namespace
+
+// Times the prototype at lx = 8 over nelv elements (corners: nelv x 24
+// fp64, device; xi, wq: the 8 GLL nodes and weights, device): *ms = average
+// kernel time over `reps` launches after one warm-up; g0 (device, 6 x 512
+// fp64, may be null) receives element 0's G (g11, g22, g33, g12, g13, g23).
+// Allocates a small sink buffer; synchronises `stream`.
+extern "C" int bench_probe_tri_df(const double *corners, const double *xi, const double *wq,
+                                  int nelv, int reps, double *g0, float *ms, void *stream) {
+  if (!corners || !xi || !wq || !ms || nelv <= 0 || reps < 1) return AX_EINVAL;
+  int dev = 0, sms = 0, bps = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, probe_tri_df_kernel<8>, 64, 0) !=
+          cudaSuccess ||
+      bps < 1) {
+    (void)cudaGetLastError();
+    return AX_ELAUNCH;
+  }
+  const int grid = std::min<long long>((long long)sms * bps, nelv);
+  double *sink = nullptr;
+  if (cudaMalloc((void **)&sink, sizeof(double) * grid * 64) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return AX_ENOMEM;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  probe_tri_df_kernel<8><<<grid, 64, 0, st>>>(corners, xi, wq, nelv, sink, g0);
+  cudaEventRecord(e0, st);
+  for (int r = 0; r < reps; ++r)
+    probe_tri_df_kernel<8><<<grid, 64, 0, st>>>(corners, xi, wq, nelv, sink, nullptr);
+  cudaEventRecord(e1, st);
+  int rc = cudaEventSynchronize(e1) == cudaSuccess ? AX_OK : AX_ELAUNCH;
+  float t = 0.f;
+  if (rc == AX_OK) cudaEventElapsedTime(&t, e0, e1);
+  *ms = t / reps;
+  if (ax::launch_status() != AX_OK) rc = AX_ELAUNCH;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  return rc;
+}
