@@ -6,7 +6,8 @@ CUDA events (kernels) or wall time around a synchronising solve (solvers):
   modes    fp64-unit, fp32 and bf16 operator kernels on the main mesh, and
            the fp32 kernel with G formed from the corner vertices
   sweep    fp64 operator (handle, prepared geometry) and ax_helm on fp64
-           geometry at E in {4096, 32768} x lx in {6, 8, 10, 12}
+           geometry at E in {4096, 32768} x lx in {6, 8, 10, 12}; the handle
+           at E = 32768 for lx in {3, 4, 5, 7}; lx 14 and 16 at E = 4096
   cg       Poisson solve to a 1e-8 relative residual at E = 32768, lx = 8:
            fp64 Jacobi-CG against fp64 iterative refinement around fp32 and
            bf16-data inner CG
@@ -206,6 +207,21 @@ def sweep(ax, synth, dev, hbm_peak):
                                          nel * (lx - 1) ** 3 / (ms * 1e-3) / 1e9, 2),
                                      "raw_geometry_ms": round(ms_raw, 4)}
             del d, w, op
+    # the paper's lower orders (lx 3-7): the operator handle at E = 32768; it
+    # prepares geometry for even lx >= 6 and applies ax_helm's choice otherwise
+    for lx in (3, 4, 5, 7):
+        d, nel = _mesh_tensors(ax, synth, 32, lx, dev)
+        w = torch.empty_like(d["u"])
+        G = [d[k] for k in GKEYS]
+        op = ax.Operator(lx, d["dx"], d["dxt"], d["h1"], *G)
+        ms = _events_ms(lambda: op.apply(w, d["u"]), 10)
+        npts = nel * lx ** 3
+        out[f"E{nel}_lx{lx}"] = {"gdofs": round(npts / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 4),
+                                 "hbm_frac": round(72.0 * npts / (ms * 1e-3) / 1e9 / hbm_peak, 4),
+                                 "gdofs_paper_convention": round(
+                                     nel * (lx - 1) ** 3 / (ms * 1e-3) / 1e9, 2),
+                                 "prepared": bool(op.info()["prepared"])}
+        del d, w, op
     # high order: the double-float k-loop kernel (ax_helm's choice) against the
     # fp64 units, E = 4096
     for lx in (14, 16):

@@ -36,6 +36,7 @@
 #include <type_traits>
 
 #include "ax_eo_persist.cuh"
+#include "dispatch.h"
 
 namespace ax {
 namespace e32 {
@@ -52,7 +53,9 @@ AX_D float hi_(u64 v) { return df::ly_(v); }
 
 constexpr size_t a128(size_t x) { return (x + 127) / 128 * 128; }
 
-template <int LX, class SU, class SG>
+// PUPD: the stage holds r, minv and the old direction instead of u (the
+// solver's fused direction update).
+template <int LX, class SU, class SG, bool PUPD = false>
 struct Cfg {
   static constexpr int H = LX / 2, N = LX - 1, H2 = H * H, H3 = H2 * H;
   static constexpr int NT = 2 * H3;                // threads per element
@@ -69,7 +72,8 @@ struct Cfg {
   static constexpr size_t LINE_BYTES = 2 * (size_t)SETE * 8;
   static constexpr unsigned UBYTES = N3 * sizeof(SU);
   static constexpr unsigned GFBYTES = N3 * sizeof(SG);  // one geometry field
-  static constexpr unsigned TXBYTES = UBYTES + 7 * GFBYTES;
+  static constexpr int NU = PUPD ? 3 : 1;                // u-sized staged arrays
+  static constexpr unsigned TXBYTES = NU * UBYTES + 7 * GFBYTES;
   static constexpr size_t SBYTES = a128(TXBYTES);        // one stage buffer
   static constexpr size_t OFF_STAGE = OFF_LINES + a128(LINE_BYTES);
   static constexpr size_t OFF_MISC = OFF_STAGE + 2 * SBYTES;
@@ -143,10 +147,12 @@ struct SeqOne {
 // a staged copy never arrived (the body then stops).
 // CREG (lx = 8 only): coefficient rows in registers (same arithmetic, so
 // the same bits, as reading them from shared memory).
-template <int LX, class SU, class SG, bool DOT, bool CREG, class Seq, class Sync, class SyncAnd>
+template <int LX, class SU, class SG, bool DOT, bool PUPD, bool CREG, class Seq, class Sync,
+          class SyncAnd>
 AX_D void e32_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd sync_and,
-                  int *err, double &dsum) {
-  using C = Cfg<LX, SU, SG>;
+                  int *err, double &dsum, const E32Upd &up = E32Upd{}) {
+  static_assert(!PUPD || std::is_same_v<SU, float>, "the fused update keeps fp32 vectors");
+  using C = Cfg<LX, SU, SG, PUPD>;
   constexpr int H = C::H, N = C::N, H2 = C::H2, NT = C::NT, N3 = C::N3;
   constexpr bool kCoefRegs = CREG && LX == 8;
   u64 *cf = reinterpret_cast<u64 *>(sm);
@@ -357,9 +363,16 @@ AX_D void e32_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
           "l"(src), "r"(bytes), "r"(bar)
           : "memory");
     };
-    copy(dst, M.u + eo, C::UBYTES);
+    if constexpr (PUPD) {
+      copy(dst, up.r + eo, C::UBYTES);
+      copy(dst + C::UBYTES, up.minv + eo, C::UBYTES);
+      copy(dst + 2 * C::UBYTES, up.pw + eo, C::UBYTES);
+    } else {
+      copy(dst, M.u + eo, C::UBYTES);
+    }
 #pragma unroll
-    for (int f = 0; f < 7; ++f) copy(dst + C::UBYTES + f * C::GFBYTES, M.g[f] + eo, C::GFBYTES);
+    for (int f = 0; f < 7; ++f)
+      copy(dst + C::NU * C::UBYTES + f * C::GFBYTES, M.g[f] + eo, C::GFBYTES);
   };
 
   if (tid == 0) {
@@ -371,6 +384,7 @@ AX_D void e32_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
   sync();  // the barriers are initialised before anyone waits on them
   if (tid == 0 && have) issue(pos, 0);
 
+  const float beta = PUPD ? (float)*up.beta : 0.f;  // the solver's scalar, on the device
   unsigned n = 0;  // elements done by this group
   while (have) {
     const int cmesh = seq.mesh_of(pos);
@@ -390,7 +404,7 @@ AX_D void e32_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
       const size_t eb = (size_t)seq.elem(pos) * N3;
       const unsigned char *st = stg + (size_t)buf * C::SBYTES;
       const SU *U = reinterpret_cast<const SU *>(st);
-      const SG *G = reinterpret_cast<const SG *>(st + C::UBYTES);
+      const SG *G = reinterpret_cast<const SG *>(st + C::NU * C::UBYTES);
       u64 *LA = Lb, *LB = Lb + C::SETE;  // gradient and weighted-gradient lines
 
       // ---- phase 1: this element's u, lines of the three directions
@@ -398,6 +412,21 @@ AX_D void e32_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
       float v[2][2];
 #pragma unroll
       for (int b = 0; b < 2; ++b) row_pair(U, b, v[b][0], v[b][1]);
+      if constexpr (PUPD) {  // v = r here: p = minv .* r + beta p, stored
+        const float *Mi = reinterpret_cast<const float *>(st + C::UBYTES);
+        const float *Po = reinterpret_cast<const float *>(st + 2 * C::UBYTES);
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          float mi[2], po[2];
+          row_pair(Mi, b, mi[0], mi[1]);
+          row_pair(Po, b, po[0], po[1]);
+#pragma unroll
+          for (int a = 0; a < 2; ++a) {
+            v[b][a] = __fmaf_rn(mi[a], v[b][a], __fmul_rn(beta, po[a]));
+            if (real) up.pw[eb + pidx(b, a)] = v[b][a];
+          }
+        }
+      }
       publish(LA, v, v, v);
       if (!sync_and(got)) {
         // a staged copy never completed: record it, write NaN into this
@@ -482,17 +511,17 @@ AX_D void e32_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
 
 // One mesh, elements blockIdx.x + k gridDim.x.  DOT: one partial of u . w
 // per CTA (fixed order) in dotp[blockIdx.x].
-template <int LX, class SU, class SG, bool DOT>
+template <int LX, class SU, class SG, bool DOT, bool PUPD = false>
 __global__ void __launch_bounds__(Cfg<LX, SU, SG>::NTB, (minb<LX, SU, SG>()))
 ax_eo32_kernel(const Mesh<SU, SG> mesh, long long nelv, int *__restrict__ err,
-               double *__restrict__ dotp) {
-  using C = Cfg<LX, SU, SG>;
+               double *__restrict__ dotp, const E32Upd up) {
+  using C = Cfg<LX, SU, SG, PUPD>;
   extern __shared__ __align__(128) unsigned char sm[];
   const SeqOne<SU, SG> seq{mesh, nelv};
   double dsum = 0.0;
-  e32_run<LX, SU, SG, DOT, kE32CoefRegs>(
+  e32_run<LX, SU, SG, DOT, PUPD, kE32CoefRegs>(
       sm, (int)threadIdx.x, seq, [] { __syncthreads(); },
-      [](bool p) { return __syncthreads_and(p) != 0; }, err, dsum);
+      [](bool p) { return __syncthreads_and(p) != 0; }, err, dsum, up);
   if constexpr (DOT) {  // one partial per CTA: fixed shuffle tree, warps in order
     double *red = reinterpret_cast<double *>(sm + C::OFF_MISC + 16);
 #pragma unroll
@@ -520,9 +549,9 @@ namespace e32 {
 
 // Resident CTAs of one kernel variant on the current device times its SMs
 // (cached per device; the shared-memory limit is raised on first use).
-template <int LX, class SU, class SG, bool DOT>
+template <int LX, class SU, class SG, bool DOT, bool PUPD>
 int grid() {
-  using C = Cfg<LX, SU, SG>;
+  using C = Cfg<LX, SU, SG, PUPD>;
   static std::atomic<int> cache[kMaxDevices];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -531,7 +560,7 @@ int grid() {
   }
   int g = cache[dev].load(std::memory_order_acquire);
   if (g > 0) return g;
-  auto kern = ax_eo32_kernel<LX, SU, SG, DOT>;
+  auto kern = ax_eo32_kernel<LX, SU, SG, DOT, PUPD>;
   int sms = 0, bps = 0;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) !=
           cudaSuccess ||
@@ -546,18 +575,19 @@ int grid() {
   return g;
 }
 
-// CTAs (and dot partials) of a launch over nelv elements: the DOT and plain
-// variants launch the same grid.
+// CTAs (and dot partials) of a launch over nelv elements: every variant of a
+// storage pair launches the same grid, so that a solver sizes its partials
+// once.
 template <int LX, class SU, class SG>
 int blocks(long long nelv) {
-  const int g = std::min(grid<LX, SU, SG, true>(), grid<LX, SU, SG, false>());
+  int g = std::min(grid<LX, SU, SG, true, false>(), grid<LX, SU, SG, false, false>());
+  if constexpr (std::is_same_v<SU, float>) g = std::min(g, grid<LX, SU, SG, true, true>());
   return g <= 0 ? 0 : (int)std::min<long long>(g, std::max(nelv, 1LL));
 }
 
 template <int LX, class SU, class SG>
 int launch(float *w, const SU *u, const float *dx, const float *dxt, const SG *const g[7],
-           int nelv, int *err, double *dotp, cudaStream_t st) {
-  using C = Cfg<LX, SU, SG>;
+           int nelv, int *err, double *dotp, cudaStream_t st, const E32Upd *up) {
   const int nb = blocks<LX, SU, SG>(nelv);
   if (nb <= 0) return AX_ELAUNCH;
   Mesh<SU, SG> m;
@@ -566,10 +596,23 @@ int launch(float *w, const SU *u, const float *dx, const float *dxt, const SG *c
   for (int f = 0; f < 7; ++f) m.g[f] = g[f];
   m.dx = dx;
   m.dxt = dxt;
-  if (dotp)
-    ax_eo32_kernel<LX, SU, SG, true><<<nb, C::NTB, C::SMEM, st>>>(m, nelv, err, dotp);
-  else
-    ax_eo32_kernel<LX, SU, SG, false><<<nb, C::NTB, C::SMEM, st>>>(m, nelv, err, dotp);
+  const E32Upd none{};
+  if (up) {
+    if constexpr (std::is_same_v<SU, float>) {
+      if (!dotp || !up->pw || !up->r || !up->minv || !up->beta) return AX_EINVAL;
+      using C = Cfg<LX, SU, SG, true>;
+      ax_eo32_kernel<LX, SU, SG, true, true><<<nb, C::NTB, C::SMEM, st>>>(m, nelv, err, dotp,
+                                                                          *up);
+    } else {
+      return AX_EINVAL;
+    }
+  } else if (dotp) {
+    using C = Cfg<LX, SU, SG>;
+    ax_eo32_kernel<LX, SU, SG, true><<<nb, C::NTB, C::SMEM, st>>>(m, nelv, err, dotp, none);
+  } else {
+    using C = Cfg<LX, SU, SG>;
+    ax_eo32_kernel<LX, SU, SG, false><<<nb, C::NTB, C::SMEM, st>>>(m, nelv, err, dotp, none);
+  }
   return launch_status();
 }
 

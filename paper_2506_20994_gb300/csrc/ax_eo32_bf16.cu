@@ -7,11 +7,11 @@ namespace ax {
 
 int dispatch_eo32_bf16(int lx, float *w, const __nv_bfloat16 *u, const float *dx, const float *dxt,
                      const __nv_bfloat16 *const g[7], int nelv, int *err, double *dotp,
-                     cudaStream_t st) {
+                     cudaStream_t st, const E32Upd *up) {
   switch (lx) {
 #define AX_CASE(L) \
   case L:          \
-    return e32::launch<L, __nv_bfloat16, __nv_bfloat16>(w, u, dx, dxt, g, nelv, err, dotp, st);
+    return e32::launch<L, __nv_bfloat16, __nv_bfloat16>(w, u, dx, dxt, g, nelv, err, dotp, st, up);
     AX_CASE(6) AX_CASE(8) AX_CASE(10) AX_CASE(12)
 #undef AX_CASE
     default:

@@ -7,11 +7,11 @@ namespace ax {
 
 int dispatch_eo32_f32(int lx, float *w, const float *u, const float *dx, const float *dxt,
                      const float *const g[7], int nelv, int *err, double *dotp,
-                     cudaStream_t st) {
+                     cudaStream_t st, const E32Upd *up) {
   switch (lx) {
 #define AX_CASE(L) \
   case L:          \
-    return e32::launch<L, float, float>(w, u, dx, dxt, g, nelv, err, dotp, st);
+    return e32::launch<L, float, float>(w, u, dx, dxt, g, nelv, err, dotp, st, up);
     AX_CASE(6) AX_CASE(8) AX_CASE(10) AX_CASE(12)
 #undef AX_CASE
     default:

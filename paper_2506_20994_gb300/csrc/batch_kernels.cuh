@@ -162,7 +162,7 @@ __device__ __noinline__ void batch_run_e32(const BatchGroup &G, const BatchItem 
     return r != 0u;
   };
   double dsum = 0.0;
-  e32::e32_run<LX, float, float, false, false>(sm + (size_t)slot * batch_e32_slot_bytes<LX>(),
+  e32::e32_run<LX, float, float, false, false, false>(sm + (size_t)slot * batch_e32_slot_bytes<LX>(),
                                                tid, seq, sync, sync_and, err, dsum);
 }
 

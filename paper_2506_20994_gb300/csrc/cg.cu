@@ -412,20 +412,23 @@ int apply_f64(ax_poisson *P, double *w, const double *u, cudaStream_t st) {
 }
 
 // dotp: also the per-block partials of u . Ax (P->ndot32 of them)
+// up: the fused direction update (even-odd fp32 kernel only; u = up->pw)
 int apply_lowp(ax_poisson *P, float *w, const float *u, cudaStream_t st,
-               double *dotp = nullptr) {
+               double *dotp = nullptr, const ax::E32Upd *up = nullptr) {
   int rc;
+  if (up && !P->lowp_eo32) return AX_EINVAL;
   if (P->lowp_eo32 && P->lowp_mode == 2) {
     auto b = [](const void *x) { return reinterpret_cast<const __nv_bfloat16 *>(x); };
     const __nv_bfloat16 *g[7] = {b(P->h1lp), b(P->glp[0]), b(P->glp[1]), b(P->glp[2]),
                                  b(P->glp[3]), b(P->glp[4]), b(P->glp[5])};
     rc = ax::dispatch_eo32_f32u_bf16(P->lx, w, u, P->dx32, P->dxt32, g, P->nelv, nullptr, dotp,
-                                     st);
+                                     st, up);
   } else if (P->lowp_eo32) {
     auto f = [](const void *x) { return reinterpret_cast<const float *>(x); };
     const float *g[7] = {f(P->h1lp), f(P->glp[0]), f(P->glp[1]), f(P->glp[2]),
                          f(P->glp[3]), f(P->glp[4]), f(P->glp[5])};
-    rc = ax::dispatch_eo32_f32(P->lx, w, u, P->dx32, P->dxt32, g, P->nelv, nullptr, dotp, st);
+    rc = ax::dispatch_eo32_f32(P->lx, w, u, P->dx32, P->dxt32, g, P->nelv, nullptr, dotp, st,
+                               up);
   } else if (P->lowp_mode == 2) {
     auto b = [](const void *x) { return reinterpret_cast<const __nv_bfloat16 *>(x); };
     // u is fp32: the bf16 mode keeps vectors in fp32 and only G, h1 in bf16
@@ -468,7 +471,7 @@ int apply_fused(ax_poisson *P, float *w, const float *u, cudaStream_t st) {
 // The direction update p = minv r + beta p folded into the apply that reads
 // p next (fp64 with prepared geometry); false where no such kernel exists.
 bool fuses_update(const ax_poisson *P, const double *) { return P->dotp && P->ndot > 0; }
-bool fuses_update(const ax_poisson *, const float *) { return false; }
+bool fuses_update(const ax_poisson *P, const float *) { return P->dotp && P->lowp_eo32; }
 int apply_fused_update(ax_poisson *P, double *w, double *p, const double *r,
                        const double *minv, const double *beta, cudaStream_t st,
                        const double *corr = nullptr, const int *use_corr = nullptr) {
@@ -476,10 +479,18 @@ int apply_fused_update(ax_poisson *P, double *w, double *p, const double *r,
   if (rc == AX_OK) rc = mass_fused(P, w, p, st);
   return rc ? rc : ax_gs_sum(P->gs, w, st);
 }
-int apply_fused_update(ax_poisson *, float *, float *, const float *, const float *,
-                       const double *, cudaStream_t, const float * = nullptr,
+// fp32 vectors (the refinement's inner CG, even-odd fp32 kernel): the same
+// fusion, p = minv .* r + beta p in fp32 inside the apply
+int apply_fused_update(ax_poisson *P, float *w, float *p, const float *r, const float *minv,
+                       const double *beta, cudaStream_t st, const float *corr = nullptr,
                        const int * = nullptr) {
-  return AX_EINVAL;
+  if (corr) return AX_EINVAL;  // the flexible loop keeps its own direction kernel
+  ax::E32Upd up;
+  up.pw = p;
+  up.r = r;
+  up.minv = minv;
+  up.beta = beta;
+  return apply_lowp(P, w, p, st, P->dotp, &up);
 }
 
 // Generic PCG loop on vectors of type T (fp64 with the fp64 operator, or
@@ -1213,8 +1224,9 @@ int fcg_loop(ax_poisson *P, const ax_mlp *M, T *x, const T *b, T *r, T *r_old, T
   const unsigned nb = kRedBlocks;
   const int have = M != nullptr;
   // fp64 with prepared geometry: after the first step the direction update
-  // p = z + beta p runs inside the next apply (see pcg_loop)
-  const bool fused_p = fused_parts(P, (const T *)nullptr) > 0 &&
+  // p = z + beta p (+ the learned correction) runs inside the next apply (see
+  // pcg_loop); the fp32 flexible loop keeps its direction kernel
+  const bool fused_p = std::is_same_v<T, double> && fused_parts(P, (const T *)nullptr) > 0 &&
                        fuses_update(P, (const T *)nullptr);
   auto precondition = [&](int first) -> int {
     if (have) {

@@ -44,18 +44,28 @@ int dispatch_kstep_f32u_bf16(int lx, float *w, const float *u, const float *dx, 
 // lx in {6, 8, 10, 12} (AX_EINVAL otherwise): u stored as fp32 or bf16,
 // g = {h1, g11, g22, g33, g12, g13, g23} as fp32 or bf16, fp32 D and w.
 // Every array must be 16-byte aligned (eo32_ok).  dotp: one partial of
-// u . w per CTA, eo32_blocks_*(lx, nelv) of them.  err: device word set to
+// u . w per CTA, eo32_blocks_*(lx, nelv) of them (the same count with and
+// without the fused update, up, which needs dotp).  err: device word set to
 // 1 if a staged copy never arrived (may be null; the affected elements are
 // then written as NaN).
+// The solver's fused direction update for the fp32-vector forms: the kernel
+// first forms pw = minv .* r + (*beta) pw in place (fp32) and applies the
+// operator to it (u is then ignored).
+struct E32Upd {
+  float *pw = nullptr;
+  const float *r = nullptr, *minv = nullptr;
+  const double *beta = nullptr;
+};
 int dispatch_eo32_f32(int lx, float *w, const float *u, const float *dx, const float *dxt,
                       const float *const g[7], int nelv, int *err, double *dotp,
-                      cudaStream_t st);
+                      cudaStream_t st, const E32Upd *up = nullptr);
 int dispatch_eo32_bf16(int lx, float *w, const __nv_bfloat16 *u, const float *dx,
                        const float *dxt, const __nv_bfloat16 *const g[7], int nelv, int *err,
-                       double *dotp, cudaStream_t st);
+                       double *dotp, cudaStream_t st, const E32Upd *up = nullptr);
 int dispatch_eo32_f32u_bf16(int lx, float *w, const float *u, const float *dx,
                             const float *dxt, const __nv_bfloat16 *const g[7], int nelv,
-                            int *err, double *dotp, cudaStream_t st);
+                            int *err, double *dotp, cudaStream_t st,
+                            const E32Upd *up = nullptr);
 int eo32_blocks_f32(int lx, int nelv);
 int eo32_blocks_bf16(int lx, int nelv);
 int eo32_blocks_f32u_bf16(int lx, int nelv);
