@@ -44,7 +44,7 @@ struct Cfg {
   static constexpr int N3 = LX * LX * LX;
   static constexpr bool SWZ = H == 4;              // swizzled, unpadded lines
   // 16-byte entry slots per line (see lpos)
-  static constexpr int LS = SWZ ? 4 : LX == 6 ? 8 : H + 1;
+  static constexpr int LS = SWZ ? 4 : H + 1;
   static constexpr int DE = LX * LX * LS;          // entries per direction
   static constexpr int GE = 2 * 7 * NT;            // geometry entries per element
   static constexpr unsigned GBYTES = GE * 16u;     // = 56 lx^3
@@ -65,20 +65,22 @@ struct Cfg {
 // swaps neighbours when bit 3 of L is set and the entry is XOR-ed with bits 1
 // and 3 of L: every line read and write of the kernel then touches each
 // 16-byte bank group at most once per wavefront's worth of distinct entries.
-// At lx = 6 (lines padded to 8 slots) and lx = 10 (6 slots) the entries
-// rotate within the line by an offset that depends on the line (lx = 6: L +
-// 6 (L / 6); lx = 10: 5 (L / 10)): a model of the kernel's warp accesses
-// (half-warp phases of 16-byte accesses) gives 182 wavefronts per element
-// pass against 556 with plain padded lines at lx = 6, and 1226 against 1848
-// at lx = 10.
-template <int LX>
+// At lx = 6 and lx = 10 (lines padded to 4 and 6 slots) the entries rotate
+// within the line by an offset that depends on the line (lx = 6: L + L / 6;
+// lx = 10: 5 (L / 10)): a model of the kernel's warp accesses (half-warp
+// phases of 16-byte accesses) gives 198 wavefronts per element pass against
+// 556 unrotated at lx = 6, and 1226 against 1848 at lx = 10.
+// ROT10: the lx = 10 rotation (the single-mesh kernel; in the batched
+// kernel's 128-register slots it measured slower, 1.74 against 1.66 ms on the
+// benchmark batch, and is left out there).
+template <int LX, bool ROT10 = true>
 AX_D int lpos(int L, int ent) {
   if constexpr (Cfg<LX>::SWZ) {
     const int b3 = (L >> 3) & 1;
     return (L ^ b3) * 4 + (ent ^ (((L >> 1) & 1) | (b3 << 1)));
   } else if constexpr (LX == 6) {
-    return L * 8 + ((ent + L + (L / 6) * 6) & 7);
-  } else if constexpr (LX == 10) {
+    return L * 4 + ((ent + L + L / 6) & 3);
+  } else if constexpr (LX == 10 && ROT10) {
     return L * 6 + (ent + (L / 10) * 5) % 6;
   } else {
     return L * Cfg<LX>::LS + ent;
@@ -160,6 +162,7 @@ struct EopPos {
 // parameters), so the compiler reads them from the constant bank; through a
 // pointer every per-element access would be a load.
 struct SeqOne {
+  static constexpr bool kRotate10 = true;  // line layout, see lpos
   EopMesh m;
   long long nelv;
   AX_D bool first(EopPos &p) const {
@@ -217,10 +220,10 @@ AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
   // half-size contractions of line L of `lines`: (y at row, y at N-row)
   auto contract = [&](const dd2 *lines, int L, const dd2 *cof, const u64 *nco, int row,
                       df2 &y_lo, df2 &y_hi) __attribute__((always_inline)) {
-    acc2 a = prod2(cof[row * CS], nco[row * H], lines[lpos<LX>(L, 0)]);
+    acc2 a = prod2(cof[row * CS], nco[row * H], lines[lpos<LX, Seq::kRotate10>(L, 0)]);
 #pragma unroll
     for (int l = 1; l < H; ++l)
-      mac2(a, cof[row * CS + l], nco[row * H + l], lines[lpos<LX>(L, l)]);
+      mac2(a, cof[row * CS + l], nco[row * H + l], lines[lpos<LX, Seq::kRotate10>(L, l)]);
     const float Es = lx_(a.s), Ec = lx_(a.c), Os = ly_(a.s), Oc = ly_(a.c);
     const dd2 r = dsum2(dd2{pk(Os, Os), pk(Oc, Oc)}, dd2{pk_pm(Es), pk_pm(Ec)});
     y_lo = df2{lx_(r.hi), lx_(r.lo)};
@@ -236,11 +239,11 @@ AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
     df2 o0 = xchg(c ? vt[0][0] : vt[1][0]), o1 = xchg(c ? vt[0][1] : vt[1][1]);
     if (real) {
 #pragma unroll
-      for (int b = 0; b < 2; ++b) Ar[lpos<LX>(lineR(b), ip)] = eo_pair(vr[b][0], vr[b][1]);
+      for (int b = 0; b < 2; ++b) Ar[lpos<LX, Seq::kRotate10>(lineR(b), ip)] = eo_pair(vr[b][0], vr[b][1]);
 #pragma unroll
-      for (int a = 0; a < 2; ++a) As[lpos<LX>(lineS(a), jp)] = eo_pair(vs[0][a], vs[1][a]);
-      At[lpos<LX>(lineT(c, 0), kp)] = c ? eo_pair(o0, vt[1][0]) : eo_pair(vt[0][0], o0);
-      At[lpos<LX>(lineT(c, 1), kp)] = c ? eo_pair(o1, vt[1][1]) : eo_pair(vt[0][1], o1);
+      for (int a = 0; a < 2; ++a) As[lpos<LX, Seq::kRotate10>(lineS(a), jp)] = eo_pair(vs[0][a], vs[1][a]);
+      At[lpos<LX, Seq::kRotate10>(lineT(c, 0), kp)] = c ? eo_pair(o0, vt[1][0]) : eo_pair(vt[0][0], o0);
+      At[lpos<LX, Seq::kRotate10>(lineT(c, 1), kp)] = c ? eo_pair(o1, vt[1][1]) : eo_pair(vt[0][1], o1);
     }
   };
   // contractions of the three directions into this thread's points

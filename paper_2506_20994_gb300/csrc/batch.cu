@@ -49,7 +49,7 @@ int choose_body(int lx) {
 double elem_cost(int lx, bool f64, bool eo) {
   double ns;
   if (f64 && eo)
-    ns = lx == 6 ? 10.8 : lx == 8 ? 7.2 : 8.6;
+    ns = lx == 6 ? 7.4 : lx == 8 ? 7.2 : 8.6;
   else if (eo)  // fp32 even-odd body: single-mesh rates scaled to the batch CTA
     ns = lx <= 6 ? 3.9 : lx == 8 ? 3.0 : 4.2;
   else if (f64)

@@ -64,6 +64,7 @@ __host__ __device__ constexpr int batch_kloop_epb(int lx) {
 // concatenation of items [ib, ie); M: the body's mesh operands.
 template <class M>
 struct SeqItemsT {
+  static constexpr bool kRotate10 = false;  // line layout of the fp64 body, see eop::lpos
   const BatchItem *items;
   int ib, ie, slot, S;
   const M *meshes;
