@@ -94,9 +94,12 @@ int ax_helm(double *w, const double *u, const double *dx, const double *dxt,
             const double *g23, int lx, int nelv, void *stream);
 
 /* Explicit fp64 variants (same arguments, errors and range as ax_helm).
- * AUTO: the even-odd kernel for lx 8, 10, 12, the double-float k-loop
+ * AUTO: the even-odd kernel for lx 6, 8, 10, 12, the double-float k-loop
  * kernel for every other lx, unless ax_tune_variant_run / _set recorded
- * another. */
+ * another.  The even-odd variant runs a persistent kernel that streams each
+ * element's geometry into shared memory with bulk copies when lx is 6-12,
+ * elems_per_block is 0 and the seven geometry arrays are 16-byte aligned;
+ * otherwise its per-block form (elems_per_block elements per block). */
 #define AX_VARIANT_AUTO 0
 #define AX_VARIANT_F64_NATIVE 1 /* fp64 FMA units                           */
 #define AX_VARIANT_F64_DF 2     /* pairs of fp32 (double-float) arithmetic   */

@@ -81,6 +81,44 @@ int eop_launch_lx(const EopArgs &a, cudaStream_t st) {
   return eop_launch_t<LX, false, false>(a, st);
 }
 
+// ax_helm on fp64 arrays (RAW body): grid of resident CTAs, cached per device
+template <int LX>
+int eopr_launch_lx(double *w, const double *u, const double *dx, const double *dxt,
+                   const guard::RawGeo &raw, int nelv, cudaStream_t st) {
+  using C = eop::Cfg<LX>;
+  static std::atomic<int> grid[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    (void)cudaGetLastError();
+    return AX_ELAUNCH;
+  }
+  int g = grid[dev].load(std::memory_order_acquire);
+  if (g <= 0) {
+    auto kern = eop::ax_eopr_kernel<LX>;
+    int sms = 0, bps = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, C::NTB, C::SMEM) !=
+            cudaSuccess ||
+        bps < 1) {
+      (void)cudaGetLastError();
+      return AX_ELAUNCH;
+    }
+    g = sms * bps;
+    grid[dev].store(g, std::memory_order_release);
+  }
+  eop::EopMesh m{};
+  m.w = w;
+  m.u = u;
+  m.raw = raw;
+  m.dx = dx;
+  m.dxt = dxt;
+  const unsigned nb = (unsigned)std::min<long long>(g, std::max(nelv, 1));
+  eop::ax_eopr_kernel<LX><<<nb, C::NTB, C::SMEM, st>>>(m, (long long)nelv);
+  return launch_status();
+}
+
 template <int LX>
 int eop_blocks_lx(int nelv, bool dot) {
   const int g = dot ? eop_grid_dot<LX>() : eop_grid<LX, false, false>();
@@ -119,6 +157,22 @@ __global__ void geo_urange_kernel(unsigned *__restrict__ keys, int nelv, int fd)
 }
 
 bool eop_supported(int lx) { return lx == 6 || lx == 8 || lx == 10 || lx == 12; }
+
+int eopr_launch(int lx, double *w, const double *u, const double *dx, const double *dxt,
+                const guard::RawGeo &raw, int nelv, cudaStream_t st) {
+  // the bulk copies read whole 16-byte aligned runs of every field
+  auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
+  if (!(al(raw.h1) && al(raw.g11) && al(raw.g22) && al(raw.g33) && al(raw.g12) &&
+        al(raw.g13) && al(raw.g23)))
+    return AX_EINVAL;
+  switch (lx) {
+    case 6: return eopr_launch_lx<6>(w, u, dx, dxt, raw, nelv, st);
+    case 8: return eopr_launch_lx<8>(w, u, dx, dxt, raw, nelv, st);
+    case 10: return eopr_launch_lx<10>(w, u, dx, dxt, raw, nelv, st);
+    case 12: return eopr_launch_lx<12>(w, u, dx, dxt, raw, nelv, st);
+    default: return AX_EINVAL;
+  }
+}
 
 int eop_launch(int lx, const EopArgs &a, cudaStream_t st) {
   if (a.pw && !(a.dotp && a.r && a.minv && a.beta)) return AX_EINVAL;

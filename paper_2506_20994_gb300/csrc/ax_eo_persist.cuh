@@ -55,7 +55,9 @@ struct Cfg {
   static constexpr size_t OFF_G = OFF_LINES + (LINE_BYTES + 127) / 128 * 128;
   static constexpr size_t OFF_MISC = OFF_G + GBYTES;
   // mbarrier (8 B, padded to 16), one key slot and one dot slot per warp
-  static constexpr size_t SMEM = OFF_MISC + 16 + NW * 8 + NW * 8;
+  // (raw-array form: the key slots of G and h1 share the dot slots, and 16
+  // bytes hold the matrices' largest entry and symmetry defect)
+  static constexpr size_t SMEM = OFF_MISC + 16 + NW * 8 + NW * 8 + 16;
   // resident CTAs per SM the launch bounds ask for
   static constexpr int MINB = LX == 6 ? 8 : LX == 8 ? 4 : LX == 10 ? 2 : 1;
   static_assert(LINE_BYTES >= 3 * (size_t)N3 * 8, "fallback scratch must fit the lines");
@@ -99,6 +101,19 @@ AX_D void mbar_init(uint32_t bar, uint32_t count) {
 AX_D void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+// The same as several copies on one phase: one arrival announcing all
+// bytes, then the copies (bulk_copy).
+AX_D void mbar_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+AX_D void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
           "r"(dst),
@@ -186,9 +201,15 @@ struct SeqOne {
 // solver's next direction in place (EopUpd), fp64 with explicit roundings,
 // and the operator is applied to it.  err: set to 1 if a staged copy never
 // arrived (the body then stops).
-template <int LX, bool DOT, bool PUPD, class Seq, class Sync, class SyncAnd>
+// RAW: the geometry comes straight from the caller's fp64 arrays (M.raw;
+// seven bulk copies per element, split per apply), the coefficients and the
+// matrices' exponent field and symmetry are formed here from M.dx, M.dxt,
+// and each element's exponent window is checked from its own values; M.gp,
+// M.coef and M.urange are not used.  (ax_helm on fp64 arrays.)
+template <int LX, bool DOT, bool PUPD, bool RAW = false, class Seq, class Sync, class SyncAnd>
 AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd sync_and,
                   int *err, const EopUpd &up, double &dsum) {
+  static_assert(!RAW || (!DOT && !PUPD), "the raw-array form is the plain apply");
   using namespace df;
   using C = Cfg<LX>;
   constexpr int H = C::H, N = C::N, H2 = C::H2, NT = C::NT, NW = C::NW, N3 = C::N3;
@@ -202,6 +223,11 @@ AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
   dd2 *Gs = reinterpret_cast<dd2 *>(sm + C::OFF_G);
   const uint32_t bar = smem_u32(sm + C::OFF_MISC);
   unsigned *kslot = reinterpret_cast<unsigned *>(sm + C::OFF_MISC + 16);
+  unsigned *gslot = reinterpret_cast<unsigned *>(sm + C::OFF_MISC + 16 + NW * 8);  // RAW
+  unsigned long long *drec =
+      reinterpret_cast<unsigned long long *>(sm + C::OFF_MISC + 16 + NW * 16);  // RAW
+  bool raw_ok = true;  // RAW: matrices centro-antisymmetric, finite
+  int raw_fd = 0;      // RAW: their exponent field
 
   const bool real = tid < NT;
   const int t = real ? tid >> 1 : 0, c = tid & 1;
@@ -266,9 +292,61 @@ AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
   };
 
   auto load_coef = [&](const EopMesh &M) __attribute__((always_inline)) {
-    for (int q = tid; q < (int)(C::COEF_BYTES / 16); q += C::NTB)
-      reinterpret_cast<ulonglong2 *>(sm)[q] =
-          __ldg(reinterpret_cast<const ulonglong2 *>(M.coef) + q);
+    if constexpr (RAW) {
+      // what the handle's set-up does on the host (eop_coefficients)
+      if (tid == 0) {
+        drec[0] = 0ull;
+        drec[1] = 0ull;
+      }
+      sync();
+      for (int q = tid; q < LX * LX; q += C::NTB) {
+        const int l = q / LX, i = q % LX;
+#pragma unroll
+        for (int tr = 0; tr < 2; ++tr) {
+          const double *m = tr ? M.dxt : M.dx;
+          const double a = __ldg(m + q), mir = __ldg(m + (N - l) * LX + (N - i));
+          atomicMax(&drec[0], guard::abs_bits(a));
+          atomicMax(&drec[1], guard::abs_bits(__dadd_rn(a, mir)));
+        }
+      }
+      for (int q = tid; q < 2 * H2; q += C::NTB) {
+        const int tr = q / H2, i = (q / H) % H, l = q % H;
+        const double *m = tr ? M.dxt : M.dx;
+        const double a = __ldg(m + l * LX + i), b = __ldg(m + (N - l) * LX + i);
+        const df2 P = split_rn(__dmul_rn(0.5, __dadd_rn(a, b)));
+        const df2 Q = split_rn(__dmul_rn(0.5, __dsub_rn(a, b)));
+        cf[(tr * H + i) * CS + l] = dd2{pk(P.hi, Q.hi), pk(P.lo, Q.lo)};
+        cn[tr * H2 + i * H + l] = pk(negf(P.hi), negf(Q.hi));
+      }
+      sync();
+      const double dmax = __longlong_as_double((long long)drec[0]);
+      const double ddev = __longlong_as_double((long long)drec[1]);
+      raw_ok = isfinite(dmax) && ddev <= dmax * 0x1p-46;
+      raw_fd = (int)((drec[0] >> 52) & 0x7FFull);
+    } else {
+      for (int q = tid; q < (int)(C::COEF_BYTES / 16); q += C::NTB)
+        reinterpret_cast<ulonglong2 *>(sm)[q] =
+            __ldg(reinterpret_cast<const ulonglong2 *>(M.coef) + q);
+    }
+  };
+  // one thread: this element's geometry into Gs (completion on `bar`)
+  auto issue_geo = [&](const EopPos &p) __attribute__((always_inline)) {
+    const EopMesh &M = seq.mesh(seq.mesh_of(p));
+    if constexpr (RAW) {
+      const size_t eo = (size_t)seq.elem(p) * N3;
+      const uint32_t dst = smem_u32(Gs);
+      constexpr uint32_t FB = N3 * 8;
+      mbar_expect(bar, 7 * FB);
+      bulk_copy(dst, M.raw.g11 + eo, FB, bar);
+      bulk_copy(dst + FB, M.raw.g22 + eo, FB, bar);
+      bulk_copy(dst + 2 * FB, M.raw.g33 + eo, FB, bar);
+      bulk_copy(dst + 3 * FB, M.raw.g12 + eo, FB, bar);
+      bulk_copy(dst + 4 * FB, M.raw.g13 + eo, FB, bar);
+      bulk_copy(dst + 5 * FB, M.raw.g23 + eo, FB, bar);
+      bulk_copy(dst + 6 * FB, M.raw.h1 + eo, FB, bar);
+    } else {
+      bulk_load(smem_u32(Gs), M.gp + (size_t)seq.elem(p) * C::GE, C::GBYTES, bar);
+    }
   };
 
   // ---- set-up: barrier, first element's geometry and inputs
@@ -277,10 +355,7 @@ AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
   bool have = seq.first(pos);
   int cmesh = -1;  // mesh whose coefficients are staged
   sync();  // the barrier is initialised before anyone waits on it
-  if (tid == 0 && have) {
-    const EopMesh &M = seq.mesh(seq.mesh_of(pos));
-    bulk_load(smem_u32(Gs), M.gp + (size_t)seq.elem(pos) * C::GE, C::GBYTES, bar);
-  }
+  if (tid == 0 && have) issue_geo(pos);
 
   double uv[2][2] = {{0.0, 0.0}, {0.0, 0.0}};      // u (or r) of the element in turn
   double mv[2][2], pv[2][2], qv[2][2];             // PUPD: minv, old direction, corr
@@ -317,7 +392,7 @@ AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
     const EopMesh &M = seq.mesh(cmesh);
     const size_t eb = (size_t)seq.elem(pos) * N3;
     // this element's admissible exponent fields of u (guard.cuh, u_range)
-    const uint2 ur_e = __ldg(M.urange + seq.elem(pos));
+    const uint2 ur_e = RAW ? make_uint2(0u, 0u) : __ldg(M.urange + seq.elem(pos));
     // ---- phase 1: this element's u (or the direction formed here), split,
     // lines of the three directions; the next element's inputs start loading
     double ucur[2][2];
@@ -353,13 +428,30 @@ AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
 
     // ---- phase 3: pointwise h1 G with this element's staged geometry
     const bool got = mbar_wait(bar, parity, kWaitLimit);
+    unsigned gk = 0u, hk = 0u;  // RAW: exponent keys of this thread's G and h1 values
     {
       const u64 zero = pk(0.f, 0.f);
 #pragma unroll
       for (int b = 0; b < 2; ++b) {
         dd2 g[7];
+        if constexpr (RAW) {  // fields g11, g22, g33, g12, g13, g23, h1 as staged
+          const double *Gr = reinterpret_cast<const double *>(Gs);
+          const int q0 = real ? pidx(b, 0) : 0, q1 = real ? pidx(b, 1) : 0;
 #pragma unroll
-        for (int f = 0; f < 7; ++f) g[f] = Gs[(b * 7 + f) * NT + (real ? tid : 0)];
+          for (int f = 0; f < 7; ++f) {
+            const double v0 = Gr[f * N3 + q0], v1 = Gr[f * N3 + q1];
+            const unsigned k = max(guard::key(v0), guard::key(v1));
+            if (f < 6)
+              gk = max(gk, k);
+            else
+              hk = max(hk, k);
+            const df2 s0 = split(v0), s1 = split(v1);
+            g[f] = dd2{pk(s0.hi, s1.hi), pk(s0.lo, s1.lo)};
+          }
+        } else {
+#pragma unroll
+          for (int f = 0; f < 7; ++f) g[f] = Gs[(b * 7 + f) * NT + (real ? tid : 0)];
+        }
         const dd2 UR{pk(gr[b][0].hi, gr[b][1].hi), pk(gr[b][0].lo, gr[b][1].lo)};
         const dd2 US{pk(gs[b][0].hi, gs[b][1].hi), pk(gs[b][0].lo, gs[b][1].lo)};
         const dd2 UT{pk(gt[b][0].hi, gt[b][1].hi), pk(gt[b][0].lo, gt[b][1].lo)};
@@ -385,26 +477,54 @@ AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
         gt[b][1] = df2{ly_(m.s), ly_(m.c)};
       }
     }
+    if constexpr (RAW) {
+      gk = __reduce_max_sync(0xffffffffu, real ? gk : 0u);
+      hk = __reduce_max_sync(0xffffffffu, real ? hk : 0u);
+      if ((tid & 31) == 0) {
+        gslot[2 * (tid >> 5)] = gk;
+        gslot[2 * (tid >> 5) + 1] = hk;
+      }
+    }
     // every thread is done with the geometry and the gradient lines
     if (!sync_and(got)) {
-      // a staged copy never completed: record it and stop (group-uniform);
+      // a staged copy never completed: record it, write NaN into this
+      // group's remaining elements (so that the failure cannot pass
+      // unnoticed where no status word is given) and stop (group-uniform);
       // the copy may still be in flight, so wait once more, bounded
       if (tid == 0) {
         if (err) atomicExch(err, 1);
         (void)mbar_wait(bar, parity, kWaitLimit);
+      }
+      for (EopPos q = pos;;) {
+        double *wp = seq.mesh(seq.mesh_of(q)).w + (size_t)seq.elem(q) * N3;
+        for (int i = tid; i < N3; i += C::NTB) wp[i] = __longlong_as_double(0x7ff8000000000000ll);
+        EopPos q2;
+        if (!seq.advance(q, q2)) break;
+        q = q2;
       }
       have = false;
       break;
     }
     if (tid == 0 && more) {
       fence_async_smem();
-      const EopMesh &Mn = seq.mesh(seq.mesh_of(nxp));
-      bulk_load(smem_u32(Gs), Mn.gp + (size_t)seq.elem(nxp) * C::GE, C::GBYTES, bar);
+      issue_geo(nxp);
     }
     unsigned uke = 0u;
 #pragma unroll
     for (int q = 0; q < NW; ++q) uke = max(uke, kslot[q]);
-    const bool bad = !guard::u_in_range(ur_e, guard::field(uke));
+    bool bad;
+    if constexpr (RAW) {
+      unsigned gke = 0u, hke = 0u;
+#pragma unroll
+      for (int q = 0; q < NW; ++q) {
+        gke = max(gke, gslot[2 * q]);
+        hke = max(hke, gslot[2 * q + 1]);
+      }
+      bad = !raw_ok || !guard::window_ok(guard::field(uke), guard::field(gke),
+                                         guard::field(hke), raw_fd);
+    } else {
+      bad = !guard::u_in_range(ur_e, guard::field(uke));
+    }
 
     // ---- phase 4: lines of the weighted gradient
     publish(Lb, gr, gs, gt);
@@ -476,6 +596,19 @@ ax_eop_kernel(const EopMesh mesh, long long nelv, int *__restrict__ err,
       dotp[blockIdx.x] = s;
     }
   }
+}
+
+// ax_helm on fp64 arrays: the same schedule on the caller's arrays (RAW).
+template <int LX>
+__global__ void __launch_bounds__(Cfg<LX>::NTB, Cfg<LX>::MINB)
+ax_eopr_kernel(const EopMesh mesh, long long nelv) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const SeqOne seq{mesh, nelv};
+  double dsum = 0.0;
+  const EopUpd none{nullptr, nullptr, nullptr, nullptr, 0.0, false};
+  eop_run<LX, false, false, true>(
+      sm, (int)threadIdx.x, seq, [] { __syncthreads(); },
+      [](bool p) { return __syncthreads_and(p) != 0; }, nullptr, none, dsum);
 }
 
 // Prepared geometry of this kernel: per element, entry (b * 7 + f) * NT + tid

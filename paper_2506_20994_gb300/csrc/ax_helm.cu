@@ -47,15 +47,16 @@ int ax_helm_variant(int variant, double *w, const double *u, const double *dx,
   int rc = check_args(w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, lx, nelv);
   if (rc != AX_OK) return rc > 0 ? AX_OK : rc;
   cudaStream_t st = (cudaStream_t)stream;
-  // measured on GB300 at E = 32768 / 13824 / 8000: the even-odd kernel wins
-  // for lx 8, 10, 12; the k-loop double-float kernel for the other lx (13-16
-  // included: the fp64 units run only on request)
+  // measured on GB300 at E = 32768: the persistent even-odd kernel wins for
+  // lx 6, 8, 10, 12 (197 / 416 / 989 / 2021 us against 218 / 564 / 2133 /
+  // 4440 for the k-loop); the k-loop double-float kernel for the other lx
+  // (13-16 included: the fp64 units run only on request)
   if (variant == AX_VARIANT_AUTO) {
     const int v = g_variant[lx].load(std::memory_order_relaxed);
     if (v != 0) variant = v;
   }
   if (variant == AX_VARIANT_AUTO)
-    variant = (lx == 8 || lx == 10 || lx == 12) ? AX_VARIANT_F64_DF_EO
+    variant = (lx == 6 || lx == 8 || lx == 10 || lx == 12) ? AX_VARIANT_F64_DF_EO
               : lx <= ax::AX_DF64_LX_MAX        ? AX_VARIANT_F64_DF
                                                 : AX_VARIANT_F64_NATIVE;
   switch (variant) {
@@ -63,6 +64,11 @@ int ax_helm_variant(int variant, double *w, const double *u, const double *dx,
       return ax::dispatch_kstep_f64(lx, w, u, dx, dxt, h1, g11, g22, g33, g12,
                                                     g13, g23, nelv, elems_per_block, st);
     case AX_VARIANT_F64_DF_EO:
+      if (elems_per_block <= 0) {  // the persistent form (lx 6-12, aligned arrays)
+        const ax::guard::RawGeo raw{h1, g11, g22, g33, g12, g13, g23};
+        const int rp = ax::eopr_launch(lx, w, u, dx, dxt, raw, nelv, st);
+        if (rp != AX_EINVAL) return rp;
+      }
       return ax::dispatch_df64eo(lx, w, u, dx, dxt, h1, g11, g22, g33, g12, g13, g23, nelv,
                                  elems_per_block, st);
     case AX_VARIANT_F64_DF:

@@ -110,6 +110,11 @@ struct EopArgs {
   const int *use_corr = nullptr;
 };
 bool eop_supported(int lx);
+// The persistent even-odd kernel on the caller's fp64 arrays (ax_helm, no
+// handle): lx in {6, 8, 10, 12} and 16-byte aligned geometry arrays, else
+// AX_EINVAL (the caller then takes another kernel).
+int eopr_launch(int lx, double *w, const double *u, const double *dx, const double *dxt,
+                const guard::RawGeo &raw, int nelv, cudaStream_t st);
 int eop_launch(int lx, const EopArgs &a, cudaStream_t st);
 int eop_blocks(int lx, int nelv, bool dot);
 // dfield: as eop_coefficients reports it (the per-element u ranges depend on it)
