@@ -264,6 +264,32 @@ def test_f64_even_odd_parity(lx, dims):
     assert np.abs(w - case["w"]).max() <= 1e-11 * np.abs(case["w"]).max()
 
 
+@pytest.mark.parametrize("lx", [6, 8, 10, 12])
+@pytest.mark.parametrize("form", ["persistent", "per_block", "unaligned"])
+def test_f64_even_odd_forms(lx, form):
+    """Both forms of the even-odd variant on fp64 arrays: the persistent one
+    (bulk-copied geometry; elements_per_block = 0, aligned arrays), the
+    per-block one (an explicit elements-per-block count), and the fallback
+    when the geometry arrays start 8 bytes past a 16-byte boundary."""
+    case = operator_case((5, 3, 2), lx, seed=60 + lx)
+    off = 1 if form == "unaligned" else 0
+
+    def put(a):
+        flat = np.ascontiguousarray(a).reshape(-1)
+        buf = torch.zeros(flat.size + off, dtype=torch.float64, device="cuda")
+        buf[off:] = torch.as_tensor(flat, device="cuda")
+        return buf[off:].view(np.shape(a))
+
+    args = [put(case[k]) for k in ("u", "dx", "dxt", "h1") + GKEYS]
+    w = torch.full_like(args[0], float("nan"))
+    ax.ax_helm(w, *args, lx, variant=ax.AX_VARIANT_F64_DF_EO,
+               elems_per_block=(1 if form == "per_block" else 0))
+    torch.cuda.synchronize()
+    w = w.cpu().numpy()
+    assert rel_l2(w, case["w"]) <= TOL["f64"]
+    assert np.abs(w - case["w"]).max() <= 1e-11 * np.abs(case["w"]).max()
+
+
 def test_f64_even_odd_rejects_odd_lx():
     case = operator_case((1, 1, 1), 5, seed=1)
     with pytest.raises(ax.AxError):
