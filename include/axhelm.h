@@ -226,10 +226,16 @@ int ax_op_set_h2(ax_op *op, const double *h2, const double *B, void *stream);
 int ax_op_info(const ax_op *op, int *prepared, int64_t *device_bytes);
 /* *flag = 1 if an apply on the prepared path gave up waiting for the
  * bulk copy that stages an element's geometry in shared memory (every wait
- * is bounded, so a lost copy ends the launch with this flag set instead of
- * hanging; the output is then incomplete), else 0.  Synchronises the
- * device; the flag stays set for the life of the handle. */
+ * is bounded, to about 2 s, so a lost copy ends the launch with this flag
+ * set instead of hanging; the elements the affected CTA had left are then
+ * written as NaN), else 0.  Synchronises the device; the flag stays set for
+ * the life of the handle. */
 int ax_op_error(const ax_op *op, int *flag);
+/* Testing aid for that path: later plain applies (ax_op_apply) on the
+ * prepared path run a kernel that does not issue the geometry copy of
+ * `element` (0 <= element < nelv), so its wait runs out; element = -1 turns
+ * this off.  AX_EINVAL otherwise. */
+int ax_op_inject_copy_loss(ax_op *op, int64_t element);
 int ax_op_destroy(ax_op *op);
 
 /* ------------------------------------------------------------------------

@@ -80,6 +80,7 @@ PROTOTYPES = {
     "ax_op_set_h1": (c_int, [P, P, P]),
     "ax_op_info": (c_int, [P, P, P]),
     "ax_op_error": (c_int, [P, P]),
+    "ax_op_inject_copy_loss": (c_int, [P, c_int64]),
     "ax_op_destroy": (c_int, [P]),
     "ax_poisson_diag": (c_int, [P, P, P]),
     "ax_poisson_set_diag": (c_int, [P, P, P]),

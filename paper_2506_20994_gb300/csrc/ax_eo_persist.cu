@@ -67,7 +67,18 @@ int eop_launch_t(const EopArgs &a, cudaStream_t st) {
   m.raw = a.raw;
   m.dx = a.dx;
   m.dxt = a.dxt;
+  m.drop = a.drop;
   eop::EopUpd up{a.pw, a.r, a.minv, a.corr, 0.0, false};
+  if constexpr (!DOT && !PUPD) {
+    if (a.drop >= 0) {  // testing aid: same grid, its own instantiation
+      cudaFuncSetAttribute(eop::ax_eop_kernel<LX, false, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+      eop::ax_eop_kernel<LX, false, false, true><<<grid, C::NTB, C::SMEM, st>>>(
+          m, (long long)a.nelv, a.err, a.dotp, eop::EopUpd{a.pw, a.r, a.minv, a.corr, 0.0, false},
+          a.beta, a.use_corr);
+      return launch_status();
+    }
+  }
   eop::ax_eop_kernel<LX, DOT, PUPD><<<grid, C::NTB, C::SMEM, st>>>(m, (long long)a.nelv, a.err,
                                                                   a.dotp, up, a.beta,
                                                                   a.use_corr);

@@ -122,9 +122,18 @@ AX_D void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 }
 // Generic-proxy reads of a buffer before the bulk engine rewrites it.
 AX_D void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// Waits for the mbarrier phase with the given parity; false after `limit`
-// polls (each poll may suspend the thread for a short, bounded time).
+AX_D unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// A wait gives up after kWaitNs of global time (or `limit` polls, a
+// backstop; each poll may suspend the thread for a short, bounded time).
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+constexpr int kWaitLimit = 1 << 30;
+// Waits for the mbarrier phase with the given parity; false when it gave up.
 AX_D bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+  unsigned long long t0 = 0ull;
   for (int it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
@@ -135,10 +144,16 @@ AX_D bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
+    if ((it & 1023) == 1023) {  // the clock only once a wait is long
+      const unsigned long long t = global_ns();
+      if (t0 == 0ull)
+        t0 = t;
+      else if (t - t0 > kWaitNs)
+        return false;
+    }
   }
   return false;
 }
-constexpr int kWaitLimit = 1 << 22;
 
 // exchange of one pair with the partner lane (tid ^ 1)
 AX_D df::df2 xchg(df::df2 v) {
@@ -149,12 +164,15 @@ AX_D df::df2 xchg(df::df2 v) {
 // geometry (gp) and its per-element u exponent ranges, the staged
 // coefficient block, and the fp64 arrays an element falls back to.
 struct EopMesh {
-  double *w;
-  const double *u;
-  const df::dd2 *coef, *gp;
-  const uint2 *urange;
-  guard::RawGeo raw;
-  const double *dx, *dxt;
+  double *w = nullptr;
+  const double *u = nullptr;
+  const df::dd2 *coef = nullptr, *gp = nullptr;
+  const uint2 *urange = nullptr;
+  guard::RawGeo raw{};
+  const double *dx = nullptr, *dxt = nullptr;
+  // testing aid (ax_op_inject_copy_loss): this element's geometry copy is
+  // never issued, so its wait runs out; -1: none
+  long long drop = -1;
 };
 
 // Solver operands of the fused direction update (PUPD): pw = minv .* r
@@ -206,7 +224,8 @@ struct SeqOne {
 // matrices' exponent field and symmetry are formed here from M.dx, M.dxt,
 // and each element's exponent window is checked from its own values; M.gp,
 // M.coef and M.urange are not used.  (ax_helm on fp64 arrays.)
-template <int LX, bool DOT, bool PUPD, bool RAW = false, class Seq, class Sync, class SyncAnd>
+template <int LX, bool DOT, bool PUPD, bool RAW = false, bool DROP = false, class Seq,
+          class Sync, class SyncAnd>
 AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd sync_and,
                   int *err, const EopUpd &up, double &dsum) {
   static_assert(!RAW || (!DOT && !PUPD), "the raw-array form is the plain apply");
@@ -332,6 +351,9 @@ AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
   // one thread: this element's geometry into Gs (completion on `bar`)
   auto issue_geo = [&](const EopPos &p) __attribute__((always_inline)) {
     const EopMesh &M = seq.mesh(seq.mesh_of(p));
+    if constexpr (DROP) {  // testing aid only (a kernel of its own)
+      if (seq.elem(p) == M.drop) return;
+    }
     if constexpr (RAW) {
       const size_t eo = (size_t)seq.elem(p) * N3;
       const uint32_t dst = smem_u32(Gs);
@@ -567,7 +589,8 @@ AX_D void eop_run(unsigned char *sm, int tid, const Seq &seq, Sync sync, SyncAnd
 
 // The operator handle's kernel: one mesh, elements blockIdx.x + k gridDim.x.
 // DOT: one partial of u . w per CTA (fixed order) in dotp[blockIdx.x].
-template <int LX, bool DOT, bool PUPD>
+// DROP: the testing aid of ax_op_inject_copy_loss (plain applies only).
+template <int LX, bool DOT, bool PUPD, bool DROP = false>
 __global__ void __launch_bounds__(Cfg<LX>::NTB, Cfg<LX>::MINB)
 ax_eop_kernel(const EopMesh mesh, long long nelv, int *__restrict__ err,
               double *__restrict__ dotp, const EopUpd up0,
@@ -581,7 +604,7 @@ ax_eop_kernel(const EopMesh mesh, long long nelv, int *__restrict__ err,
   }
   const SeqOne seq{mesh, nelv};
   double dsum = 0.0;
-  eop_run<LX, DOT, PUPD>(
+  eop_run<LX, DOT, PUPD, false, DROP>(
       sm, (int)threadIdx.x, seq, [] { __syncthreads(); },
       [](bool p) { return __syncthreads_and(p) != 0; }, err, up, dsum);
   if constexpr (DOT) {  // one partial per CTA: fixed shuffle tree, warps in order

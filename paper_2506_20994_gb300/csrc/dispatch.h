@@ -108,6 +108,7 @@ struct EopArgs {
   double *dotp = nullptr, *pw = nullptr;
   const double *r = nullptr, *minv = nullptr, *beta = nullptr, *corr = nullptr;
   const int *use_corr = nullptr;
+  long long drop = -1;  // testing aid: element whose geometry copy is not issued
 };
 bool eop_supported(int lx);
 // The persistent even-odd kernel on the caller's fp64 arrays (ax_helm, no

@@ -21,6 +21,7 @@ struct ax_op {
   int *err = nullptr;           // device word: a staged copy never arrived (owned)
   int dfield = 0;               // exponent field of the matrices' largest entry
   double *hb = nullptr;         // h2 .* B of the Helmholtz form (owned), or null
+  long long drop = -1;          // testing aid (ax_op_inject_copy_loss)
 };
 
 namespace {
@@ -50,6 +51,7 @@ ax::EopArgs eop_args(const ax_op *op, double *w, const double *u) {
   a.dfield = op->dfield;
   a.nelv = op->nelv;
   a.err = op->err;
+  a.drop = op->drop;
   return a;
 }
 
@@ -207,6 +209,12 @@ extern "C" int ax_op_info(const ax_op *op, int *prepared, int64_t *device_bytes)
     *device_bytes = op->gp ? (int64_t)(ax::eo_prep_bytes(op->lx, op->nelv) +
                                        ax::eop_coef_bytes(op->lx) + sizeof(int))
                            : 0;
+  return AX_OK;
+}
+
+extern "C" int ax_op_inject_copy_loss(ax_op *op, int64_t element) {
+  if (!op || element < -1 || element >= op->nelv) return AX_EINVAL;
+  op->drop = element;
   return AX_OK;
 }
 
