@@ -21,10 +21,11 @@
 //  * The (lx/2)^3 mirror octants get two threads each, thread 2t + c owning
 //    the points {i', N-i'} x {j} x {k', N-k'}, j = j' (c = 0) or N - j'
 //    (c = 1): a warp's reads of a staged field then cover the eight rows of
-//    one k-plane.  Pairs along i
-//    and k stay inside a thread; pairs along j take one shuffle with the
-//    partner lane.  The two contractions of a direction share their
-//    coefficient loads.
+//    one k-plane.  Pairs along i and k stay inside a thread; pairs along j
+//    take one shuffle with the partner lane.  The two contractions of a
+//    direction share their coefficient rows (held in registers at lx = 8).
+//  * PUPD (the refinement's inner CG): the stage holds r, minv and the old
+//    direction instead of u, and the kernel forms p = minv r + beta p first.
 //  * The (e, o) lines of the three directions go to shared memory as 8-byte
 //    entries, those of the gradient and those of the weighted gradient in
 //    two separate sets: two barriers per element (after each publication)

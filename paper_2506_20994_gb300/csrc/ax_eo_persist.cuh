@@ -24,8 +24,11 @@
 // (double-float pairs, packed f32x2, the two half-size sums of each 1-D
 // contraction as the two lanes).  Elements outside the double-float range
 // (guard.cuh) are recomputed with fp64 units from the caller's fp64 arrays;
-// matrices that are not centro-antisymmetric never reach this kernel (the
-// handle checks them when it is created).
+// matrices that are not centro-antisymmetric never reach the handle's kernel
+// (the handle checks them when it is created).  The same body also runs on
+// the caller's raw fp64 arrays (RAW, ax_helm): seven bulk copies per
+// element, geometry split per apply, matrices and exponent window checked in
+// the kernel.  Lines at lx = 6 and 10 rotate their entries (lpos).
 #pragma once
 
 #include "common.cuh"
