@@ -8,6 +8,8 @@ namespace ax {
 int dispatch_eo32_bf16(int lx, float *w, const __nv_bfloat16 *u, const float *dx, const float *dxt,
                      const __nv_bfloat16 *const g[7], int nelv, int *err, double *dotp,
                      cudaStream_t st, const E32Upd *up) {
+  // lx = 8 without the fused update: one warp per element (ax_eo32w.cuh)
+  if (lx == 8 && !up && !dotp) return dispatch_eo32w_bf16(w, u, dx, dxt, g, nelv, err, dotp, st);
   switch (lx) {
 #define AX_CASE(L) \
   case L:          \

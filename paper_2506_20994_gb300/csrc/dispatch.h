@@ -66,6 +66,13 @@ int dispatch_eo32_f32u_bf16(int lx, float *w, const float *u, const float *dx,
                             const float *dxt, const __nv_bfloat16 *const g[7], int nelv,
                             int *err, double *dotp, cudaStream_t st,
                             const E32Upd *up = nullptr);
+// The same operator at lx = 8 on bf16 data, one warp per element
+// (ax_eo32w.cuh); the same bits as dispatch_eo32_bf16.  dotp: one partial
+// per CTA, eo32w_blocks_bf16(nelv) of them.
+int dispatch_eo32w_bf16(float *w, const __nv_bfloat16 *u, const float *dx, const float *dxt,
+                        const __nv_bfloat16 *const g[7], int nelv, int *err, double *dotp,
+                        cudaStream_t st);
+int eo32w_blocks_bf16(int nelv);
 int eo32_blocks_f32(int lx, int nelv);
 int eo32_blocks_bf16(int lx, int nelv);
 int eo32_blocks_f32u_bf16(int lx, int nelv);

@@ -179,6 +179,37 @@ def test_lowp_general_matrices(mode, lx):
     assert rel_l2(w, ref) <= TOL[mode]
 
 
+@pytest.mark.parametrize("lx", [6, 8, 10, 12])
+@pytest.mark.parametrize("nel", [1, 3, 5, 611, 1237])
+@pytest.mark.parametrize("general", [False, True])
+def test_bf16_matches_f32_on_bf16_values(lx, nel, general):
+    """bf16 storage only changes what is read: on values that bf16 holds
+    exactly, ax_helm_bf16 and ax_helm_f32 do the same fp32 operations in the
+    same order (even-odd chains, pointwise h1 G, w = (r + s) + t), whatever
+    the layout of threads over the element (one warp per element at lx = 8
+    for bf16, mirror octants for fp32), so w agrees bit for bit; element
+    counts below, at and above one CTA's share, with ragged tails."""
+    g = synth.rng(700 + lx + nel)
+    shape = (nel, lx, lx, lx)
+    b = torch.bfloat16
+    q = lambda a: torch.as_tensor(a).to(device="cuda", dtype=b)
+    u = q(g.uniform(-1.0, 1.0, shape))
+    fields = [q(g.uniform(0.5, 2.0, shape))] + [q(g.uniform(-1.0, 1.0, shape)) for _ in GKEYS]
+    if general:
+        dx, dxt = g.uniform(-1.0, 1.0, (lx, lx)), g.uniform(-1.0, 1.0, (lx, lx))
+    else:
+        dx, dxt = ax.dmat(lx)
+    dx, dxt = _dev(dx, torch.float32), _dev(dxt, torch.float32)
+    wb = torch.full(shape, float("nan"), dtype=torch.float32, device="cuda")
+    wf = torch.full(shape, float("nan"), dtype=torch.float32, device="cuda")
+    ax.ax_helm_bf16(wb, u, dx, dxt, *fields, lx)
+    ax.ax_helm_f32(wf, u.float(), dx, dxt, *[f.float() for f in fields], lx)
+    torch.cuda.synchronize()
+    a, c = wb.cpu().numpy(), wf.cpu().numpy()
+    assert np.isfinite(a).all()
+    np.testing.assert_array_equal(a.view(np.uint32), c.view(np.uint32))
+
+
 @pytest.mark.parametrize("mode", ["f32", "bf16"])
 @pytest.mark.parametrize("lx", [6, 8])
 def test_lowp_unaligned_arrays(mode, lx):
