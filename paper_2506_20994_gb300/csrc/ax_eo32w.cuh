@@ -9,9 +9,10 @@
 // synchronisation is within the warp (__syncwarp): the warps of a CTA run
 // independently, each with its own stage (u and the seven geometry fields of
 // one element, bulk-copied under one mbarrier, waits bounded) and its own
-// lines.  A warp issues its next element's copy once the pointwise step has
-// read the stage, so the copy overlaps the transposed contractions and the
-// other warps' work.
+// lines.  u and the geometry complete on two mbarriers: a warp issues its
+// next element's u as soon as it holds this element's u in registers, and
+// the next geometry once the pointwise step has read this one, so each copy
+// overlaps most of an element's work.
 //
 // Same arithmetic as ax_eo32.cuh, operation for operation (chains over
 // l = 0..3, y_i = E + O, y_{N-i} = O - E, pointwise h1 G, w = (r + s) + t):
@@ -46,14 +47,13 @@ template <class SU, class SG>
 struct Cfg {
   static constexpr unsigned UBYTES = N3 * sizeof(SU);
   static constexpr unsigned GFBYTES = N3 * sizeof(SG);
-  static constexpr unsigned TXBYTES = UBYTES + 7 * GFBYTES;
-  static constexpr size_t SBYTES = e32::a128(TXBYTES);
+  static constexpr size_t SBYTES = e32::a128(UBYTES + 7 * GFBYTES);
   static constexpr size_t LBYTES = 2 * 64 * H * 8;  // r-lines (k, j) and s-lines (k, i)
   static constexpr size_t WBYTES = SBYTES + LBYTES;
   // coefficients [m][rows i, rows N - i][H][H], as in ax_eo32.cuh
   static constexpr size_t OFF_W = e32::a128(2 * 2 * H2 * 8);
   static constexpr size_t OFF_BAR = OFF_W + kWarps * WBYTES;
-  static constexpr size_t SMEM = OFF_BAR + kWarps * 8 + kWarps * 8;
+  static constexpr size_t SMEM = OFF_BAR + kWarps * 16 + kWarps * 8;
 };
 
 // entry e of line L (4 entries of 8 bytes): the 16-byte halves swap with
@@ -74,8 +74,8 @@ ax_eo32w_kernel(const e32::Mesh<SU, SG> M, long long nelv, int *__restrict__ err
   unsigned char *stg = sm + C::OFF_W + (size_t)wp * C::WBYTES;
   u64 *Lr = reinterpret_cast<u64 *>(stg + C::SBYTES);
   u64 *Ls = Lr + 64 * H;
-  const uint32_t bar = eop::smem_u32(sm + C::OFF_BAR + wp * 8);
-  double *red = reinterpret_cast<double *>(sm + C::OFF_BAR + kWarps * 8);
+  const uint32_t barU = eop::smem_u32(sm + C::OFF_BAR + wp * 16), barG = barU + 8;
+  double *red = reinterpret_cast<double *>(sm + C::OFF_BAR + kWarps * 16);
 
   // even-odd coefficients of dx (m = 0) and dxt (m = 1): M(i, l) = D[l * 8 + i]
   bool ok = true;
@@ -91,22 +91,30 @@ ax_eo32w_kernel(const e32::Mesh<SU, SG> M, long long nelv, int *__restrict__ err
     cf[m * 2 * H2 + H2 + i * H + l] = pk(A2, B2);
     ok = ok && A2 == -A && B2 == B;
   }
-  if (lane == 0) eop::mbar_init(bar, 1);
+  if (lane == 0) {
+    eop::mbar_init(barU, 1);
+    eop::mbar_init(barG, 1);
+  }
   // coefficients and barriers ready; from here on the warps are independent
   const bool gen_m = __syncthreads_and(ok) == 0;
 
-  auto issue = [&](long long e) __attribute__((always_inline)) {
-    const size_t eo = (size_t)e * N3;
-    const uint32_t dst = eop::smem_u32(stg);
-    eop::mbar_expect(bar, C::TXBYTES);
-    eop::bulk_copy(dst, M.u + eo, C::UBYTES, bar);
+  auto issue_u = [&](long long e) __attribute__((always_inline)) {
+    eop::mbar_expect(barU, C::UBYTES);
+    eop::bulk_copy(eop::smem_u32(stg), M.u + (size_t)e * N3, C::UBYTES, barU);
+  };
+  auto issue_g = [&](long long e) __attribute__((always_inline)) {
+    const uint32_t dst = eop::smem_u32(stg) + C::UBYTES;
+    eop::mbar_expect(barG, 7 * C::GFBYTES);
 #pragma unroll
     for (int f = 0; f < 7; ++f)
-      eop::bulk_copy(dst + C::UBYTES + f * C::GFBYTES, M.g[f] + eo, C::GFBYTES, bar);
+      eop::bulk_copy(dst + f * C::GFBYTES, M.g[f] + (size_t)e * N3, C::GFBYTES, barG);
   };
   const long long nw = (long long)gridDim.x * kWarps;
   long long e = (long long)blockIdx.x * kWarps + wp;
-  if (lane == 0 && e < nelv) issue(e);
+  if (lane == 0 && e < nelv) {
+    issue_u(e);
+    issue_g(e);
+  }
   __syncwarp();
 
   // this lane's values of row (k, j) of one staged field at i' and 7 - i'.
@@ -215,49 +223,69 @@ ax_eo32w_kernel(const e32::Mesh<SU, SG> M, long long nelv, int *__restrict__ err
       y[k][1] = add ? __fadd_rn(y[k][1], y1) : y1;
     }
   };
-  // t-contractions of this lane's two columns, in registers
+  // t-contractions of this lane's two columns, in registers (centro-
+  // antisymmetric matrices: each coefficient row read once for both)
   auto contract_t = [&](const u64 *cof, const float (&v)[LX][2], float (&y)[LX][2], bool add,
-                        auto gen)
-                        __attribute__((always_inline)) {
+                        auto gen) __attribute__((always_inline)) {
+    auto put = [&](int kr, int a, float y0, float y1) __attribute__((always_inline)) {
+      y[kr][a] = add ? __fadd_rn(y[kr][a], y0) : y0;
+      y[N - kr][a] = add ? __fadd_rn(y[N - kr][a], y1) : y1;
+    };
+    if constexpr (decltype(gen)::value) {
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      u64 ln[H];
+      for (int a = 0; a < 2; ++a) {
+        u64 ln[H];
 #pragma unroll
-      for (int l = 0; l < H; ++l) ln[l] = eo(v[l][a], v[N - l][a]);
+        for (int l = 0; l < H; ++l) ln[l] = eo(v[l][a], v[N - l][a]);
+#pragma unroll
+        for (int kr = 0; kr < H; ++kr) {
+          u64 cr[H];
+          row(cof, kr, cr);
+          const u64 c = chainR(ln, cr);
+          row(cof + H2, kr, cr);
+          const u64 b = chainR(ln, cr);
+          put(kr, a, __fadd_rn(lo_(c), hi_(c)), __fadd_rn(lo_(b), hi_(b)));
+        }
+      }
+    } else {
+      u64 ln[2][H];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int l = 0; l < H; ++l) ln[a][l] = eo(v[l][a], v[N - l][a]);
 #pragma unroll
       for (int kr = 0; kr < H; ++kr) {
         u64 cr[H];
         row(cof, kr, cr);
-        const u64 c = chainR(ln, cr);
-        const float y0 = __fadd_rn(lo_(c), hi_(c));
-        float y1 = __fsub_rn(hi_(c), lo_(c));
-        if constexpr (decltype(gen)::value) {
-          row(cof + H2, kr, cr);
-          const u64 b = chainR(ln, cr);
-          y1 = __fadd_rn(lo_(b), hi_(b));
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const u64 c = chainR(ln[a], cr);
+          put(kr, a, __fadd_rn(lo_(c), hi_(c)), __fsub_rn(hi_(c), lo_(c)));
         }
-        y[kr][a] = add ? __fadd_rn(y[kr][a], y0) : y0;
-        y[N - kr][a] = add ? __fadd_rn(y[N - kr][a], y1) : y1;
       }
     }
+  };
+
+  // a staged copy never completed: record it, write NaN into this warp's
+  // elements from e on, wait once more (bounded) for the copies that may
+  // still be in flight (phases pu of u, pg of the geometry)
+  auto fail = [&](unsigned pu, unsigned pg) {
+    if (lane == 0) {
+      if (err) atomicExch(err, 1);
+      (void)eop::mbar_wait(barU, pu, eop::kWaitLimit);
+      (void)eop::mbar_wait(barG, pg, eop::kWaitLimit);
+    }
+    for (long long q = e; q < nelv; q += nw)
+      for (int i = lane; i < N3; i += 32) M.w[(size_t)q * N3 + i] = __int_as_float(0x7fc00000);
   };
 
   double dsum = 0.0;
   // the element loop, compiled for both matrix forms (gen: CTA-uniform)
   auto run = [&](auto gen) __attribute__((always_inline)) {
     for (unsigned parity = 0u; e < nelv; e += nw, parity ^= 1u) {
-      const bool got = eop::mbar_wait(bar, parity, eop::kWaitLimit);
-      if (!__all_sync(0xffffffffu, got)) {
-        // a staged copy never completed: record it, write NaN into this
-        // warp's remaining elements, wait for the copy once more (bounded)
-        // and stop
-        if (lane == 0) {
-          if (err) atomicExch(err, 1);
-          (void)eop::mbar_wait(bar, parity, eop::kWaitLimit);
-        }
-        for (long long q = e; q < nelv; q += nw)
-          for (int i = lane; i < N3; i += 32)
-            M.w[(size_t)q * N3 + i] = __int_as_float(0x7fc00000);
+      const bool more = e + nw < nelv;
+      if (!__all_sync(0xffffffffu, eop::mbar_wait(barU, parity, eop::kWaitLimit))) {
+        fail(parity, parity);
         break;
       }
       const SU *U = reinterpret_cast<const SU *>(stg);
@@ -265,6 +293,11 @@ ax_eo32w_kernel(const e32::Mesh<SU, SG> M, long long nelv, int *__restrict__ err
       float v[LX][2];
 #pragma unroll
       for (int k = 0; k < LX; ++k) rowv(U, k, v[k][0], v[k][1]);
+      __syncwarp();  // u is in registers: the next element's u may replace it
+      if (lane == 0 && more) {
+        eop::fence_async_smem();
+        issue_u(e + nw);
+      }
 
       // reference gradient
       float gr[LX][2], gs[LX][2], gt[LX][2];
@@ -274,7 +307,11 @@ ax_eo32w_kernel(const e32::Mesh<SU, SG> M, long long nelv, int *__restrict__ err
       contract_t(cf, v, gt, false, gen);
       __syncwarp();  // the lines are read
 
-      // pointwise h1 G
+      // pointwise h1 G (the next u, if any, is in flight on phase parity ^ 1)
+      if (!__all_sync(0xffffffffu, eop::mbar_wait(barG, parity, eop::kWaitLimit))) {
+        fail(more ? parity ^ 1u : parity, parity);
+        break;
+      }
 #pragma unroll
       for (int k = 0; k < LX; ++k) {
         float h[2], g11[2], g22[2], g33[2], g12[2], g13[2], g23[2];
@@ -296,10 +333,10 @@ ax_eo32w_kernel(const e32::Mesh<SU, SG> M, long long nelv, int *__restrict__ err
               h[a], __fmaf_rn(g33[a], ut, __fmaf_rn(g23[a], us, __fmul_rn(g13[a], ur))));
         }
       }
-      __syncwarp();  // the stage is read: the next element's copy may replace it
-      if (lane == 0 && e + nw < nelv) {
+      __syncwarp();  // the geometry is read: the next element's may replace it
+      if (lane == 0 && more) {
         eop::fence_async_smem();
-        issue(e + nw);
+        issue_g(e + nw);
       }
 
       // transposed contractions, w = (r + s) + t
@@ -325,7 +362,10 @@ ax_eo32w_kernel(const e32::Mesh<SU, SG> M, long long nelv, int *__restrict__ err
   else
     run(std::false_type{});
   __syncwarp();
-  if (lane == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+  if (lane == 0) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(barU) : "memory");
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(barG) : "memory");
+  }
   if constexpr (DOT) {  // one partial per CTA: fixed shuffle tree, warps in order
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
