@@ -1,5 +1,6 @@
 // One warp per element: the fp32-arithmetic even-odd operator (ax_eo32.cuh)
-// at lx = 8, with the t-direction (along k) contracted in registers.
+// at lx = 8 on bf16 geometry (u in bf16, or the solvers' fp32 vectors), with
+// the t-direction (along k) contracted in registers.
 //
 // Lane 4 j + i' owns the 16 points {i', 7 - i'} x {j} x {k = 0..7}.  Its two
 // k-columns are whole, so the t-contractions (even-odd on the columns'
@@ -15,8 +16,10 @@
 // overlaps most of an element's work.
 //
 // Same arithmetic as ax_eo32.cuh, operation for operation (chains over
-// l = 0..3, y_i = E + O, y_{N-i} = O - E, pointwise h1 G, w = (r + s) + t):
-// the two kernels give the same bits.  Matrices that are not
+// l = 0..3, y_i = E + O, y_{N-i} = O - E, pointwise h1 G, w = (r + s) + t;
+// with the solver's fused direction update, p = minv r + beta p first): the
+// two kernels give the same w.  The dot partial (DOT) sums the same products
+// in another order.  Matrices that are not
 // centro-antisymmetric take a second chain for the rows N - i, as there.
 // Shared memory per element and warp: about 130 load and 64 store wavefronts
 // for the lines (16-byte line reads; 8-byte entry writes) against about 450
@@ -43,11 +46,14 @@ using e32::pk;
 constexpr int LX = 8, H = 4, N = 7, H2 = 16, N3 = 512;
 constexpr int kWarps = 4;  // warps (elements in flight) per CTA
 
-template <class SU, class SG>
+// PUPD (the solver's fused direction update, fp32 vectors): the u part of
+// the stage holds r, minv and the old direction instead of u.
+template <class SU, class SG, bool PUPD = false>
 struct Cfg {
   static constexpr unsigned UBYTES = N3 * sizeof(SU);
   static constexpr unsigned GFBYTES = N3 * sizeof(SG);
-  static constexpr size_t SBYTES = e32::a128(UBYTES + 7 * GFBYTES);
+  static constexpr int NU = PUPD ? 3 : 1;  // u-sized staged arrays
+  static constexpr size_t SBYTES = e32::a128(NU * UBYTES + 7 * GFBYTES);
   static constexpr size_t LBYTES = 2 * 64 * H * 8;  // r-lines (k, j) and s-lines (k, i)
   static constexpr size_t WBYTES = SBYTES + LBYTES;
   // coefficients [m][rows i, rows N - i][H][H], as in ax_eo32.cuh
@@ -60,11 +66,20 @@ struct Cfg {
 // bit 2 of the line, so that lines L and L + 4 start in different banks
 AX_D int rpos(int L, int e) { return L * 4 + ((((e >> 1) ^ (L >> 2)) & 1) << 1) + (e & 1); }
 
-template <class SU, class SG, bool DOT>
-__global__ void __launch_bounds__(kWarps * 32, 4)
+// Resident CTAs per SM the launch bounds ask for: 4 on bf16 data without
+// the dot (128 registers); 3 where fp32 vectors or the dot partial add
+// registers and shared memory.
+template <class SU, bool DOT>
+constexpr int minb() {
+  return std::is_same_v<SU, float> || DOT ? 3 : 4;
+}
+
+template <class SU, class SG, bool DOT, bool PUPD = false>
+__global__ void __launch_bounds__(kWarps * 32, (minb<SU, DOT>()))
 ax_eo32w_kernel(const e32::Mesh<SU, SG> M, long long nelv, int *__restrict__ err,
-                double *__restrict__ dotp) {
-  using C = Cfg<SU, SG>;
+                double *__restrict__ dotp, const E32Upd up) {
+  static_assert(!PUPD || std::is_same_v<SU, float>, "the fused update keeps fp32 vectors");
+  using C = Cfg<SU, SG, PUPD>;
   extern __shared__ __align__(128) unsigned char sm[];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int ip = lane & 3, j = lane >> 2;  // i in {i', 7 - i'}; this lane's j
@@ -99,11 +114,19 @@ ax_eo32w_kernel(const e32::Mesh<SU, SG> M, long long nelv, int *__restrict__ err
   const bool gen_m = __syncthreads_and(ok) == 0;
 
   auto issue_u = [&](long long e) __attribute__((always_inline)) {
-    eop::mbar_expect(barU, C::UBYTES);
-    eop::bulk_copy(eop::smem_u32(stg), M.u + (size_t)e * N3, C::UBYTES, barU);
+    const uint32_t dst = eop::smem_u32(stg);
+    const size_t eo = (size_t)e * N3;
+    eop::mbar_expect(barU, C::NU * C::UBYTES);
+    if constexpr (PUPD) {
+      eop::bulk_copy(dst, up.r + eo, C::UBYTES, barU);
+      eop::bulk_copy(dst + C::UBYTES, up.minv + eo, C::UBYTES, barU);
+      eop::bulk_copy(dst + 2 * C::UBYTES, up.pw + eo, C::UBYTES, barU);
+    } else {
+      eop::bulk_copy(dst, M.u + eo, C::UBYTES, barU);
+    }
   };
   auto issue_g = [&](long long e) __attribute__((always_inline)) {
-    const uint32_t dst = eop::smem_u32(stg) + C::UBYTES;
+    const uint32_t dst = eop::smem_u32(stg) + C::NU * C::UBYTES;
     eop::mbar_expect(barG, 7 * C::GFBYTES);
 #pragma unroll
     for (int f = 0; f < 7; ++f)
@@ -280,6 +303,7 @@ ax_eo32w_kernel(const e32::Mesh<SU, SG> M, long long nelv, int *__restrict__ err
   };
 
   double dsum = 0.0;
+  const float beta = PUPD ? (float)*up.beta : 0.f;  // the solver's scalar, on the device
   // the element loop, compiled for both matrix forms (gen: CTA-uniform)
   auto run = [&](auto gen) __attribute__((always_inline)) {
     for (unsigned parity = 0u; e < nelv; e += nw, parity ^= 1u) {
@@ -289,11 +313,26 @@ ax_eo32w_kernel(const e32::Mesh<SU, SG> M, long long nelv, int *__restrict__ err
         break;
       }
       const SU *U = reinterpret_cast<const SU *>(stg);
-      const SG *G = reinterpret_cast<const SG *>(stg + C::UBYTES);
+      const SG *G = reinterpret_cast<const SG *>(stg + C::NU * C::UBYTES);
+      const size_t eb = (size_t)e * N3;
       float v[LX][2];
 #pragma unroll
       for (int k = 0; k < LX; ++k) rowv(U, k, v[k][0], v[k][1]);
-      __syncwarp();  // u is in registers: the next element's u may replace it
+      if constexpr (PUPD) {  // v = r here: p = minv .* r + beta p, stored
+        const float *Mi = reinterpret_cast<const float *>(stg + C::UBYTES);
+        const float *Po = reinterpret_cast<const float *>(stg + 2 * C::UBYTES);
+#pragma unroll
+        for (int k = 0; k < LX; ++k) {
+          float mi[2], po[2];
+          rowv(Mi, k, mi[0], mi[1]);
+          rowv(Po, k, po[0], po[1]);
+#pragma unroll
+          for (int a = 0; a < 2; ++a) v[k][a] = __fmaf_rn(mi[a], v[k][a], __fmul_rn(beta, po[a]));
+          up.pw[eb + (k * LX + j) * LX + ip] = v[k][0];
+          up.pw[eb + (k * LX + j) * LX + N - ip] = v[k][1];
+        }
+      }
+      __syncwarp();  // the staged vectors are read: the next element's may replace them
       if (lane == 0 && more) {
         eop::fence_async_smem();
         issue_u(e + nw);
@@ -346,7 +385,6 @@ ax_eo32w_kernel(const e32::Mesh<SU, SG> M, long long nelv, int *__restrict__ err
       contract_s(cf + 2 * H2, w, true, gen);
       contract_t(cf + 2 * H2, gt, w, true, gen);
       __syncwarp();  // the lines are read
-      const size_t eb = (size_t)e * N3;
       float el = 0.f;
 #pragma unroll
       for (int k = 0; k < LX; ++k) {

@@ -66,13 +66,19 @@ int dispatch_eo32_f32u_bf16(int lx, float *w, const float *u, const float *dx,
                             const float *dxt, const __nv_bfloat16 *const g[7], int nelv,
                             int *err, double *dotp, cudaStream_t st,
                             const E32Upd *up = nullptr);
-// The same operator at lx = 8 on bf16 data, one warp per element
-// (ax_eo32w.cuh); the same bits as dispatch_eo32_bf16.  dotp: one partial
-// per CTA, eo32w_blocks_bf16(nelv) of them.
+// The same operator at lx = 8 on bf16 geometry, one warp per element
+// (ax_eo32w.cuh): u in bf16 (dispatch_eo32_bf16 takes it without dotp) or
+// the solvers' fp32 vectors (dispatch_eo32_f32u_bf16 takes it at lx = 8 in
+// every variant, the fused update included); w has the same bits as the
+// octant kernel's.  dotp: one partial per CTA, eo32w_blocks_*(nelv) of them.
 int dispatch_eo32w_bf16(float *w, const __nv_bfloat16 *u, const float *dx, const float *dxt,
                         const __nv_bfloat16 *const g[7], int nelv, int *err, double *dotp,
                         cudaStream_t st);
+int dispatch_eo32w_f32u_bf16(float *w, const float *u, const float *dx, const float *dxt,
+                             const __nv_bfloat16 *const g[7], int nelv, int *err, double *dotp,
+                             cudaStream_t st, const E32Upd *up = nullptr);
 int eo32w_blocks_bf16(int nelv);
+int eo32w_blocks_f32u_bf16(int nelv);
 int eo32_blocks_f32(int lx, int nelv);
 int eo32_blocks_bf16(int lx, int nelv);
 int eo32_blocks_f32u_bf16(int lx, int nelv);
